@@ -1,0 +1,104 @@
+/*
+ * CPU oracle of the Looking Forward track-following path — TEST INFRASTRUCTURE.
+ *
+ * A plain, single-threaded, obviously-correct restatement of the paper's
+ * method (Sec. "Algorithm logic": search windows, triplet seeding, extension,
+ * quality filter; Sec. "Calculation of momentum and track states" in its
+ * linear pT-kick form).  It exists only to check the CUDA library: only the
+ * tests, the smoke check and the benchmark's CPU-baseline leg may load it.
+ * It shares no code, header or table with the CUDA path.
+ *
+ * Arithmetic: binary32 with round-to-nearest and no contraction (built with
+ * -ffp-contract=off), expressions evaluated in the order written; a binary64
+ * refit of the selected hits runs alongside (lfo_fit64).
+ */
+#ifndef LF_ORACLE_H
+#define LF_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LFO_NL 12   /* SciFi layers: three x-u-v-x stations */
+#define LFO_NB 24   /* (zone, layer) buckets per event: bucket = zone*12 + layer */
+
+typedef struct {
+    float z[LFO_NL];      /* layer z (mm) */
+    float dxdy[LFO_NL];   /* stereo slope: 0 for x layers, +-tan(5 deg) for u/v */
+    float z_state;        /* z of the upstream state */
+    float z_magnet;       /* kick plane */
+    float z_ref;          /* reference plane of the T-station model (8520 mm) */
+    float kappa;          /* slope kick per unit q/p (GeV rad) */
+    float gamma;          /* curvature per unit q/p (GeV/mm^2) */
+    float dratio;         /* dRatio (1/mm) */
+    int32_t polarity;     /* +1 MagUp, -1 MagDown */
+} lfo_geometry;
+
+typedef struct {
+    float xtol_c, xtol_p;       /* x_tol = xtol_c + xtol_p / p */
+    float x_asym;               /* magnet asymmetry term */
+    float uv_tol;               /* u/v window half width */
+    int32_t n_hits_window;      /* hits kept per window (<= 64) */
+    int32_t n_triplets;         /* triplets kept per input track (<= 32) */
+    int32_t min_hits;           /* >= 9 */
+    float K_first, K_last;      /* sagitta-like correction of x1_expected */
+    float p_bend;               /* bending-sign filter applies below this p */
+    float magtol_min, magtol_max, magtol_c, magtol_tx; /* doublet tolerance at the magnet */
+    float T_triplet, T_x, T_uv_scale, T_uv_min, T_ty, T_y, T_Q;
+    float C_n[4];               /* C(9), C(10), C(11), C(12) */
+} lfo_params;
+
+/* Outputs of lfo_find_tracks.  Per input track t (global index):
+ *   found[t], nhits[t], hit_idx[t*12 + layer] (packed hit index or -1),
+ *   state[t*6 + k] = (x, y, tx, ty, c, q/p) at z_ref, quality[t].
+ * Optional stage dumps (NULL to skip):
+ *   win_begin/win_count [t*12+l], win_xmin/xmax/centre [t*12+l],
+ *   n_trip[t], trip[(t*32 + r)*4 + {cfg,h0,h1,h2}], trip_chi2[t*32 + r],
+ *   cand_status[t*32 + r] (0 accepted, else the first failed requirement),
+ *   cand_q[t*32 + r], state64[t*6 + k] (binary64 refit of the selected hits). */
+typedef struct {
+    uint8_t* found; uint8_t* nhits; int32_t* hit_idx; float* state; float* quality;
+    int32_t* win_begin; int32_t* win_count; float* win_xmin; float* win_xmax; float* win_centre;
+    int32_t* n_trip; int32_t* trip; float* trip_chi2; int32_t* cand_status; float* cand_q;
+    double* state64;
+} lfo_output;
+
+#define LFO_MAX_TRIP 32
+
+/* Sort each event's raw hits into (zone, layer) buckets, ascending x inside a
+ * bucket, ties by raw index.  Returns 0, or -1 on a plane code >= 24. */
+int lfo_pack(int32_t n_events, const int32_t* raw_offsets,
+             const float* x, const float* z, const float* dxdy, const float* w, const uint8_t* plane,
+             int32_t* hit_offsets, float* ox, float* oz, float* odxdy, float* ow,
+             uint8_t* olayer, int32_t* perm);
+
+/* Run windows -> triplets -> extension -> fit/quality -> selection for every
+ * input track of events [0, n_events).  x64 (optional) gives binary64 hit
+ * coordinates for the state64 refit; NULL promotes the binary32 ones. */
+int lfo_find_tracks(const lfo_geometry* g, const lfo_params* p, int32_t n_events,
+                    const int32_t* hit_offsets, const float* x, const float* z,
+                    const float* dxdy, const float* w, const double* x64,
+                    const int32_t* trk_offsets, const float* sx, const float* sy,
+                    const float* stx, const float* sty, const float* sqop,
+                    lfo_output* out);
+
+/* Same, with the events split over n_threads POSIX threads (the per-event
+ * code is unchanged).  Used to time the oracle on all host cores. */
+int lfo_find_tracks_mt(const lfo_geometry* g, const lfo_params* p, int32_t n_events,
+                       const int32_t* hit_offsets, const float* x, const float* z,
+                       const float* dxdy, const float* w,
+                       const int32_t* trk_offsets, const float* sx, const float* sy,
+                       const float* stx, const float* sty, const float* sqop,
+                       lfo_output* out, int32_t n_threads);
+
+/* Stream compaction of found tracks: out_offsets[e] = number of found tracks
+ * in events before e; out_trk lists found track indices in event order.
+ * Returns the total. */
+int32_t lfo_compact(int32_t n_events, const int32_t* trk_offsets, const uint8_t* found,
+                    int32_t* out_offsets, int32_t* out_trk);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,454 @@
+"""Pins of the oracle to facts outside itself.
+
+Each ``pin_*`` takes an ``oracle.Oracle`` and raises AssertionError when the
+oracle disagrees with what the paper or the mathematics fixes.  The same
+functions run against the committed oracle (they must pass) and against
+copies with a planted mistake (at least one must fail).
+
+What pins what:
+  pack            numpy lexsort over (plane, x, raw index)           [library routine]
+  closed form     noise-free particles from the exact trajectory model are
+                  recovered with exactly their hits; the binary64 refit returns
+                  the generating parameters to 1e-5                   [closed form]
+  window edges    half widths x_tol = 150 + 2000/p, the 100 mm asymmetry side
+                  and the 800 mm stereo tolerance (Sec. Defining the search
+                  windows), hand-worked in tests/golden/window_examples.txt
+  window cap      32 hits kept symmetrically around the centre, clamped at the
+                  window ends
+  closest tie     equal distances pick the lower packed index
+  triplet chi2/K  chi2 of a hit placed at a known offset from the straight line;
+                  K multiplies the intercept (Sec. Triplet Seeding)
+  top-n           kept triplets are the smallest chi2 (prefix property)
+  bending filter  below 5 GeV the doublet must bend with the charge
+  magnet tol      doublets inside/outside the 8..40 mm tolerance
+  known-residual Q  Q of the paper's formula on residuals fixed by construction,
+                  for n_hits = 9..12 (Table C_nhits, nDoF_x, nDoF_y)
+  T_Q, T_ty       acceptance thresholds
+  invariants      unique hits, >= 9 hits, >= 1 stereo hit per station, Q < T_Q,
+                  hits inside windows, true hits inside pre-cap windows
+  binary32 fit    the binary32 fit agrees with the binary64 refit
+  compact         exclusive scan of per-event counts
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+import oracle
+from helpers import geo_dict, make_batch, raw_ids_in_windows, track_hits
+from paper_2402_14670_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _params(**kw):
+    p = oracle.default_params()
+    p.update(kw)
+    return p
+
+
+def _rel_close(a, b, rtol, atol):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.all(np.abs(a - b) <= atol + rtol * np.abs(b))
+
+
+# --------------------------------------------------------------------- pack
+
+def pin_pack_lexsort(orc):
+    b = synth.generate(1, n_events=4)
+    x = b.x.numpy().copy()
+    plane = b.plane.numpy()
+    ro = b.raw_offsets.numpy()
+    # plant exact duplicates and a negative zero inside buckets
+    for e in range(4):
+        s = ro[e]
+        x[s + 1] = x[s]
+        plane[s + 1] = plane[s]
+        x[s + 3] = -0.0
+        x[s + 4] = 0.0
+        plane[s + 4] = plane[s + 3]
+    pk = orc.pack(ro, x, b.z.numpy(), b.dxdy.numpy(), b.w.numpy(), plane)
+    for e in range(4):
+        idx = np.arange(ro[e], ro[e + 1])
+        order = np.lexsort((idx, x[idx].astype(np.float64), plane[idx]))
+        assert np.array_equal(pk["perm"][ro[e]:ro[e + 1]], idx[order]), "pack order"
+        cnt = np.bincount(plane[idx], minlength=24)
+        exp_off = ro[e] + np.concatenate([[0], np.cumsum(cnt)[:-1]])
+        assert np.array_equal(pk["hit_offsets"][24 * e:24 * e + 24], exp_off), "bucket offsets"
+    assert pk["hit_offsets"][-1] == ro[-1]
+    assert np.array_equal(pk["x"], x[pk["perm"]])
+    assert not np.any(np.signbit(pk["x"][pk["x"] == 0.0])), "negative zero kept"
+    assert np.array_equal(pk["layer"], plane[pk["perm"]] % 12)
+
+
+# --------------------------------------------------------------- closed form
+
+def closed_form_batch(polarity=1, n_tracks=60, seed=11):
+    geo = synth.Geometry(polarity=polarity)
+    cfg = synth.EventConfig("closed form", 1, seed, ("fixed", n_tracks), match_frac=1.0,
+                            extra=("none",), noise=("per_layer", 0), sigma=0.0, efficiency=1.0,
+                            qop_smear=0.0)
+    return geo, synth.generate(cfg, geometry=geo)
+
+
+def pin_closed_form(orc, polarity=1):
+    geo, b = closed_form_batch(polarity)
+    res = orc.run_batch(b, geometry=geo_dict(geo), use_x64=True)
+    perm = res["packed"]["perm"]
+    hit_mcp = b.hit_mcp.numpy()[perm]
+    layer = res["packed"]["layer"]
+    trk_mcp = b.trk_mcp.numpy()
+    mc = {k: v.numpy() for k, v in b.mcp.items()}
+    n_checked = 0
+    for t in range(b.n_tracks):
+        m = trk_mcp[t]
+        own = np.nonzero(hit_mcp == m)[0]
+        lay = set(layer[own].tolist())
+        uv_st = [any(l in lay for l in (4 * s + 1, 4 * s + 2)) for s in range(3)]
+        trip_ok = {0, 4, 8} <= lay or {3, 7, 11} <= lay
+        reco = len(own) >= 9 and all(uv_st) and trip_ok
+        if not reco:
+            continue
+        n_checked += 1
+        assert res["found"][t], "reconstructible track %d not found" % t
+        got = res["hit_idx"][t]
+        got = np.sort(got[got >= 0])
+        assert np.array_equal(got, np.sort(own)), "track %d hit set" % t
+        truth = synth.truth_params(mc["tx"][m], mc["ty"][m], mc["qop"][m], geo)
+        st64 = res["state64"][t]
+        # binary64 refit on binary64 hits: all five parameters and q/p to 1e-5
+        for k, (rt, at) in enumerate([(1e-5, 1e-6), (1e-5, 1e-6), (1e-5, 1e-9), (1e-5, 1e-9),
+                                      (1e-5, 1e-15), (1e-5, 1e-9)]):
+            assert _rel_close(st64[k], truth[k], rt, at), ("state64", t, k, st64[k], truth[k])
+        st = res["state"][t]
+        # binary32 path: 1e-5 relative with absolute floors; c to a few ulp of x
+        for k, (rt, at) in enumerate([(1e-5, 1e-3), (1e-5, 2e-2), (1e-5, 1e-6), (1e-5, 2e-5),
+                                      (0.0, 5e-9), (1e-5, 1e-6)]):
+            assert _rel_close(st[k], truth[k], rt, at), ("state", t, k, st[k], truth[k])
+    assert n_checked >= 20
+    # no noise: every found track is made of a single particle's hits (an input
+    # state whose own particle left the acceptance may pick up a neighbour)
+    for t in np.nonzero(res["found"])[0]:
+        h = res["hit_idx"][t]
+        assert len(set(hit_mcp[h[h >= 0]].tolist())) == 1
+
+
+def pin_closed_form_md(orc):
+    pin_closed_form(orc, polarity=-1)
+
+
+# ------------------------------------------------------------------- windows
+
+def _golden_windows():
+    rows = []
+    with open(os.path.join(GOLDEN, "window_examples.txt")) as f:
+        for ln in f:
+            ln = ln.strip()
+            if not ln or ln.startswith("#"):
+                continue
+            p, q, pol, xt, le, ri = ln.split()
+            rows.append((float(p), int(q), int(pol), float(xt), float(le), float(ri)))
+    return rows
+
+
+def pin_window_edges(orc):
+    tx, ty = 0.05, 0.1
+    for (p, q, pol, x_tol, left, right) in _golden_windows():
+        geo = synth.Geometry(polarity=pol)
+        qop = q / p
+        _, y, xm = synth.trajectory(tx, ty, qop, geo)
+        hits, expect = [], {}
+        for l in range(12):
+            if l % 4 in (0, 3):
+                lo, hi = xm[l] - (x_tol + left), xm[l] + (x_tol + right)
+            else:
+                lo, hi = xm[l] - 800.0, xm[l] + 800.0
+            probes = [(lo - 0.5, False), (lo + 0.5, True), (hi - 0.5, True), (hi + 0.5, False)]
+            expect[l] = []
+            for xv, inside in probes:
+                if inside:
+                    expect[l].append(len(hits))
+                hits.append((l, 1, float(xv)))
+        b = make_batch([dict(hits=hits, states=[synth.state_of(tx, ty, qop, geo)])], geo)
+        res = orc.run_batch(b, geometry=geo_dict(geo))
+        got = raw_ids_in_windows(res, 0)
+        for l in range(12):
+            assert got[l] == sorted(expect[l]), ("window", p, q, pol, l, got[l], expect[l])
+
+
+def pin_window_cap(orc):
+    tx, ty, qop = 0.05, 0.1, 1.0 / 20.0
+    _, y, xm = synth.trajectory(tx, ty, qop)
+    c0 = float(xm[0])
+    cases = [
+        ([c0 + (k - 24.5) * 2.0 for k in range(50)], list(range(9, 41))),   # symmetric
+        ([c0 + 1.0 + 2.0 * k for k in range(50)], list(range(0, 32))),     # all above the centre
+        ([c0 - 1.0 - 2.0 * k for k in range(50)], list(range(18, 50))),    # all below (ids in x order)
+        ([c0 + (k - 9.5) * 2.0 for k in range(50)], list(range(0, 32))),    # centre near the low edge
+    ]
+    for xs, exp_rank in cases:
+        order = np.argsort(np.asarray(xs), kind="stable")
+        hits = [(0, 1, x) for x in xs]
+        b = make_batch([dict(hits=hits, states=[synth.state_of(tx, ty, qop)])])
+        res = orc.run_batch(b)
+        got = raw_ids_in_windows(res, 0)[0]
+        exp = sorted(int(order[r]) for r in exp_rank)
+        assert got == exp, ("cap", got, exp)
+
+
+# ----------------------------------------------------------------- triplets
+
+def _vertical_track():
+    """p = 20 GeV, q = +1, MagUp, slope after the kick 0: x = 100 mm in the T stations."""
+    qop = 0.05
+    txs = -1.2 * qop
+    return (100.0 - txs * 2500.0, 270.0, txs, 0.1, qop)
+
+
+def pin_closest_tie(orc):
+    st = _vertical_track()
+    hits = [(0, 1, 100.0), (8, 1, 100.0), (4, 1, 100.5), (4, 1, 99.5)]
+    res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]))
+    perm = res["packed"]["perm"]
+    assert res["n_trip"][0] >= 1
+    cfg, h0, h1, h2 = res["trip"][0, 0]
+    assert cfg == 0 and perm[h1] == 3, ("closest tie", perm[h1])
+    assert abs(res["trip_chi2"][0, 0] - 0.25) < 1e-6
+
+
+def pin_triplet_chi2_K(orc):
+    st = _vertical_track()
+    for d, kept in ((1.5, True), (2.9, False)):
+        hits = [(0, 1, 100.0), (8, 1, 100.0), (4, 1, 100.0 + d)]
+        res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]))
+        assert (res["n_trip"][0] == 1) == kept, ("T_triplet", d)
+        if kept:
+            assert abs(res["trip_chi2"][0, 0] - d * d) < 1e-4
+    # sloped doublet: K multiplies the intercept at z = 0 of the h0-h2 line
+    qop = 0.05
+    txs = 0.1 - 1.2 * qop
+    st = (100.0 - txs * 2500.0, 270.0, txs, 0.1, qop)
+    g = synth.Geometry()
+    x0 = 100.0 + 0.1 * (g.z[0] - 5200.0)
+    x2 = 100.0 + 0.1 * (g.z[8] - 5200.0)
+    tx_d = (x2 - x0) / (g.z[8] - g.z[0])
+    K = oracle.default_params(paper_K=True)["K_first"]
+    x1_paper = g.z[4] * tx_d + (x0 - tx_d * g.z[0]) * K
+    x1_line = x0 + tx_d * (g.z[4] - g.z[0])
+    hits = [(0, 1, x0), (8, 1, x2), (4, 1, x1_paper)]
+    b = make_batch([dict(hits=hits, states=[st])])
+    rp = orc.run_batch(b, params=oracle.default_params(paper_K=True))
+    r1 = orc.run_batch(b)
+    assert rp["n_trip"][0] == 1 and rp["trip_chi2"][0, 0] < 1e-5, rp["trip_chi2"][0, 0]
+    assert r1["n_trip"][0] == 1
+    assert abs(r1["trip_chi2"][0, 0] - (x1_paper - x1_line) ** 2) < 2e-4 * max(1.0, (x1_paper - x1_line) ** 2)
+
+
+def _key(row, chi2):
+    cfg, h0, h1, h2 = row
+    return (float(chi2), int(cfg), int(h0), int(h2))
+
+
+def pin_top_n(orc):
+    b = synth.generate(1, n_events=6)
+    r12 = orc.run_batch(b, params=_params(n_triplets=12))
+    r32 = orc.run_batch(b, params=_params(n_triplets=32))
+    n_full = 0
+    for t in range(b.n_tracks):
+        n12, n32 = r12["n_trip"][t], r32["n_trip"][t]
+        assert n12 == min(12, n32)
+        k32 = [_key(r32["trip"][t, r], r32["trip_chi2"][t, r]) for r in range(n32)]
+        k12 = [_key(r12["trip"][t, r], r12["trip_chi2"][t, r]) for r in range(n12)]
+        assert k32 == sorted(k32), "triplets not ascending"
+        assert k12 == k32[:n12], "kept triplets are not the smallest"
+        n_full += n32 > 12
+    assert n_full > 10
+
+
+def pin_bending_filter(orc):
+    tx, ty, p = 0.05, 0.1, 4.0
+    hits = track_hits(tx, ty, 1.0 / p)
+    wide = dict(xtol_c=5000.0, uv_tol=5000.0)   # windows that hold the hits whatever the charge
+    for qop_in, p_bend, found in ((1.0 / p, 5.0, True), (-1.0 / p, 5.0, False), (-1.0 / p, 0.0, True)):
+        st = synth.state_of(tx, ty, qop_in)
+        res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]), params=_params(p_bend=p_bend, **wide))
+        assert bool(res["found"][0]) == found, ("bending filter", qop_in, p_bend)
+
+
+def pin_magnet_tolerance(orc):
+    # p = 20 GeV, slope 0.3 after the kick, x = 100 mm at the magnet centre
+    p, T0 = 20.0, 0.3
+    qop = 1.0 / p
+    txs = T0 - 1.2 * qop
+    st = (100.0 - txs * 2500.0, 270.0, txs, 0.1, qop)
+    g = synth.Geometry()
+    line = lambda z: 100.0 + T0 * (z - g.z_magnet)
+    dz = g.z[8] - g.z[0]
+    r = (g.z[0] - g.z_magnet) / dz          # x offset at the magnet per unit x2 offset
+    # decoy h2 shifted by s: |dx_mag| = r*s against tol = 8 + 96/p + 10*(T0 + s/dz)
+    s_star = (8.0 + 96.0 / p + 10.0 * T0) / (r - 10.0 / dz)
+    for s, inside in ((s_star - 0.05, True), (s_star + 0.05, False)):
+        x1 = line(g.z[4]) + s * (g.z[4] - g.z[0]) / dz
+        hits = [(0, 1, line(g.z[0])), (8, 1, line(g.z[8])), (4, 1, line(g.z[4])),
+                (8, 1, line(g.z[8]) + s), (4, 1, x1)]
+        res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]))
+        perm = res["packed"]["perm"]
+        h2s = {int(perm[res["trip"][0, k, 3]]) for k in range(res["n_trip"][0])}
+        assert 1 in h2s, "true doublet lost"
+        assert (3 in h2s) == inside, ("magnet tolerance", s, h2s)
+
+
+# ------------------------------------------------------------------- quality
+
+def _orth(v, cols):
+    q, _ = np.linalg.qr(cols)
+    return v - q @ (q.T @ v)
+
+
+def known_residual_event(drop_uv=(), ax=0.35, ay=4.0, tx=0.1, ty=0.08, p=10.0, dty_in=0.0):
+    """A track whose x hits are displaced orthogonally to the x model and whose
+    stereo hits are displaced orthogonally (in y) to the y line, so the fits
+    return the true parameters and every residual is known."""
+    geo = synth.Geometry()
+    qop = 1.0 / p
+    _, y, xm = synth.trajectory(tx, ty, qop, geo)
+    z = np.asarray(geo.z, np.float64)
+    u = (z - geo.z_ref) * 1e-3
+    f2 = u * u * (1.0 + geo.dratio * 1000.0 * u)
+    xl = [l for l in range(12) if l % 4 in (0, 3)]
+    uvl = [l for l in range(12) if l % 4 in (1, 2) and l not in drop_uv]
+    rng = np.random.default_rng(7)
+    dx = _orth(rng.standard_normal(len(xl)), np.stack([np.ones(len(xl)), u[xl], f2[xl]], 1))
+    dx *= ax / np.linalg.norm(dx)
+    dy = _orth(rng.standard_normal(len(uvl)), np.stack([np.ones(len(uvl)), u[uvl]], 1))
+    dy *= ay / np.linalg.norm(dy)
+    off = {l: dx[i] for i, l in enumerate(xl)}
+    dxdy = np.asarray(geo.dxdy, np.float64)
+    for i, l in enumerate(uvl):
+        off[l] = -dy[i] * dxdy[l]
+    hits = track_hits(tx, ty, qop, geo, layers=xl + uvl, offsets=off)
+    T_uv = max(2.0, 50.0 * (abs(tx) + abs(ty)))
+    n, n_uv = len(xl) + len(uvl), len(uvl)
+    Qx = np.sum(dx ** 2) / 2.0 + np.sum((dy * dxdy[uvl]) ** 2) / T_uv
+    Qy = np.sum(dy ** 2) / 800.0
+    C = {9: 5.0, 10: 1.0, 11: 0.8, 12: 0.5}[n]
+    Q = (Qx / (n - 3) + Qy / (n_uv - 2)) * C
+    xs, ys, txs, tys, qo = synth.state_of(tx, ty, qop, geo)
+    # an input t_y slightly off the truth moves the stereo search centre but
+    # not the fits, so Q is unchanged
+    return hits, (xs, ys, txs, tys + dty_in, qo), Q, n
+
+
+def pin_known_residual_Q(orc):
+    for drop, dty in (((), 0.0), ((1,), 0.0), ((1, 6), 0.0), ((1, 6, 9), 0.0), ((), 0.003)):
+        hits, st, Q, n = known_residual_event(drop, dty_in=dty)
+        res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]))
+        assert res["found"][0] and res["nhits"][0] == n, ("known residual", drop, res["nhits"][0])
+        assert abs(res["quality"][0] - Q) <= 5e-3 * Q, ("Q", drop, res["quality"][0], Q)
+
+
+def pin_T_Q(orc):
+    # nine hits (one stereo hit per station): Q = (Q_x/6 + Q_y/1) * 5; scale
+    # the y residuals so that Q lands just below and just above T_Q = 0.5
+    drop = (1, 6, 9)
+    _, _, q0, _ = known_residual_event(drop, ax=0.2, ay=0.0)
+    _, _, q1, _ = known_residual_event(drop, ax=0.2, ay=1.0)
+    for target, acc in ((0.47, True), (0.53, False)):
+        ay = np.sqrt((target - q0) / (q1 - q0))
+        hits, st, Q, n = known_residual_event(drop, ax=0.2, ay=ay)
+        assert abs(Q - target) < 1e-9
+        res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]))
+        assert bool(res["found"][0]) == acc, ("T_Q", Q)
+        status = res["cand_status"][0, :res["n_trip"][0]]
+        assert acc or np.any(status == 5), status
+
+
+def pin_ty_cut(orc):
+    tx, ty, p = 0.1, 0.1, 10.0
+    hits = track_hits(tx, ty, 1.0 / p)
+    for d, found in ((0.015, True), (-0.015, True), (0.025, False), (-0.025, False)):
+        xs, ys, txs, tys, qop = synth.state_of(tx, ty, 1.0 / p)
+        res = orc.run_batch(make_batch([dict(hits=hits, states=[(xs, ys, txs, tys + d, qop)])]),
+                            params=_params(T_uv_min=1e4))
+        assert bool(res["found"][0]) == found, ("T_ty", d)
+
+
+# ---------------------------------------------------------------- invariants
+
+def pin_invariants(orc):
+    b = synth.generate(1, n_events=25)
+    res = orc.run_batch(b)
+    layer = res["packed"]["layer"]
+    ho = res["packed"]["hit_offsets"]
+    to = b.trk_offsets.numpy()
+    ev_of = np.repeat(np.arange(b.n_events), np.diff(to))
+    nf = 0
+    for t in np.nonzero(res["found"])[0]:
+        nf += 1
+        h = res["hit_idx"][t]
+        used = h[h >= 0]
+        assert len(set(used.tolist())) == len(used)
+        assert res["nhits"][t] == len(used) >= 9
+        zone = 1 if b.sty[t] >= 0 else 0
+        for l in range(12):
+            if h[l] < 0:
+                continue
+            assert layer[h[l]] == l
+            bk = 24 * ev_of[t] + 12 * zone + l
+            assert ho[bk] <= h[l] < ho[bk + 1], "hit outside the track's zone bucket"
+            wb, wc = res["win_begin"][t, l], res["win_count"][t, l]
+            assert wb <= h[l] < wb + wc, "hit outside its window"
+        for s in range(3):
+            assert h[4 * s + 1] >= 0 or h[4 * s + 2] >= 0, "no stereo hit in a station"
+        assert all(h[l] >= 0 for l in (0, 4, 8)) or all(h[l] >= 0 for l in (3, 7, 11))
+        assert res["quality"][t] < 0.5
+        assert np.all(np.isfinite(res["state"][t]))
+        assert np.all(res["win_count"][t] <= 32)
+    assert nf > 500
+
+
+def pin_true_hits_in_window(orc):
+    b = synth.generate(1, n_events=10, qop_smear=0.0)
+    res = orc.run_batch(b)
+    perm = res["packed"]["perm"]
+    hit_mcp = b.hit_mcp.numpy()[perm]
+    layer = res["packed"]["layer"]
+    x = res["packed"]["x"]
+    trk_mcp = b.trk_mcp.numpy()
+    n = 0
+    for t in range(b.n_tracks):
+        m = trk_mcp[t]
+        if m < 0:
+            continue
+        for h in np.nonzero(hit_mcp == m)[0]:
+            l = layer[h]
+            assert res["win_xmin"][t, l] <= x[h] <= res["win_xmax"][t, l], ("true hit outside", t, l)
+            n += 1
+    assert n > 1000
+
+
+def pin_fit32_vs_fit64(orc):
+    b = synth.generate(1, n_events=10)
+    res = orc.run_batch(b)
+    f = res["found"].astype(bool)
+    st, s64 = res["state"][f].astype(np.float64), res["state64"][f]
+    tol = [(1e-6, 2e-3), (1e-5, 0.2), (1e-5, 2e-6), (1e-4, 5e-5), (0.0, 2e-8), (1e-5, 2e-6)]
+    for k, (rt, at) in enumerate(tol):
+        assert _rel_close(st[:, k], s64[:, k], rt, at), ("fit32 vs fit64", k, np.max(np.abs(st[:, k] - s64[:, k])))
+
+
+def pin_compact(orc):
+    b = synth.generate(1, n_events=8)
+    res = orc.run_batch(b)
+    to = b.trk_offsets.numpy()
+    found = res["found"].astype(np.int64)
+    cnt = np.array([found[to[e]:to[e + 1]].sum() for e in range(b.n_events)])
+    assert np.array_equal(res["out_offsets"], np.concatenate([[0], np.cumsum(cnt)]))
+    assert np.array_equal(res["out_trk"], np.nonzero(found)[0])
+
+
+ALL_PINS = [pin_pack_lexsort, pin_closed_form, pin_closed_form_md, pin_window_edges, pin_window_cap,
+            pin_closest_tie, pin_triplet_chi2_K, pin_top_n, pin_bending_filter,
+            pin_magnet_tolerance, pin_known_residual_Q, pin_T_Q, pin_ty_cut, pin_invariants,
+            pin_true_hits_in_window, pin_fit32_vs_fit64, pin_compact]

@@ -1,0 +1,85 @@
+"""Each pin must catch a plausible mistake planted in a copy of the oracle.
+
+Every case below edits one expression of ``oracle/lf_oracle.c`` in a
+temporary copy, compiles it, and runs the pins named beside it: at least one
+must fail.  This shows that the pins fix the oracle's arithmetic, not only
+that the oracle agrees with itself.  CPU only.
+"""
+import pytest
+
+import oracle
+import pins
+
+MUTANTS = [
+    ("x_tol uses p instead of 1/p",
+     "p->xtol_c + p->xtol_p / pmom", "p->xtol_c + p->xtol_p * pmom", ["pin_window_edges"]),
+    ("asymmetry on the wrong side",
+     "float a_left = ((qpos && mu) || (!qpos && !mu))", "float a_left = ((!qpos && mu) || (qpos && !mu))",
+     ["pin_window_edges"]),
+    ("stereo correction with the wrong sign",
+     "centre = (xn + tx_f * (g->z[l] - g->z[n])) - yl * g->dxdy[l];",
+     "centre = (xn + tx_f * (g->z[l] - g->z[n])) + yl * g->dxdy[l];", ["pin_window_edges"]),
+    ("window cap not symmetric", "start = c - cap / 2;", "start = c - cap / 4;", ["pin_window_cap"]),
+    ("window cap not clamped at the low end", "if (start < lo) start = lo;", "", ["pin_window_cap"]),
+    ("closest-hit tie to the higher index", "if (best < 0 || d < bd)", "if (best < 0 || d <= bd)",
+     ["pin_closest_tie"]),
+    ("K multiplies the whole extrapolation",
+     "float x1_exp = z1 * tx_d + (x0 - tx_d * z0) * K;",
+     "float x1_exp = (z1 * tx_d + (x0 - tx_d * z0)) * K;", ["pin_triplet_chi2_K"]),
+    ("T_triplet inclusive and doubled", "if (!(chi2 < p->T_triplet)) continue;",
+     "if (!(chi2 <= 2.0f * p->T_triplet)) continue;", ["pin_triplet_chi2_K"]),
+    ("keeps the largest chi2",
+     "if (p->chi2 < q->chi2) return -1;\n    if (p->chi2 > q->chi2) return 1;",
+     "if (p->chi2 < q->chi2) return 1;\n    if (p->chi2 > q->chi2) return -1;", ["pin_top_n"]),
+    ("bending filter inverted",
+     "int ok = (bend > 0.0f) ? (d > 0.0f) : (d < 0.0f);",
+     "int ok = (bend > 0.0f) ? (d < 0.0f) : (d > 0.0f);", ["pin_bending_filter", "pin_closed_form"]),
+    ("magnet tolerance without the slope term",
+     "float tol = tol_base + p->magtol_tx * fabsf(tx_d);", "float tol = tol_base;",
+     ["pin_magnet_tolerance"]),
+    ("extension searches the triplet layers",
+     "static const int CFG_MISSING[2][3] = {{3, 7, 11}, {0, 4, 8}};",
+     "static const int CFG_MISSING[2][3] = {{0, 4, 8}, {3, 7, 11}};", ["pin_closed_form"]),
+    ("C(n) table reversed", "* p->C_n[n - 9];", "* p->C_n[12 - n];", ["pin_known_residual_Q"]),
+    ("nDoF_x = n - 2", "(qx / (float)(n - 3)", "(qx / (float)(n - 2)", ["pin_known_residual_Q"]),
+    ("Q_y dropped", "qy = qy + (ry * ry) / p->T_y;", "qy = qy + 0.0f * ry;", ["pin_known_residual_Q"]),
+    ("stereo residual against the input y", "float r = hx[h] - (xf - yf * hdxdy[h]);",
+     "float r = hx[h] - (xf - (s->ys + s->tys * (hz[h] - g->z_state)) * hdxdy[h]);",
+     ["pin_known_residual_Q"]),
+    ("T_Q doubled", "if (!(Q < p->T_Q))", "if (!(Q < 2.0f * p->T_Q))", ["pin_T_Q"]),
+    ("t_y cut against the sum", "fabsf(ty_fit - s->tys) < p->T_ty", "fabsf(ty_fit + s->tys) < p->T_ty",
+     ["pin_ty_cut", "pin_closed_form"]),
+    ("y from the hit minus the model", "float y = (model_x(A, T, C, u, D) - hx[h]) / hdxdy[h];",
+     "float y = (hx[h] - model_x(A, T, C, u, D)) / hdxdy[h];", ["pin_closed_form", "pin_ty_cut"]),
+    ("binary64 model without dRatio", "double f[3] = {1.0, dz, dz * dz * (1.0 + dR * dz)};",
+     "double f[3] = {1.0, dz, dz * dz};", ["pin_closed_form"]),
+    ("q/p ignores the polarity", "cd->state[5] = (tx - s->txs) / ((float)g->polarity * g->kappa);",
+     "cd->state[5] = (tx - s->txs) / g->kappa;", ["pin_closed_form_md"]),
+    ("x refit skipped", "A = A + ((c00 * b0 + c01 * b1) + c02 * b2) / dt;", "A = A + 0.0f * dt;",
+     ["pin_fit32_vs_fit64"]),
+    ("stereo-hit-per-station requirement dropped",
+     "if (!st_uv[0] || !st_uv[1] || !st_uv[2]) { cd->status = CS_UV_STATION; return; }", "",
+     ["pin_invariants", "pin_known_residual_Q"]),
+    ("pack sorts x descending",
+     "if (p->x < q->x) return -1;\n    if (p->x > q->x) return 1;",
+     "if (p->x < q->x) return 1;\n    if (p->x > q->x) return -1;", ["pin_pack_lexsort"]),
+    ("pack keeps negative zero", "ox[o] = x[r] + 0.0f;", "ox[o] = x[r];", ["pin_pack_lexsort"]),
+    ("compaction skips the last track of an event",
+     "for (int32_t t = trk_offsets[e]; t < trk_offsets[e + 1]; ++t)\n            if (found[t])",
+     "for (int32_t t = trk_offsets[e]; t + 1 < trk_offsets[e + 1]; ++t)\n            if (found[t])",
+     ["pin_compact"]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pin_names", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(name, old, new, pin_names, tmp_path):
+    src = oracle.source()
+    assert src.count(old) == 1, "mutation anchor not found once: %r" % old
+    orc = oracle.variant(src.replace(old, new), str(tmp_path), "mutant")
+    caught = []
+    for pn in pin_names:
+        try:
+            getattr(pins, pn)(orc)
+        except AssertionError:
+            caught.append(pn)
+    assert caught, "no pin caught: %s" % name
