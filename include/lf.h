@@ -1,0 +1,199 @@
+/*
+ * lf.h — C ABI of the GB300 (sm_103a) forward-tracking library.
+ *
+ * The library follows upstream (VELO-UT) track states into the twelve
+ * x-u-v-x layers of the downstream tracker, as in "Looking Forward"
+ * (arXiv:2402.14670):
+ *   Sec. "Defining the search windows"            magnet extrapolation with a pT
+ *       kick, per-layer windows x_tol = xtol_c + xtol_p/p plus the magnet
+ *       asymmetry term, u/v windows around the stereo-corrected centre,
+ *       at most n_hits_window hits kept symmetrically around the centre;
+ *   Sec. "Triplet Seeding"                        doublets from the first/last
+ *       x layers of T1 and T3 with the bending and magnet-opening filters,
+ *       x1_expected with K, chi2_triplet < T_triplet, the n_triplets smallest;
+ *   Sec. "Extending triplets to other layers"     Eq. dratio_model_x_expected
+ *       around z_ref, T_x and T_uv acceptance;
+ *   Sec. "Quality Filter"                         y line fit, T_ty, Q_x, Q_y,
+ *       Q = (Q_x/nDoF_x + Q_y/nDoF_y) C(n_hits) (Table C_nhits), Q < T_Q,
+ *       best Q per input track;
+ *   Sec. "Calculation of momentum and track states" q/p from the slope change
+ *       in the linear kick form.
+ *
+ * Conventions
+ *   - Every pointer inside lf_raw_hits, lf_packed, lf_batch and lf_output is a
+ *     DEVICE pointer owned by the caller, unless a function says otherwise.
+ *     The library never frees caller memory.
+ *   - The context owns its scratch memory and the device copy of geometry
+ *     and parameters; scratch grows on demand and is freed by lf_destroy.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *     void*; NULL is the legacy default stream).  The returned status covers
+ *     argument checks and launch errors only.  Device-side conditions (a
+ *     bucket or window over capacity, a bounded wait that ran out) are
+ *     recorded in a status word that lf_sync_status reads.
+ *   - One context per stream at a time; different contexts are independent.
+ *   - Floating point: binary32, round to nearest, no contraction, in the
+ *     expression order of the method's definition, so results are
+ *     deterministic and independent of launch shape.
+ *   - Hit indices are indices into the packed (sorted) hit arrays; perm maps
+ *     them back to raw indices.
+ */
+#ifndef LF_H
+#define LF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LF_N_LAYERS 12
+#define LF_N_BUCKETS 24          /* (zone, layer) buckets per event: zone*12 + layer */
+#define LF_MAX_WINDOW 64         /* largest n_hits_window */
+#define LF_MAX_TRIPLETS 32       /* largest n_triplets */
+#define LF_MAX_BUCKET 8192       /* largest number of hits in one (event, zone, layer) bucket */
+
+typedef enum {
+    LF_OK = 0,
+    LF_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, bad parameter) */
+    LF_ERR_CUDA = 2,       /* a CUDA call failed; lf_last_error has the message */
+    LF_ERR_OOM = 3,        /* scratch allocation failed */
+    LF_ERR_CAPACITY = 4,   /* device status: a bucket above LF_MAX_BUCKET hits */
+    LF_ERR_TIMEOUT = 5,    /* device status: a bounded wait ran out */
+    LF_ERR_INTERNAL = 6
+} lf_status;
+
+/* device status word bits, read by lf_sync_status */
+#define LF_FLAG_BUCKET_OVERFLOW 0x1
+#define LF_FLAG_PLANE_RANGE     0x2
+#define LF_FLAG_TIMEOUT         0x4
+
+typedef struct lf_ctx lf_ctx;
+
+/* Detector and field constants (Sec. "Context", Sec. "Propagation of tracks
+ * in LHCb's magnetic field").  Layers are ordered x,u,v,x per station. */
+typedef struct {
+    float z[LF_N_LAYERS];      /* layer z, mm */
+    float dxdy[LF_N_LAYERS];   /* stereo slope: 0 for x layers, +-tan(5 deg) for u/v */
+    float z_state;             /* z of the input states */
+    float z_magnet;            /* pT-kick plane */
+    float z_ref;               /* reference plane of the T-station model */
+    float kappa;               /* slope kick per unit q/p */
+    float gamma;               /* curvature per unit q/p */
+    float dratio;              /* dRatio of Eq. trackfitmodel */
+    int32_t polarity;          /* +1 MagUp, -1 MagDown */
+} lf_geometry;
+
+/* Tunable parameters (Table tolerances, Table C_nhits). */
+typedef struct {
+    float xtol_c, xtol_p;      /* x_tol = xtol_c + xtol_p / p */
+    float x_asym;              /* magnet asymmetry term */
+    float uv_tol;              /* u/v window half width */
+    int32_t n_hits_window;     /* 1..64 */
+    int32_t n_triplets;        /* 0..32 */
+    int32_t min_hits;          /* 9..12 */
+    float K_first, K_last;     /* correction factor of x1_expected */
+    float p_bend;              /* the bending-sign filter applies below this p */
+    float magtol_min, magtol_max, magtol_c, magtol_tx; /* clamp(min + c/p + tx*|t_x|, min, max) */
+    float T_triplet, T_x, T_uv_scale, T_uv_min, T_ty, T_y, T_Q;
+    float C_n[4];              /* C(9), C(10), C(11), C(12) */
+} lf_params;
+
+/* Raw hits of n_events events, unsorted inside each event (device). */
+typedef struct {
+    int32_t n_events;
+    int32_t n_hits;            /* == raw_offsets[n_events] */
+    const int32_t* raw_offsets;/* [n_events+1] */
+    const float* x;            /* measured coordinate */
+    const float* z;
+    const float* dxdy;
+    const float* w;            /* weight */
+    const uint8_t* plane;      /* zone*12 + layer, zone 1 = upper half */
+} lf_raw_hits;
+
+/* Packed hits written by lf_pack_hits (caller-allocated device arrays). */
+typedef struct {
+    int32_t* hit_offsets;      /* [24*n_events+1] bucket starts */
+    float* x; float* z; float* dxdy; float* w;   /* [n_hits] */
+    uint8_t* layer;            /* [n_hits] */
+    int32_t* perm;             /* [n_hits] packed index -> raw index */
+} lf_packed;
+
+/* Input of the track finding: packed hits plus input states (device). */
+typedef struct {
+    int32_t n_events;
+    int32_t n_hits;
+    int32_t n_tracks;          /* == trk_offsets[n_events] */
+    const int32_t* hit_offsets;/* [24*n_events+1], x ascending inside each bucket */
+    const float* x; const float* z; const float* dxdy; const float* w;
+    const int32_t* trk_offsets;/* [n_events+1] */
+    const float* sx; const float* sy; const float* stx; const float* sty; const float* sqop;
+} lf_batch;
+
+/* Output per input track t (device, caller-allocated).
+ *   found[t] 0/1; nhits[t];
+ *   hit_idx[t*12 + layer]: packed hit index or -1; state[t*6 + k]:
+ *   (x, y, tx, ty, c, q/p) at z_ref; quality[t] = Q.
+ *   hit_idx, state and quality are written only where found[t] == 1.
+ * Compaction: out_offsets[n_events+1] (found tracks before each event),
+ *   out_trk[n_tracks] (indices of found tracks, event order), n_out[1]. */
+typedef struct {
+    uint8_t* found; uint8_t* nhits; int32_t* hit_idx; float* state; float* quality;
+    int32_t* out_offsets; int32_t* out_trk; int32_t* n_out;
+} lf_output;
+
+/* Launch shape of the persistent form (filled by the autotuner or the user;
+ * zeros select the defaults). */
+typedef struct {
+    int32_t warps_per_block;   /* 1..16 */
+    int32_t blocks_per_sm;     /* resident blocks per SM of the persistent grid */
+    int32_t grain;             /* input tracks taken from the work queue at a time */
+    int32_t reserved;
+} lf_tuning;
+
+/* Create a context: validates and copies geometry and parameters.
+ * Returns LF_ERR_ARG on a parameter outside its range. */
+lf_status lf_create(const lf_geometry* geometry, const lf_params* params, lf_ctx** out);
+
+/* Release the context and its scratch (synchronises the device). */
+void lf_destroy(lf_ctx* ctx);
+
+/* Message of the last error on this context ("" if none). */
+const char* lf_last_error(const lf_ctx* ctx);
+
+/* Number of SMs of the current device (for launch sizing). */
+int32_t lf_device_sm_count(void);
+
+/* Bucket and sort raw hits: per event, buckets ordered zone*12+layer, x
+ * ascending inside a bucket, ties by raw index; -0.0 becomes +0.0.  Output
+ * arrays hold raw->n_hits entries and hit_offsets 24*n_events+1.  A plane
+ * code >= 24 or a bucket above LF_MAX_BUCKET hits sets a status flag. */
+lf_status lf_pack_hits(lf_ctx* ctx, const lf_raw_hits* raw, const lf_packed* packed, void* stream);
+
+/* Plain form: one launch per stage (windows, triplets, extension+fit,
+ * selection, compaction) over the whole batch, intermediate results in
+ * context scratch. */
+lf_status lf_find_tracks(lf_ctx* ctx, const lf_batch* batch, const lf_output* out, void* stream);
+
+/* Persistent form: one fused kernel over a device work queue of input-track
+ * grains, then compaction; launched through a CUDA graph captured per
+ * launch shape.  tuning may be NULL (defaults).  Results are identical to
+ * lf_find_tracks. */
+lf_status lf_find_tracks_batched(lf_ctx* ctx, const lf_batch* batch, const lf_output* out,
+                                 const lf_tuning* tuning, void* stream);
+
+/* Stage dumps of the plain form for debugging and parity tests:
+ * win_begin/win_count [n_tracks*12] (int32), n_trip [n_tracks] (int32),
+ * trip [n_tracks*n_triplets*4] (int32 cfg, h0, h1, h2; packed indices),
+ * trip_chi2 [n_tracks*n_triplets] (float).  Device pointers. */
+lf_status lf_debug_stages(lf_ctx* ctx, const lf_batch* batch, int32_t* win_begin, int32_t* win_count,
+                          int32_t* n_trip, int32_t* trip, float* trip_chi2, void* stream);
+
+/* Synchronise the stream, read and clear the device status word.
+ * Returns LF_OK, LF_ERR_CAPACITY or LF_ERR_TIMEOUT; *flags gets the bits. */
+lf_status lf_sync_status(lf_ctx* ctx, void* stream, int32_t* flags);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LF_H */

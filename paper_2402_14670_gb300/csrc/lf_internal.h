@@ -1,0 +1,102 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace lfk {
+
+constexpr int NL = 12;
+constexpr int NB = 24;
+constexpr int MAX_CAP = 64;     // largest n_hits_window
+constexpr int MAX_NT = 32;      // largest n_triplets
+constexpr int WARP_SORT_MAX = 768;   // buckets up to this size are sorted by one warp
+constexpr int BLOCK_SORT_MAX = 8192; // larger buckets by one block (LF_MAX_BUCKET)
+constexpr int BLOCK_SORT_THREADS = 512;
+
+// Geometry, parameters and the few products both the method and the oracle
+// form once per call (polarity*kappa, polarity*gamma, 1000*dRatio).
+struct KParams {
+    float z[NL], dxdy[NL];
+    float z_state, z_magnet, z_ref, kappa, gamma, dratio;
+    int polarity;
+    float xtol_c, xtol_p, x_asym, uv_tol;
+    int cap, n_trip, min_hits;
+    float K_first, K_last, p_bend, magtol_min, magtol_max, magtol_c, magtol_tx;
+    float T_triplet, T_x, T_uv_scale, T_uv_min, T_ty, T_y, T_Q;
+    float C_n[4];
+    float pol_f;  // (float)polarity
+    float pk;     // pol_f * kappa
+    float pg;     // pol_f * gamma
+    float D;      // dratio * 1000 (model in u = dz/1000)
+};
+
+struct KBatch {
+    int n_events, n_hits, n_tracks;
+    const int* hit_offsets;
+    const float *x, *z, *dxdy, *w;
+    const int* trk_offsets;
+    const float *sx, *sy, *stx, *sty, *sqop;
+};
+
+struct KOut {
+    uint8_t* found;
+    uint8_t* nhits;
+    int* hit_idx;
+    float* state;
+    float* quality;
+};
+
+// One candidate of the plain form's extension stage (48 bytes).
+struct CandRec {
+    float Q;
+    int8_t status;   // 0 accepted
+    int8_t n;
+    int8_t hl[NL];   // window-local hit index per layer, -1 none
+    int8_t pad[6];
+    float st[6];
+};
+static_assert(sizeof(CandRec) == 48, "CandRec layout");
+
+// Per-warp shared-memory block: window descriptors, the flattened doublet
+// enumeration, then the staged window hits (x, z, dxdy, w), 12 x cap each.
+struct WarpHead {
+    int wbeg[NL];
+    int wcnt[NL];
+    int zuni[NL];
+    int pre[2 * MAX_CAP];   // exclusive prefix of the h2-interval sizes, per (cfg, h0) item
+    int aa[2 * MAX_CAP];    // first h2 of each item's interval
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+__host__ __device__ inline size_t warp_smem_bytes(int cap) {
+    return align16(sizeof(WarpHead)) + size_t(4) * NL * cap * sizeof(float);
+}
+
+// ---- launchers (defined in the .cu files) ----
+cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, const float* dxdy,
+                        const float* w, const uint8_t* plane, int n_events, int n_hits,
+                        int* hit_offsets, float* ox, float* oz, float* odxdy, float* ow, uint8_t* olayer,
+                        int* perm, int* tmp, int* big_list, int* status, int n_sm, cudaStream_t s);
+
+cudaError_t launch_track_event(const KBatch& b, int* trk_event, cudaStream_t s);
+cudaError_t launch_windows(const KParams& k, const KBatch& b, const int* trk_event, int* wbeg, uint8_t* wcnt,
+                           cudaStream_t s);
+cudaError_t launch_triplets(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
+                            const uint8_t* wcnt, uint64_t* keys, uint8_t* ntrip, cudaStream_t s);
+cudaError_t launch_extend(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
+                          const uint8_t* wcnt, const uint64_t* keys, const uint8_t* ntrip, CandRec* cands,
+                          cudaStream_t s);
+cudaError_t launch_select(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* ntrip,
+                          const CandRec* cands, const KOut& o, cudaStream_t s);
+cudaError_t launch_fused(const KParams& k, const KBatch& b, const KOut& o, int* cursor, int grain,
+                         int warps_per_block, int n_blocks, cudaStream_t s);
+cudaError_t fused_max_blocks_per_sm(const KParams& k, int warps_per_block, int* out);
+cudaError_t launch_compact(const int* trk_offsets, const uint8_t* found, int n_events, int* ev_count,
+                           int* out_offsets, int* out_trk, int* n_out, cudaStream_t s);
+cudaError_t launch_debug_triplets(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* wcnt,
+                                  const uint64_t* keys, const uint8_t* ntrip, int* win_count_out, int* n_trip_out,
+                                  int* trip_out, float* chi2_out, cudaStream_t s);
+
+}  // namespace lfk

@@ -1,0 +1,327 @@
+"""Python binding of the C ABI in include/lf.h (argument marshalling only).
+
+The functions keep the C names (lf_create, lf_pack_hits, lf_find_tracks,
+lf_find_tracks_batched, lf_debug_stages, lf_sync_status, lf_destroy); every
+step of the path runs in the CUDA library.  ``Tracker`` wraps them for torch
+tensors: it allocates outputs with torch and passes raw device pointers and
+the current CUDA stream.
+
+Importing this module loads ``liblf.so``; it raises if the library has not
+been built (there is no fallback of any kind).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblf.so")
+NL = 12
+NB = 24
+
+LF_OK, LF_ERR_ARG, LF_ERR_CUDA, LF_ERR_OOM, LF_ERR_CAPACITY, LF_ERR_TIMEOUT, LF_ERR_INTERNAL = range(7)
+_STATUS = {0: "LF_OK", 1: "LF_ERR_ARG", 2: "LF_ERR_CUDA", 3: "LF_ERR_OOM", 4: "LF_ERR_CAPACITY",
+           5: "LF_ERR_TIMEOUT", 6: "LF_ERR_INTERNAL"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("liblf.so is not built: run paper_2402_14670_gb300.build.build() "
+                      "(the CUDA library is required; there is no CPU path)")
+_lib = C.CDLL(LIB_PATH)
+
+_P = C.c_void_p
+
+
+class lf_geometry(C.Structure):
+    _fields_ = [("z", C.c_float * NL), ("dxdy", C.c_float * NL), ("z_state", C.c_float),
+                ("z_magnet", C.c_float), ("z_ref", C.c_float), ("kappa", C.c_float), ("gamma", C.c_float),
+                ("dratio", C.c_float), ("polarity", C.c_int32)]
+
+
+class lf_params(C.Structure):
+    _fields_ = [("xtol_c", C.c_float), ("xtol_p", C.c_float), ("x_asym", C.c_float), ("uv_tol", C.c_float),
+                ("n_hits_window", C.c_int32), ("n_triplets", C.c_int32), ("min_hits", C.c_int32),
+                ("K_first", C.c_float), ("K_last", C.c_float), ("p_bend", C.c_float),
+                ("magtol_min", C.c_float), ("magtol_max", C.c_float), ("magtol_c", C.c_float),
+                ("magtol_tx", C.c_float), ("T_triplet", C.c_float), ("T_x", C.c_float),
+                ("T_uv_scale", C.c_float), ("T_uv_min", C.c_float), ("T_ty", C.c_float), ("T_y", C.c_float),
+                ("T_Q", C.c_float), ("C_n", C.c_float * 4)]
+
+
+class lf_raw_hits(C.Structure):
+    _fields_ = [("n_events", C.c_int32), ("n_hits", C.c_int32), ("raw_offsets", _P), ("x", _P), ("z", _P),
+                ("dxdy", _P), ("w", _P), ("plane", _P)]
+
+
+class lf_packed(C.Structure):
+    _fields_ = [("hit_offsets", _P), ("x", _P), ("z", _P), ("dxdy", _P), ("w", _P), ("layer", _P), ("perm", _P)]
+
+
+class lf_batch(C.Structure):
+    _fields_ = [("n_events", C.c_int32), ("n_hits", C.c_int32), ("n_tracks", C.c_int32), ("hit_offsets", _P),
+                ("x", _P), ("z", _P), ("dxdy", _P), ("w", _P), ("trk_offsets", _P), ("sx", _P), ("sy", _P),
+                ("stx", _P), ("sty", _P), ("sqop", _P)]
+
+
+class lf_output(C.Structure):
+    _fields_ = [("found", _P), ("nhits", _P), ("hit_idx", _P), ("state", _P), ("quality", _P),
+                ("out_offsets", _P), ("out_trk", _P), ("n_out", _P)]
+
+
+class lf_tuning(C.Structure):
+    _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("grain", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+_lib.lf_create.argtypes = [C.POINTER(lf_geometry), C.POINTER(lf_params), C.POINTER(_P)]
+_lib.lf_create.restype = C.c_int
+_lib.lf_destroy.argtypes = [_P]
+_lib.lf_destroy.restype = None
+_lib.lf_last_error.argtypes = [_P]
+_lib.lf_last_error.restype = C.c_char_p
+_lib.lf_device_sm_count.argtypes = []
+_lib.lf_device_sm_count.restype = C.c_int32
+_lib.lf_pack_hits.argtypes = [_P, C.POINTER(lf_raw_hits), C.POINTER(lf_packed), _P]
+_lib.lf_pack_hits.restype = C.c_int
+_lib.lf_find_tracks.argtypes = [_P, C.POINTER(lf_batch), C.POINTER(lf_output), _P]
+_lib.lf_find_tracks.restype = C.c_int
+_lib.lf_find_tracks_batched.argtypes = [_P, C.POINTER(lf_batch), C.POINTER(lf_output), C.POINTER(lf_tuning), _P]
+_lib.lf_find_tracks_batched.restype = C.c_int
+_lib.lf_debug_stages.argtypes = [_P, C.POINTER(lf_batch), _P, _P, _P, _P, _P, _P]
+_lib.lf_debug_stages.restype = C.c_int
+_lib.lf_sync_status.argtypes = [_P, _P, C.POINTER(C.c_int32)]
+_lib.lf_sync_status.restype = C.c_int
+
+EXPORTED = ["lf_create", "lf_destroy", "lf_last_error", "lf_device_sm_count", "lf_pack_hits", "lf_find_tracks",
+            "lf_find_tracks_batched", "lf_debug_stages", "lf_sync_status"]
+
+
+class LFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+# ------------------------------------------------------------- defaults
+
+def default_geometry() -> dict:
+    """Synthetic detector: three x-u-v-x stations, stereo +-tan(5 deg),
+    kick plane at 5200 mm, reference plane at 8520 mm (Sec. "Extending
+    triplets to other layers")."""
+    t = float(np.float32(math.tan(math.radians(5.0))))
+    kinds = ("x", "u", "v", "x") * 3
+    return dict(z=[7826.0, 7896.0, 7966.0, 8036.0, 8508.0, 8578.0, 8648.0, 8718.0,
+                   9193.0, 9263.0, 9333.0, 9403.0],
+                dxdy=[0.0 if k == "x" else (t if k == "u" else -t) for k in kinds],
+                z_state=2700.0, z_magnet=5200.0, z_ref=8520.0, kappa=1.2, gamma=2.4e-9, dratio=4e-4,
+                polarity=1)
+
+
+def default_params(paper_K: bool = False) -> dict:
+    """'Forward' column of Table tolerances and Table C_nhits.  K_x1 = 1
+    unless paper_K (the synthetic detector has no field in the T stations);
+    the magnet tolerance clamp(8 + 96/p + 10|t_x|, 8, 40) mm and
+    T_uv = max(2, 50 (|t_x| + |t_y|)) are the readings of what the paper
+    leaves open."""
+    return dict(xtol_c=150.0, xtol_p=2000.0, x_asym=100.0, uv_tol=800.0, n_hits_window=32, n_triplets=12,
+                min_hits=9, K_first=1.00177513 if paper_K else 1.0, K_last=1.00142634 if paper_K else 1.0,
+                p_bend=5.0, magtol_min=8.0, magtol_max=40.0, magtol_c=96.0, magtol_tx=10.0, T_triplet=8.0,
+                T_x=2.0, T_uv_scale=50.0, T_uv_min=2.0, T_ty=0.02, T_y=800.0, T_Q=0.5,
+                C_n=[5.0, 1.0, 0.8, 0.5])
+
+
+def _geometry(g: dict) -> lf_geometry:
+    s = lf_geometry()
+    s.z[:] = [float(v) for v in g["z"]]
+    s.dxdy[:] = [float(v) for v in g["dxdy"]]
+    for k in ("z_state", "z_magnet", "z_ref", "kappa", "gamma", "dratio"):
+        setattr(s, k, float(g[k]))
+    s.polarity = int(g["polarity"])
+    return s
+
+
+def _params(p: dict) -> lf_params:
+    s = lf_params()
+    for name, _ in lf_params._fields_:
+        if name == "C_n":
+            s.C_n[:] = [float(v) for v in p["C_n"]]
+        else:
+            setattr(s, name, p[name])
+    return s
+
+
+# ------------------------------------------------------------- C names
+
+def _check(ctx, st):
+    if st != LF_OK:
+        msg = _lib.lf_last_error(ctx).decode() if ctx else ""
+        raise LFError(st, msg)
+
+
+def lf_create(geometry: Optional[dict] = None, params: Optional[dict] = None):
+    g = _geometry(geometry or default_geometry())
+    p = _params(params or default_params())
+    h = _P()
+    st = _lib.lf_create(C.byref(g), C.byref(p), C.byref(h))
+    if st != LF_OK:
+        raise LFError(st, "lf_create rejected the geometry or parameters")
+    return h
+
+
+def lf_destroy(ctx) -> None:
+    _lib.lf_destroy(ctx)
+
+
+def lf_last_error(ctx) -> str:
+    return _lib.lf_last_error(ctx).decode()
+
+
+def lf_device_sm_count() -> int:
+    return int(_lib.lf_device_sm_count())
+
+
+def lf_pack_hits(ctx, raw: lf_raw_hits, packed: lf_packed, stream) -> None:
+    _check(ctx, _lib.lf_pack_hits(ctx, C.byref(raw), C.byref(packed), stream))
+
+
+def lf_find_tracks(ctx, batch: lf_batch, out: lf_output, stream) -> None:
+    _check(ctx, _lib.lf_find_tracks(ctx, C.byref(batch), C.byref(out), stream))
+
+
+def lf_find_tracks_batched(ctx, batch: lf_batch, out: lf_output, tuning: Optional[lf_tuning], stream) -> None:
+    tp = C.byref(tuning) if tuning is not None else None
+    _check(ctx, _lib.lf_find_tracks_batched(ctx, C.byref(batch), C.byref(out), tp, stream))
+
+
+def lf_debug_stages(ctx, batch: lf_batch, win_begin, win_count, n_trip, trip, trip_chi2, stream) -> None:
+    _check(ctx, _lib.lf_debug_stages(ctx, C.byref(batch), win_begin, win_count, n_trip, trip, trip_chi2, stream))
+
+
+def lf_sync_status(ctx, stream) -> int:
+    f = C.c_int32(0)
+    _check(ctx, _lib.lf_sync_status(ctx, stream, C.byref(f)))
+    return int(f.value)
+
+
+# ------------------------------------------------------------- torch layer
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return _P(t.data_ptr()) if t.numel() else _P(t.data_ptr() or 0)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _P(s.cuda_stream)
+
+
+class Tracker:
+    """A library context plus torch-allocated inputs and outputs."""
+
+    def __init__(self, geometry: Optional[dict] = None, params: Optional[dict] = None):
+        self.geometry = dict(geometry or default_geometry())
+        self.params = dict(params or default_params())
+        self.ctx = lf_create(self.geometry, self.params)
+
+    def close(self):
+        if self.ctx:
+            lf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # raw -> packed
+    def pack(self, raw, stream=None, out: Optional[dict] = None) -> dict:
+        n_ev, n_h = int(raw.n_events), int(raw.x.numel())
+        dev = raw.x.device
+        if out is None:
+            out = dict(hit_offsets=torch.empty(NB * n_ev + 1, dtype=torch.int32, device=dev),
+                       x=torch.empty(n_h, dtype=torch.float32, device=dev),
+                       z=torch.empty(n_h, dtype=torch.float32, device=dev),
+                       dxdy=torch.empty(n_h, dtype=torch.float32, device=dev),
+                       w=torch.empty(n_h, dtype=torch.float32, device=dev),
+                       layer=torch.empty(n_h, dtype=torch.uint8, device=dev),
+                       perm=torch.empty(n_h, dtype=torch.int32, device=dev))
+        r = lf_raw_hits(n_ev, n_h, _ptr(raw.raw_offsets), _ptr(raw.x), _ptr(raw.z), _ptr(raw.dxdy), _ptr(raw.w),
+                        _ptr(raw.plane))
+        p = lf_packed(_ptr(out["hit_offsets"]), _ptr(out["x"]), _ptr(out["z"]), _ptr(out["dxdy"]), _ptr(out["w"]),
+                      _ptr(out["layer"]), _ptr(out["perm"]))
+        lf_pack_hits(self.ctx, r, p, _stream(stream))
+        return out
+
+    @staticmethod
+    def batch_struct(packed: dict, states, n_events: int) -> lf_batch:
+        return lf_batch(int(n_events), int(packed["x"].numel()), int(states.sx.numel()), _ptr(packed["hit_offsets"]),
+                        _ptr(packed["x"]), _ptr(packed["z"]), _ptr(packed["dxdy"]), _ptr(packed["w"]),
+                        _ptr(states.trk_offsets), _ptr(states.sx), _ptr(states.sy), _ptr(states.stx),
+                        _ptr(states.sty), _ptr(states.sqop))
+
+    @staticmethod
+    def alloc_output(n_tracks: int, n_events: int, device) -> dict:
+        return dict(found=torch.empty(n_tracks, dtype=torch.uint8, device=device),
+                    nhits=torch.empty(n_tracks, dtype=torch.uint8, device=device),
+                    hit_idx=torch.empty((n_tracks, NL), dtype=torch.int32, device=device),
+                    state=torch.empty((n_tracks, 6), dtype=torch.float32, device=device),
+                    quality=torch.empty(n_tracks, dtype=torch.float32, device=device),
+                    out_offsets=torch.empty(n_events + 1, dtype=torch.int32, device=device),
+                    out_trk=torch.empty(max(n_tracks, 1), dtype=torch.int32, device=device),
+                    n_out=torch.empty(1, dtype=torch.int32, device=device))
+
+    @staticmethod
+    def output_struct(o: dict) -> lf_output:
+        return lf_output(_ptr(o["found"]), _ptr(o["nhits"]), _ptr(o["hit_idx"]), _ptr(o["state"]),
+                         _ptr(o["quality"]), _ptr(o["out_offsets"]), _ptr(o["out_trk"]), _ptr(o["n_out"]))
+
+    def find(self, packed: dict, states, n_events: int, mode: str = "batched", tuning: Optional[dict] = None,
+             stream=None, out: Optional[dict] = None) -> dict:
+        b = self.batch_struct(packed, states, n_events)
+        if out is None:
+            out = self.alloc_output(int(states.sx.numel()), int(n_events), packed["x"].device)
+        o = self.output_struct(out)
+        if mode == "plain":
+            lf_find_tracks(self.ctx, b, o, _stream(stream))
+        elif mode == "batched":
+            tu = None
+            if tuning:
+                tu = lf_tuning(int(tuning.get("warps_per_block", 0)), int(tuning.get("blocks_per_sm", 0)),
+                               int(tuning.get("grain", 0)), 0)
+            lf_find_tracks_batched(self.ctx, b, o, tu, _stream(stream))
+        else:
+            raise ValueError(mode)
+        return out
+
+    def debug_stages(self, packed: dict, states, n_events: int, stream=None) -> dict:
+        n_t = int(states.sx.numel())
+        nt = max(int(self.params["n_triplets"]), 1)
+        dev = packed["x"].device
+        d = dict(win_begin=torch.empty((n_t, NL), dtype=torch.int32, device=dev),
+                 win_count=torch.empty((n_t, NL), dtype=torch.int32, device=dev),
+                 n_trip=torch.empty(n_t, dtype=torch.int32, device=dev),
+                 trip=torch.full((n_t, nt, 4), -1, dtype=torch.int32, device=dev),
+                 trip_chi2=torch.zeros((n_t, nt), dtype=torch.float32, device=dev))
+        b = self.batch_struct(packed, states, n_events)
+        lf_debug_stages(self.ctx, b, _ptr(d["win_begin"]), _ptr(d["win_count"]), _ptr(d["n_trip"]),
+                        _ptr(d["trip"]), _ptr(d["trip_chi2"]), _stream(stream))
+        return d
+
+    def status(self, stream=None) -> int:
+        return lf_sync_status(self.ctx, _stream(stream))
+
+    def run(self, raw, mode: str = "batched", tuning: Optional[dict] = None, stream=None):
+        """pack + find for a batch whose tensors live on the GPU."""
+        packed = self.pack(raw, stream)
+        out = self.find(packed, raw, raw.n_events, mode, tuning, stream)
+        return packed, out

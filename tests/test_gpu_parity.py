@@ -1,0 +1,193 @@
+"""CUDA library against the oracle, element by element, on the same inputs.
+
+Both forms (plain: one kernel per stage; batched: persistent fused kernel)
+must give the oracle's packed hits bit for bit, the same windows and triplet
+lists, the same selected hit lists for every input track and the same states
+and Q (compared bit for bit, within 1e-4 relative at worst).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import geo_dict, make_batch
+from parity import compare_outputs, compare_pack, run_both, to_np
+from paper_2402_14670_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lfm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_14670_gb300 import build
+    build.build()
+    from paper_2402_14670_gb300 import lf
+    return lf
+
+
+def _tracker(lfm, geometry=None, params=None):
+    return lfm.Tracker(geometry, params)
+
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_tiny_event(lfm, mode):
+    b = synth.generate(0).to("cuda")
+    tr = _tracker(lfm)
+    info, *_ = run_both(tr, b, mode=mode, stages=True)
+    assert info["n_found"] >= 10
+
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_minimum_bias_subset(lfm, mode):
+    b = synth.generate(1, n_events=300).to("cuda")
+    tr = _tracker(lfm)
+    info, *_ = run_both(tr, b, mode=mode, stages=(mode == "plain"))
+    assert info["n_found"] > 8000
+
+
+def test_high_occupancy_subset(lfm):
+    # ~25k hits per event: most buckets exceed one warp's sort and take the block path
+    b = synth.generate(4, n_events=30).to("cuda")
+    tr = _tracker(lfm)
+    info, *_ = run_both(tr, b, mode="batched", stages=True)
+    assert info["n_found"] > 1000
+
+
+def test_uneven_subset(lfm):
+    b = synth.generate(2, n_events=200).to("cuda")
+    tr = _tracker(lfm)
+    run_both(tr, b, mode="batched")
+
+
+def test_paper_constants_and_magdown(lfm):
+    geo = synth.Geometry(polarity=-1)
+    b = synth.generate(1, n_events=100, geometry=geo).to("cuda")
+    g = geo_dict(geo)
+    p = lfm.default_params(paper_K=True)
+    tr = _tracker(lfm, g, p)
+    run_both(tr, b, mode="plain", geometry=g, params=p, stages=True)
+    run_both(tr, b, mode="batched", geometry=g, params=p)
+
+
+@pytest.mark.parametrize("cap,nt", [(1, 1), (5, 3), (17, 32), (64, 20), (32, 0)])
+def test_parameter_edges(lfm, cap, nt):
+    p = lfm.default_params()
+    p.update(n_hits_window=cap, n_triplets=nt)
+    b = synth.generate(1, n_events=40).to("cuda")
+    tr = _tracker(lfm, None, p)
+    for mode in ("plain", "batched"):
+        run_both(tr, b, mode=mode, params=p, stages=(mode == "plain" and nt > 0))
+
+
+@pytest.mark.parametrize("tuning", [dict(warps_per_block=1, grain=1, blocks_per_sm=1),
+                                    dict(warps_per_block=4, grain=3),
+                                    dict(warps_per_block=16, grain=16),
+                                    dict(warps_per_block=8, grain=64, blocks_per_sm=2)])
+def test_launch_shapes_identical(lfm, tuning):
+    b = synth.generate(1, n_events=120).to("cuda")
+    tr = _tracker(lfm)
+    run_both(tr, b, mode="batched", tuning=tuning)
+
+
+def test_ragged_and_empty_events(lfm):
+    geo = synth.Geometry()
+    tx, ty, q = 0.1, 0.05, 1 / 8.0
+    _, y, xm = synth.trajectory(tx, ty, q)
+    full = [(l, 1, float(xm[l])) for l in range(12)]
+    st = synth.state_of(tx, ty, q)
+    events = [
+        dict(hits=[], states=[]),                        # nothing
+        dict(hits=full, states=[]),                      # hits, no tracks
+        dict(hits=[], states=[st, st]),                  # tracks, no hits
+        dict(hits=full + [(0, 1, float(xm[0]))] * 3, states=[st]),   # duplicate x values
+        dict(hits=full, states=[st] * 40),               # many identical tracks
+        dict(hits=[], states=[]),
+    ]
+    b = make_batch(events, geo).to("cuda")
+    tr = _tracker(lfm)
+    for mode in ("plain", "batched"):
+        info, *_ = run_both(tr, b, mode=mode, stages=(mode == "plain"))
+        assert info["n_found"] == 41
+
+
+def test_empty_batch(lfm):
+    b = make_batch([], synth.Geometry()).to("cuda")
+    tr = _tracker(lfm)
+    for mode in ("plain", "batched"):
+        packed, out = tr.run(b, mode=mode)
+        torch.cuda.synchronize()
+        assert int(to_np(out["n_out"])[0]) == 0
+        assert to_np(packed["hit_offsets"]).tolist() == [0]
+
+
+def test_bucket_over_capacity_is_reported(lfm):
+    # one bucket above the largest sortable size: the pack skips it and flags it
+    n = 8193
+    hits = [(0, 1, float(i % 5000)) for i in range(n)]
+    b = make_batch([dict(hits=hits, states=[])], synth.Geometry()).to("cuda")
+    tr = _tracker(lfm)
+    tr.pack(b)
+    with pytest.raises(lfm.LFError) as ei:
+        tr.status()
+    assert ei.value.status == lfm.LF_ERR_CAPACITY
+    assert tr.status() == 0  # cleared
+
+
+def test_bad_parameters_rejected(lfm):
+    p = lfm.default_params()
+    p["n_hits_window"] = 65
+    with pytest.raises(lfm.LFError):
+        lfm.Tracker(None, p)
+    p = lfm.default_params()
+    p["min_hits"] = 8
+    with pytest.raises(lfm.LFError):
+        lfm.Tracker(None, p)
+
+
+def test_full_size_uneven_sampled(lfm):
+    """The uneven 100 000-event workload in the launch configuration the
+    benchmark times; the oracle recomputes a sample of events one by one."""
+    b = synth.generate(2, device="cuda", truth=False)
+    tr = _tracker(lfm)
+    packed, out = tr.run(b, mode="batched")
+    torch.cuda.synchronize()
+    assert tr.status() == 0
+    ro = to_np(b.raw_offsets).astype(np.int64)
+    to = to_np(b.trk_offsets).astype(np.int64)
+    ntrk = np.diff(to)
+    rng = np.random.default_rng(5)
+    sample = sorted(set(rng.choice(b.n_events, 48, replace=False).tolist()) |
+                    {int(np.argmax(ntrk)), int(np.argmax(np.diff(ro))), b.n_events - 1})
+    sub = b.select_events(sample).to("cpu")
+    res = oracle.run_batch(sub, dumps=False)
+    perm_g = to_np(packed["perm"])
+    found_g = to_np(out["found"]).astype(bool)
+    hit_g = to_np(out["hit_idx"])
+    st_g = to_np(out["state"])
+    q_g = to_np(out["quality"])
+    ro_s = to_np(sub.raw_offsets).astype(np.int64)
+    to_s = to_np(sub.trk_offsets).astype(np.int64)
+    perm_o = res["packed"]["perm"]
+    n_cmp = 0
+    for k, e in enumerate(sample):
+        for j in range(to_s[k + 1] - to_s[k]):
+            ts, tg = to_s[k] + j, to[e] + j
+            assert bool(res["found"][ts]) == found_g[tg], ("found", e, j)
+            if not found_g[tg]:
+                continue
+            raw_o = [ro[e] + (perm_o[h] - ro_s[k]) if h >= 0 else -1 for h in res["hit_idx"][ts]]
+            raw_g = [perm_g[h] if h >= 0 else -1 for h in hit_g[tg]]
+            assert raw_o == raw_g, ("hits", e, j)
+            assert np.array_equal(st_g[tg].view(np.uint32), res["state"][ts].view(np.uint32)), ("state", e, j)
+            assert q_g[tg] == res["quality"][ts]
+            n_cmp += 1
+    assert n_cmp > 1000
+    # compaction over the whole batch
+    f = found_g.astype(np.int64)
+    cnt = np.add.reduceat(f, to[:-1]) if f.size else f
+    cnt = np.where(ntrk > 0, cnt, 0)
+    assert np.array_equal(to_np(out["out_offsets"]), np.concatenate([[0], np.cumsum(cnt)]))
+    n_out = int(to_np(out["n_out"])[0])
+    assert np.array_equal(to_np(out["out_trk"])[:n_out], np.nonzero(found_g)[0])
