@@ -182,6 +182,35 @@ lf_status lf_find_tracks(lf_ctx* ctx, const lf_batch* batch, const lf_output* ou
 lf_status lf_find_tracks_batched(lf_ctx* ctx, const lf_batch* batch, const lf_output* out,
                                  const lf_tuning* tuning, void* stream);
 
+/* Host-resident batch for lf_process_host: pointers are HOST pointers
+ * (pinned memory gives full copy bandwidth; pageable memory also works). */
+typedef struct {
+    int32_t n_events;
+    int32_t n_hits;
+    int32_t n_tracks;
+    const int32_t* raw_offsets;   /* [n_events+1] */
+    const float* x; const float* z; const float* dxdy; const float* w;
+    const uint8_t* plane;
+    const int32_t* trk_offsets;   /* [n_events+1] */
+    const float* sx; const float* sy; const float* stx; const float* sty; const float* sqop;
+} lf_host_batch;
+
+/* Host-resident per-track results of lf_process_host (HOST pointers).
+ * hit_idx holds RAW hit indices of the input batch (-1 none); hit_idx,
+ * state and quality are written only where found[t] == 1. */
+typedef struct {
+    uint8_t* found; uint8_t* nhits; int32_t* hit_idx; float* state; float* quality;
+} lf_host_output;
+
+/* End-to-end call on host buffers: the batch is cut at event boundaries into
+ * chunks of at most chunk_hits hits; each chunk is copied to the device,
+ * packed, followed (persistent form) and its results copied back, with two
+ * chunks in flight on two internal streams so copies overlap compute.  The
+ * device staging buffers belong to the context.  Synchronous: returns after
+ * the results are in host memory.  chunk_hits <= 0 selects 1<<26. */
+lf_status lf_process_host(lf_ctx* ctx, const lf_host_batch* batch, const lf_host_output* out,
+                          const lf_tuning* tuning, int64_t chunk_hits);
+
 /* Stage dumps of the plain form for debugging and parity tests:
  * win_begin/win_count [n_tracks*12] (int32), n_trip [n_tracks] (int32),
  * trip [n_tracks*n_triplets*4] (int32 cfg, h0, h1, h2; packed indices),

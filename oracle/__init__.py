@@ -121,6 +121,7 @@ def build(force: bool = False) -> str:
 def _bind(path: str):
     lib = C.CDLL(path)
     lib.lfo_pack.restype = C.c_int
+    lib.lfo_pack_mt.restype = C.c_int
     lib.lfo_find_tracks.restype = C.c_int
     lib.lfo_find_tracks_mt.restype = C.c_int
     lib.lfo_compact.restype = C.c_int32
@@ -197,7 +198,7 @@ class Oracle:
     def __init__(self, lib_path: str):
         self.lib = _bind(lib_path)
 
-    def pack(self, raw_offsets, x, z, dxdy, w, plane) -> dict:
+    def pack(self, raw_offsets, x, z, dxdy, w, plane, n_threads: int = 1) -> dict:
         """Bucket and sort raw hits: returns hit_offsets [24*n_ev+1], the
         packed x, z, dxdy, w, layer and perm (packed index -> raw index)."""
         ro = _c(raw_offsets, np.int32)
@@ -209,8 +210,13 @@ class Oracle:
         outs = [np.zeros(n, np.float32) for _ in range(4)]
         layer = np.zeros(n, np.uint8)
         perm = np.zeros(n, np.int32)
-        rc = self.lib.lfo_pack(C.c_int32(n_ev), _ptr(ro), *[_ptr(a) for a in arrs], _ptr(pl), _ptr(ho),
-                               *[_ptr(a) for a in outs], _ptr(layer), _ptr(perm))
+        if n_threads > 1:
+            rc = self.lib.lfo_pack_mt(C.c_int32(n_ev), _ptr(ro), *[_ptr(a) for a in arrs], _ptr(pl), _ptr(ho),
+                                      *[_ptr(a) for a in outs], _ptr(layer), _ptr(perm), C.c_int32(n_threads))
+            ho[NB * n_ev] = ro[n_ev] if n_ev else 0
+        else:
+            rc = self.lib.lfo_pack(C.c_int32(n_ev), _ptr(ro), *[_ptr(a) for a in arrs], _ptr(pl), _ptr(ho),
+                                   *[_ptr(a) for a in outs], _ptr(layer), _ptr(perm))
         if rc != 0:
             raise ValueError("lfo_pack failed (%d)" % rc)
         return dict(hit_offsets=ho, x=outs[0], z=outs[1], dxdy=outs[2], w=outs[3],
@@ -258,7 +264,7 @@ class Oracle:
         """Pack + find + compact for an ``EventBatch`` (tensors on any device)."""
         t = lambda a: a.detach().cpu().numpy()
         pk = self.pack(t(batch.raw_offsets), t(batch.x), t(batch.z), t(batch.dxdy), t(batch.w),
-                       t(batch.plane))
+                       t(batch.plane), n_threads=n_threads)
         states = dict(trk_offsets=t(batch.trk_offsets), sx=t(batch.sx), sy=t(batch.sy),
                       stx=t(batch.stx), sty=t(batch.sty), sqop=t(batch.sqop))
         x64 = None

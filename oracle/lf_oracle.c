@@ -625,6 +625,51 @@ int lfo_find_tracks_mt(const lfo_geometry* g, const lfo_params* p, int32_t n_eve
     return rc;
 }
 
+/* pack with the events split over n_threads POSIX threads (the per-event
+ * code is lfo_pack's; offsets are absolute, so ranges are independent) */
+typedef struct {
+    int32_t e0, e1; const int32_t* raw_offsets; const float *x, *z, *dxdy, *w; const uint8_t* plane;
+    int32_t* hit_offsets; float *ox, *oz, *odxdy, *ow; uint8_t* olayer; int32_t* perm; int rc;
+} pk_job;
+
+static void* pk_run(void* arg)
+{
+    pk_job* j = (pk_job*)arg;
+    int32_t n = j->e1 - j->e0;
+    /* run lfo_pack on the sub-range: it writes hit_offsets[e*24 ..] for its
+     * events relative to the sub-range base, so shift the pointer */
+    j->rc = lfo_pack(n, j->raw_offsets + j->e0, j->x, j->z, j->dxdy, j->w, j->plane,
+                     j->hit_offsets + (size_t)j->e0 * LFO_NB, j->ox, j->oz, j->odxdy, j->ow, j->olayer, j->perm);
+    return NULL;
+}
+
+int lfo_pack_mt(int32_t n_events, const int32_t* raw_offsets,
+                const float* x, const float* z, const float* dxdy, const float* w, const uint8_t* plane,
+                int32_t* hit_offsets, float* ox, float* oz, float* odxdy, float* ow,
+                uint8_t* olayer, int32_t* perm, int32_t n_threads)
+{
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 1024) n_threads = 1024;
+    pthread_t th[1024];
+    pk_job jobs[1024];
+    int32_t per = (n_events + n_threads - 1) / n_threads;
+    int started = 0, rc = 0;
+    for (int i = 0; i < n_threads; ++i) {
+        int32_t e0 = i * per, e1 = e0 + per;
+        if (e1 > n_events) e1 = n_events;
+        if (e0 >= e1) break;
+        pk_job jb = {e0, e1, raw_offsets, x, z, dxdy, w, plane, hit_offsets, ox, oz, odxdy, ow, olayer, perm, 0};
+        jobs[i] = jb;
+        if (pthread_create(&th[i], NULL, pk_run, &jobs[i]) != 0) { rc = -4; break; }
+        ++started;
+    }
+    for (int i = 0; i < started; ++i) {
+        pthread_join(th[i], NULL);
+        if (jobs[i].rc) rc = jobs[i].rc;
+    }
+    return rc;
+}
+
 /* ------------------------------------------------------------- compaction */
 
 int32_t lfo_compact(int32_t n_events, const int32_t* trk_offsets, const uint8_t* found,

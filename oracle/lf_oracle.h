@@ -73,6 +73,12 @@ int lfo_pack(int32_t n_events, const int32_t* raw_offsets,
              int32_t* hit_offsets, float* ox, float* oz, float* odxdy, float* ow,
              uint8_t* olayer, int32_t* perm);
 
+/* lfo_pack with the events split over n_threads POSIX threads. */
+int lfo_pack_mt(int32_t n_events, const int32_t* raw_offsets,
+                const float* x, const float* z, const float* dxdy, const float* w, const uint8_t* plane,
+                int32_t* hit_offsets, float* ox, float* oz, float* odxdy, float* ow,
+                uint8_t* olayer, int32_t* perm, int32_t n_threads);
+
 /* Run windows -> triplets -> extension -> fit/quality -> selection for every
  * input track of events [0, n_events).  x64 (optional) gives binary64 hit
  * coordinates for the state64 refit; NULL promotes the binary32 ones. */

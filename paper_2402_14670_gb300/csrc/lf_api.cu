@@ -3,8 +3,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <tuple>
+#include <vector>
 
 #include "lf.h"
 #include "lf_internal.h"
@@ -41,6 +43,11 @@ struct lf_ctx {
         cudaStream_t stream = nullptr;
     };
     std::map<GraphKey, GraphEntry> graphs;
+    // end-to-end host pipeline: two sub-contexts (own scratch), two streams,
+    // two device staging arenas
+    lf_ctx* sub[2] = {nullptr, nullptr};
+    cudaStream_t pipe_stream[2] = {nullptr, nullptr};
+    DevBuf arena[2];
 };
 
 namespace {
@@ -248,6 +255,11 @@ lf_status lf_create(const lf_geometry* geometry, const lf_params* params, lf_ctx
 void lf_destroy(lf_ctx* c) {
     if (!c) return;
     cudaDeviceSynchronize();
+    for (int i = 0; i < 2; ++i) {
+        if (c->sub[i]) lf_destroy(c->sub[i]);
+        if (c->pipe_stream[i]) cudaStreamDestroy(c->pipe_stream[i]);
+        if (c->arena[i].p) cudaFree(c->arena[i].p);
+    }
     for (auto& kv : c->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     DevBuf* bufs[] = {&c->trk_event, &c->wbeg, &c->wcnt, &c->keys, &c->ntrip,
@@ -305,6 +317,38 @@ lf_status lf_find_tracks(lf_ctx* c, const lf_batch* b, const lf_output* o, void*
                               o->out_trk, o->n_out, s));
     return LF_OK;
 }
+
+namespace {
+
+struct Shape {
+    int wpb, bps, grain;
+};
+
+lf_status resolve_shape(lf_ctx* c, const lf_tuning* tuning, Shape& sh) {
+    sh.wpb = tuning && tuning->warps_per_block > 0 ? tuning->warps_per_block : 8;
+    sh.grain = tuning && tuning->grain > 0 ? tuning->grain : 4;
+    if (sh.wpb > 16) return fail(c, LF_ERR_ARG, "warps_per_block %d above 16", sh.wpb);
+    int max_bps = 0;
+    LF_CUDA(c, fused_max_blocks_per_sm(c->kp, sh.wpb, &max_bps));
+    if (max_bps < 1) return fail(c, LF_ERR_ARG, "launch shape does not fit on an SM");
+    sh.bps = tuning && tuning->blocks_per_sm > 0 ? tuning->blocks_per_sm : max_bps;
+    if (sh.bps > max_bps) sh.bps = max_bps;
+    return LF_OK;
+}
+
+// persistent form without a graph: queue reset, fused kernel, compaction
+lf_status batched_direct(lf_ctx* c, const lf_batch* b, const lf_output* o, const Shape& sh, cudaStream_t s) {
+    lf_status st;
+    if ((st = ensure(c, c->ev_count, (size_t)b->n_events * 4)) != LF_OK) return st;
+    LF_CUDA(c, cudaMemsetAsync(c->cursor, 0, sizeof(int), s));
+    if (b->n_tracks > 0)
+        LF_CUDA(c, launch_fused(c->kp, to_kbatch(b), to_kout(o), c->cursor, sh.grain, sh.wpb, sh.bps * c->n_sm, s));
+    LF_CUDA(c, launch_compact(b->trk_offsets, o->found, b->n_events, (int*)c->ev_count.p, o->out_offsets, o->out_trk,
+                              o->n_out, s));
+    return LF_OK;
+}
+
+}  // namespace
 
 lf_status lf_find_tracks_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const lf_tuning* tuning,
                                  void* stream) {
@@ -391,6 +435,151 @@ lf_status lf_sync_status(lf_ctx* c, void* stream, int32_t* flags) {
     if (v & LF_FLAG_TIMEOUT) return fail(c, LF_ERR_TIMEOUT, "a bounded device wait ran out");
     if (v & (LF_FLAG_BUCKET_OVERFLOW | LF_FLAG_PLANE_RANGE))
         return fail(c, LF_ERR_CAPACITY, "bucket over %d hits or plane code >= 24 (flags 0x%x)", LF_MAX_BUCKET, v);
+    return LF_OK;
+}
+
+lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_output* ho, const lf_tuning* tuning,
+                          int64_t chunk_hits) {
+    if (!c) return LF_ERR_ARG;
+    if (!hb || !ho) return fail(c, LF_ERR_ARG, "batch or output is NULL");
+    if (hb->n_events < 0 || hb->n_hits < 0 || hb->n_tracks < 0) return fail(c, LF_ERR_ARG, "negative size");
+    if (!hb->raw_offsets || !hb->trk_offsets) return fail(c, LF_ERR_ARG, "offsets are NULL");
+    if (hb->raw_offsets[hb->n_events] != hb->n_hits || hb->trk_offsets[hb->n_events] != hb->n_tracks)
+        return fail(c, LF_ERR_ARG, "offsets do not end at n_hits / n_tracks");
+    if (hb->n_events == 0) return LF_OK;
+    if (chunk_hits <= 0) chunk_hits = (int64_t)1 << 26;
+    lf_status st;
+    Shape sh;
+    if ((st = resolve_shape(c, tuning, sh)) != LF_OK) return st;
+    for (int i = 0; i < 2; ++i) {
+        if (!c->sub[i] && (st = lf_create(&c->g, &c->p, &c->sub[i])) != LF_OK)
+            return fail(c, st, "sub-context creation failed");
+        if (!c->pipe_stream[i]) LF_CUDA(c, cudaStreamCreateWithFlags(&c->pipe_stream[i], cudaStreamNonBlocking));
+    }
+    // chunk boundaries at event boundaries
+    std::vector<int> cut{0};
+    const int32_t* ro = hb->raw_offsets;
+    const int32_t* to = hb->trk_offsets;
+    for (int e = 0; e < hb->n_events; ++e) {
+        int s0 = cut.back();
+        if (e > s0 && (int64_t)ro[e + 1] - ro[s0] > chunk_hits) cut.push_back(e);
+    }
+    cut.push_back(hb->n_events);
+    size_t H = 0, E = 0, T = 0;
+    for (size_t k = 0; k + 1 < cut.size(); ++k) {
+        H = std::max(H, (size_t)(ro[cut[k + 1]] - ro[cut[k]]));
+        E = std::max(E, (size_t)(cut[k + 1] - cut[k]));
+        T = std::max(T, (size_t)(to[cut[k + 1]] - to[cut[k]]));
+    }
+    // rebased offsets of every chunk, in one pinned block
+    const size_t n_chunks = cut.size() - 1;
+    int32_t* pin = nullptr;
+    const size_t pin_n = 2 * ((size_t)hb->n_events + n_chunks);
+    LF_CUDA(c, cudaMallocHost(&pin, pin_n * sizeof(int32_t)));
+    std::vector<size_t> pin_off(n_chunks);
+    {
+        size_t q = 0;
+        for (size_t k = 0; k < n_chunks; ++k) {
+            pin_off[k] = q;
+            int e0 = cut[k], e1 = cut[k + 1];
+            for (int e = e0; e <= e1; ++e) pin[q++] = ro[e] - ro[e0];
+            for (int e = e0; e <= e1; ++e) pin[q++] = to[e] - to[e0];
+        }
+    }
+    // device arena per slot
+    auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+    size_t off_raw = 0, sz = 0;
+    size_t o_x = sz; sz += al(4 * H);
+    size_t o_z = sz; sz += al(4 * H);
+    size_t o_d = sz; sz += al(4 * H);
+    size_t o_w = sz; sz += al(4 * H);
+    size_t o_pl = sz; sz += al(H);
+    size_t o_ro = sz; sz += al(4 * (E + 1));
+    size_t o_to = sz; sz += al(4 * (E + 1));
+    size_t o_st = sz; sz += al(4 * 5 * T);
+    size_t o_ho = sz; sz += al(4 * (NB * E + 1));
+    size_t o_px = sz; sz += al(4 * H);
+    size_t o_pz = sz; sz += al(4 * H);
+    size_t o_pd = sz; sz += al(4 * H);
+    size_t o_pw = sz; sz += al(4 * H);
+    size_t o_pl2 = sz; sz += al(H);
+    size_t o_pm = sz; sz += al(4 * H);
+    size_t o_fd = sz; sz += al(T);
+    size_t o_nh = sz; sz += al(T);
+    size_t o_hi = sz; sz += al(4 * NL * T);
+    size_t o_sv = sz; sz += al(4 * 6 * T);
+    size_t o_q = sz; sz += al(4 * T);
+    size_t o_oo = sz; sz += al(4 * (E + 1));
+    size_t o_ot = sz; sz += al(4 * (T + 1));
+    size_t o_no = sz; sz += al(4);
+    (void)off_raw;
+    for (int i = 0; i < 2; ++i) {
+        if ((st = ensure(c, c->arena[i], sz)) != LF_OK) {
+            cudaFreeHost(pin);
+            return st;
+        }
+    }
+    lf_status rc = LF_OK;
+    cudaError_t ce = cudaSuccess;
+    for (size_t k = 0; k < n_chunks && rc == LF_OK && ce == cudaSuccess; ++k) {
+        const int slot = (int)(k & 1);
+        lf_ctx* sc = c->sub[slot];
+        cudaStream_t s = c->pipe_stream[slot];
+        char* A = (char*)c->arena[slot].p;
+        const int e0 = cut[k], e1 = cut[k + 1];
+        const int ne = e1 - e0, h0 = ro[e0], nh = ro[e1] - ro[e0], t0 = to[e0], nt = to[e1] - to[e0];
+        auto cp = [&](size_t dst, const void* src, size_t bytes) {
+            if (ce == cudaSuccess && bytes) ce = cudaMemcpyAsync(A + dst, src, bytes, cudaMemcpyHostToDevice, s);
+        };
+        cp(o_ro, pin + pin_off[k], 4 * (size_t)(ne + 1));
+        cp(o_to, pin + pin_off[k] + ne + 1, 4 * (size_t)(ne + 1));
+        cp(o_x, hb->x + h0, 4 * (size_t)nh);
+        cp(o_z, hb->z + h0, 4 * (size_t)nh);
+        cp(o_d, hb->dxdy + h0, 4 * (size_t)nh);
+        cp(o_w, hb->w + h0, 4 * (size_t)nh);
+        cp(o_pl, hb->plane + h0, (size_t)nh);
+        cp(o_st + 0 * 4 * T, hb->sx + t0, 4 * (size_t)nt);
+        cp(o_st + 1 * 4 * T, hb->sy + t0, 4 * (size_t)nt);
+        cp(o_st + 2 * 4 * T, hb->stx + t0, 4 * (size_t)nt);
+        cp(o_st + 3 * 4 * T, hb->sty + t0, 4 * (size_t)nt);
+        cp(o_st + 4 * 4 * T, hb->sqop + t0, 4 * (size_t)nt);
+        if (ce != cudaSuccess) break;
+        lf_raw_hits raw{ne, nh, (const int32_t*)(A + o_ro), (const float*)(A + o_x), (const float*)(A + o_z),
+                        (const float*)(A + o_d), (const float*)(A + o_w), (const uint8_t*)(A + o_pl)};
+        lf_packed pk{(int32_t*)(A + o_ho), (float*)(A + o_px), (float*)(A + o_pz), (float*)(A + o_pd),
+                     (float*)(A + o_pw), (uint8_t*)(A + o_pl2), (int32_t*)(A + o_pm)};
+        if ((rc = lf_pack_hits(sc, &raw, &pk, s)) != LF_OK) break;
+        lf_batch bt{ne, nh, nt, pk.hit_offsets, pk.x, pk.z, pk.dxdy, pk.w, (const int32_t*)(A + o_to),
+                    (const float*)(A + o_st), (const float*)(A + o_st + 4 * T), (const float*)(A + o_st + 8 * T),
+                    (const float*)(A + o_st + 12 * T), (const float*)(A + o_st + 16 * T)};
+        lf_output out{(uint8_t*)(A + o_fd), (uint8_t*)(A + o_nh), (int32_t*)(A + o_hi), (float*)(A + o_sv),
+                      (float*)(A + o_q), (int32_t*)(A + o_oo), (int32_t*)(A + o_ot), (int32_t*)(A + o_no)};
+        if ((rc = batched_direct(sc, &bt, &out, sh, s)) != LF_OK) break;
+        ce = launch_hits_to_raw(out.found, out.hit_idx, pk.perm, nt, h0, s);
+        auto back = [&](void* dst, size_t src, size_t bytes) {
+            if (ce == cudaSuccess && bytes && dst) ce = cudaMemcpyAsync(dst, A + src, bytes, cudaMemcpyDeviceToHost, s);
+        };
+        back(ho->found + t0, o_fd, (size_t)nt);
+        back(ho->nhits + t0, o_nh, (size_t)nt);
+        back(ho->hit_idx + (size_t)t0 * NL, o_hi, 4 * NL * (size_t)nt);
+        back(ho->state + (size_t)t0 * 6, o_sv, 4 * 6 * (size_t)nt);
+        back(ho->quality + t0, o_q, 4 * (size_t)nt);
+    }
+    for (int i = 0; i < 2; ++i) {
+        cudaError_t e2 = cudaStreamSynchronize(c->pipe_stream[i]);
+        if (ce == cudaSuccess) ce = e2;
+    }
+    cudaFreeHost(pin);
+    if (rc != LF_OK) return fail(c, rc, "chunk failed: %s", lf_last_error(c->sub[0])[0] ? lf_last_error(c->sub[0]) : lf_last_error(c->sub[1]));
+    if (ce != cudaSuccess) return fail(c, LF_ERR_CUDA, "host pipeline: %s", cudaGetErrorString(ce));
+    int flags = 0;
+    for (int i = 0; i < 2; ++i) {
+        int32_t f = 0;
+        lf_status s2 = lf_sync_status(c->sub[i], c->pipe_stream[i], &f);
+        flags |= f;
+        if (s2 != LF_OK && rc == LF_OK) rc = s2;
+    }
+    if (rc != LF_OK) return fail(c, rc, "device status flags 0x%x", flags);
     return LF_OK;
 }
 

@@ -93,6 +93,8 @@ cudaError_t launch_select(const KParams& k, const KBatch& b, const int* wbeg, co
 cudaError_t launch_fused(const KParams& k, const KBatch& b, const KOut& o, int* cursor, int grain,
                          int warps_per_block, int n_blocks, cudaStream_t s);
 cudaError_t fused_max_blocks_per_sm(const KParams& k, int warps_per_block, int* out);
+cudaError_t launch_hits_to_raw(const uint8_t* found, int* hit_idx, const int* perm, int n_tracks, int base,
+                              cudaStream_t s);
 cudaError_t launch_compact(const int* trk_offsets, const uint8_t* found, int n_events, int* ev_count,
                            int* out_offsets, int* out_trk, int* n_out, cudaStream_t s);
 cudaError_t launch_debug_triplets(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* wcnt,

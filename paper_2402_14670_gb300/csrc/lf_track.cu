@@ -778,6 +778,16 @@ __global__ void k_debug_triplets(KParams k, KBatch b, const int* __restrict__ wb
     }
 }
 
+// packed hit indices -> raw hit indices (+ base), for results leaving the device
+__global__ void k_hits_to_raw(const uint8_t* __restrict__ found, int* hit_idx, const int* __restrict__ perm,
+                              int n_tracks, int base) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tracks * NL) return;
+    if (!found[i / NL]) return;
+    int h = hit_idx[i];
+    hit_idx[i] = h >= 0 ? __ldg(perm + h) + base : -1;
+}
+
 // ------------------------------------------------------------- compaction
 
 // per-event count of found tracks (warp per event)
@@ -907,6 +917,13 @@ cudaError_t launch_fused(const KParams& k, const KBatch& b, const KOut& o, int* 
     cudaError_t err = set_smem((const void*)k_fused, sm);
     if (err != cudaSuccess) return err;
     k_fused<<<n_blocks, warps_per_block * 32, sm, s>>>(k, b, o, cursor, grain);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hits_to_raw(const uint8_t* found, int* hit_idx, const int* perm, int n_tracks, int base,
+                              cudaStream_t s) {
+    if (n_tracks <= 0) return cudaSuccess;
+    k_hits_to_raw<<<cdiv((long)n_tracks * NL, 256), 256, 0, s>>>(found, hit_idx, perm, n_tracks, base);
     return cudaGetLastError();
 }
 

@@ -72,6 +72,16 @@ class lf_output(C.Structure):
                 ("out_offsets", _P), ("out_trk", _P), ("n_out", _P)]
 
 
+class lf_host_batch(C.Structure):
+    _fields_ = [("n_events", C.c_int32), ("n_hits", C.c_int32), ("n_tracks", C.c_int32), ("raw_offsets", _P),
+                ("x", _P), ("z", _P), ("dxdy", _P), ("w", _P), ("plane", _P), ("trk_offsets", _P), ("sx", _P),
+                ("sy", _P), ("stx", _P), ("sty", _P), ("sqop", _P)]
+
+
+class lf_host_output(C.Structure):
+    _fields_ = [("found", _P), ("nhits", _P), ("hit_idx", _P), ("state", _P), ("quality", _P)]
+
+
 class lf_tuning(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("grain", C.c_int32),
                 ("reserved", C.c_int32)]
@@ -95,9 +105,12 @@ _lib.lf_debug_stages.argtypes = [_P, C.POINTER(lf_batch), _P, _P, _P, _P, _P, _P
 _lib.lf_debug_stages.restype = C.c_int
 _lib.lf_sync_status.argtypes = [_P, _P, C.POINTER(C.c_int32)]
 _lib.lf_sync_status.restype = C.c_int
+_lib.lf_process_host.argtypes = [_P, C.POINTER(lf_host_batch), C.POINTER(lf_host_output), C.POINTER(lf_tuning),
+                                 C.c_int64]
+_lib.lf_process_host.restype = C.c_int
 
 EXPORTED = ["lf_create", "lf_destroy", "lf_last_error", "lf_device_sm_count", "lf_pack_hits", "lf_find_tracks",
-            "lf_find_tracks_batched", "lf_debug_stages", "lf_sync_status"]
+            "lf_find_tracks_batched", "lf_debug_stages", "lf_sync_status", "lf_process_host"]
 
 
 class LFError(RuntimeError):
@@ -199,6 +212,12 @@ def lf_find_tracks_batched(ctx, batch: lf_batch, out: lf_output, tuning: Optiona
 
 def lf_debug_stages(ctx, batch: lf_batch, win_begin, win_count, n_trip, trip, trip_chi2, stream) -> None:
     _check(ctx, _lib.lf_debug_stages(ctx, C.byref(batch), win_begin, win_count, n_trip, trip, trip_chi2, stream))
+
+
+def lf_process_host(ctx, batch: lf_host_batch, out: lf_host_output, tuning: Optional[lf_tuning],
+                    chunk_hits: int = 0) -> None:
+    tp = C.byref(tuning) if tuning is not None else None
+    _check(ctx, _lib.lf_process_host(ctx, C.byref(batch), C.byref(out), tp, C.c_int64(chunk_hits)))
 
 
 def lf_sync_status(ctx, stream) -> int:
@@ -319,6 +338,41 @@ class Tracker:
 
     def status(self, stream=None) -> int:
         return lf_sync_status(self.ctx, _stream(stream))
+
+    @staticmethod
+    def _hptr(t: torch.Tensor):
+        if t.is_cuda:
+            raise ValueError("expected a host tensor")
+        if not t.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return _P(t.data_ptr()) if t.numel() else None
+
+    @staticmethod
+    def alloc_host_output(n_tracks: int, pin: bool = True) -> dict:
+        e = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=pin)
+        return dict(found=e(n_tracks, torch.uint8), nhits=e(n_tracks, torch.uint8),
+                    hit_idx=e((n_tracks, NL), torch.int32), state=e((n_tracks, 6), torch.float32),
+                    quality=e(n_tracks, torch.float32))
+
+    def process_host(self, batch, out: Optional[dict] = None, tuning: Optional[dict] = None,
+                     chunk_hits: int = 0) -> dict:
+        """End to end on host tensors (pinned for full speed): copies in,
+        pack, find, copies the per-track results out; hit_idx are raw
+        indices of the input batch."""
+        h = self._hptr
+        n_t = int(batch.sx.numel())
+        if out is None:
+            out = self.alloc_host_output(n_t)
+        hb = lf_host_batch(int(batch.n_events), int(batch.x.numel()), n_t, h(batch.raw_offsets), h(batch.x),
+                           h(batch.z), h(batch.dxdy), h(batch.w), h(batch.plane), h(batch.trk_offsets), h(batch.sx),
+                           h(batch.sy), h(batch.stx), h(batch.sty), h(batch.sqop))
+        ho = lf_host_output(h(out["found"]), h(out["nhits"]), h(out["hit_idx"]), h(out["state"]), h(out["quality"]))
+        tu = None
+        if tuning:
+            tu = lf_tuning(int(tuning.get("warps_per_block", 0)), int(tuning.get("blocks_per_sm", 0)),
+                           int(tuning.get("grain", 0)), 0)
+        lf_process_host(self.ctx, hb, ho, tu, int(chunk_hits))
+        return out
 
     def run(self, raw, mode: str = "batched", tuning: Optional[dict] = None, stream=None):
         """pack + find for a batch whose tensors live on the GPU."""

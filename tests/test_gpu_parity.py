@@ -191,3 +191,24 @@ def test_full_size_uneven_sampled(lfm):
     assert np.array_equal(to_np(out["out_offsets"]), np.concatenate([[0], np.cumsum(cnt)]))
     n_out = int(to_np(out["n_out"])[0])
     assert np.array_equal(to_np(out["out_trk"])[:n_out], np.nonzero(found_g)[0])
+
+
+@pytest.mark.parametrize("chunk_hits", [0, 150_000])
+def test_end_to_end_host_pipeline(lfm, chunk_hits):
+    """lf_process_host (host buffers, chunked and double-buffered) gives the
+    device path's results, with hit indices mapped back to raw indices."""
+    b = synth.generate(1, n_events=120)           # host tensors
+    bp = b.pin_memory()
+    tr = _tracker(lfm)
+    ho = tr.process_host(bp, chunk_hits=chunk_hits)
+    packed, out = tr.run(b.to("cuda"), mode="batched")
+    torch.cuda.synchronize()
+    found = to_np(out["found"]).astype(bool)
+    assert np.array_equal(ho["found"].numpy().astype(bool), found)
+    perm = to_np(packed["perm"])
+    hd = to_np(out["hit_idx"])[found]
+    raw = np.where(hd >= 0, perm[np.maximum(hd, 0)], -1)
+    assert np.array_equal(ho["hit_idx"].numpy()[found], raw)
+    assert np.array_equal(ho["state"].numpy()[found].view(np.uint32), to_np(out["state"])[found].view(np.uint32))
+    res = oracle.run_batch(b, dumps=False)
+    assert np.array_equal(res["found"].astype(bool), found)
