@@ -211,6 +211,31 @@ typedef struct {
 lf_status lf_process_host(lf_ctx* ctx, const lf_host_batch* batch, const lf_host_output* out,
                           const lf_tuning* tuning, int64_t chunk_hits);
 
+/* Largest batch (events) lf_find_tracks_static accepts. */
+#define LF_STATIC_MAX_EVENTS 262144
+
+/* lf_find_tracks_static — for callers that cannot allocate device memory.
+ * (The paper has no counterpart: this is a deployment variant.)
+ * Some callers may not call cudaMalloc: a process whose device memory is all
+ * owned by its own pool, code on a latency-critical path where cudaMalloc and
+ * cudaFree (which synchronises the device) are not acceptable, or a framework
+ * that forbids allocation after start-up.  Such callers cannot use lf_create.
+ * This call runs the same persistent kernel and compaction as
+ * lf_find_tracks_batched (default launch shape) without a context and without
+ * allocating: its scratch (work-queue cursor, per-event counts) is a static
+ * device array of 4*(64 + LF_STATIC_MAX_EVENTS) bytes (about 1 MiB) that every
+ * GPU loading the library keeps until the process exits.  The caller passes
+ * inputs and outputs as for lf_find_tracks_batched.
+ *   - The first call on a device (with that device current) looks the array's
+ *     address up once; make that first call before any stream capture.
+ *   - All calls share the array; each call clears the cursor it needs.  Calls
+ *     that overlap on the GPU (other streams, other threads) race on it.
+ *   - Returns LF_ERR_CAPACITY, without launching, when batch->n_events is
+ *     above LF_STATIC_MAX_EVENTS; LF_ERR_ARG on invalid parameters or a NULL
+ *     pointer; LF_ERR_CUDA on a launch error.  Asynchronous on stream. */
+lf_status lf_find_tracks_static(const lf_geometry* geometry, const lf_params* params, const lf_batch* batch,
+                                const lf_output* out, void* stream);
+
 /* Stage dumps of the plain form for debugging and parity tests:
  * win_begin/win_count [n_tracks*12] (int32), n_trip [n_tracks] (int32),
  * trip [n_tracks*n_triplets*4] (int32 cfg, h0, h1, h2; packed indices),

@@ -109,8 +109,13 @@ _lib.lf_process_host.argtypes = [_P, C.POINTER(lf_host_batch), C.POINTER(lf_host
                                  C.c_int64]
 _lib.lf_process_host.restype = C.c_int
 
+_lib.lf_find_tracks_static.argtypes = [C.POINTER(lf_geometry), C.POINTER(lf_params), C.POINTER(lf_batch),
+                                       C.POINTER(lf_output), _P]
+_lib.lf_find_tracks_static.restype = C.c_int
+
 EXPORTED = ["lf_create", "lf_destroy", "lf_last_error", "lf_device_sm_count", "lf_pack_hits", "lf_find_tracks",
-            "lf_find_tracks_batched", "lf_debug_stages", "lf_sync_status", "lf_process_host"]
+            "lf_find_tracks_batched", "lf_debug_stages", "lf_sync_status", "lf_process_host",
+            "lf_find_tracks_static"]
 
 
 class LFError(RuntimeError):
@@ -218,6 +223,15 @@ def lf_process_host(ctx, batch: lf_host_batch, out: lf_host_output, tuning: Opti
                     chunk_hits: int = 0) -> None:
     tp = C.byref(tuning) if tuning is not None else None
     _check(ctx, _lib.lf_process_host(ctx, C.byref(batch), C.byref(out), tp, C.c_int64(chunk_hits)))
+
+
+def lf_find_tracks_static(geometry: dict, params: dict, batch: lf_batch, out: lf_output, stream) -> None:
+    """Context-free persistent form for callers that cannot allocate device
+    memory (scratch is a fixed static device array; see include/lf.h)."""
+    g, p = _geometry(geometry), _params(params)
+    st = _lib.lf_find_tracks_static(C.byref(g), C.byref(p), C.byref(batch), C.byref(out), stream)
+    if st != LF_OK:
+        raise LFError(st, "lf_find_tracks_static")
 
 
 def lf_sync_status(ctx, stream) -> int:
