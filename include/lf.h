@@ -146,9 +146,14 @@ typedef struct {
  * zeros select the defaults). */
 typedef struct {
     int32_t warps_per_block;   /* 1..16 */
-    int32_t blocks_per_sm;     /* resident blocks per SM of the persistent grid */
-    int32_t grain;             /* input tracks taken from the work queue at a time */
-    int32_t reserved;
+    int32_t blocks_per_sm;     /* resident blocks per SM of the persistent grid (0: as many as fit) */
+    int32_t grain;             /* tile kernel: input tracks per warp per step, 1 or 2 (default when
+                                  n_triplets <= 16: the extension runs two tracks per warp, 16 lanes each) */
+    int32_t queue;             /* 0: pipeline of persistent stage kernels (windows, triplets, extension,
+                                  selection), each draining its own device work queue (default);
+                                  1: one tile kernel, blocks take tiles of tracks and their warps step
+                                  through the stages together; 2: the tile kernel, warps take their
+                                  own tracks */
 } lf_tuning;
 
 /* Create a context: validates and copies geometry and parameters.
@@ -175,9 +180,10 @@ lf_status lf_pack_hits(lf_ctx* ctx, const lf_raw_hits* raw, const lf_packed* pac
  * context scratch. */
 lf_status lf_find_tracks(lf_ctx* ctx, const lf_batch* batch, const lf_output* out, void* stream);
 
-/* Persistent form: one fused kernel over a device work queue of input-track
- * grains, then compaction; launched through a CUDA graph captured per
- * launch shape.  tuning may be NULL (defaults).  Results are identical to
+/* Persistent form: persistent kernels over device work queues (by default a
+ * pipeline of one persistent kernel per stage; see lf_tuning.queue), then
+ * compaction; launched through a CUDA graph captured per launch shape and
+ * batch buffers.  tuning may be NULL (defaults).  Results are identical to
  * lf_find_tracks. */
 lf_status lf_find_tracks_batched(lf_ctx* ctx, const lf_batch* batch, const lf_output* out,
                                  const lf_tuning* tuning, void* stream);

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <cstdint>
 #include <map>
 #include <tuple>
 #include <vector>
@@ -36,7 +37,9 @@ struct lf_ctx {
     int n_sm = 0;
     char err[512] = {0};
     int* status = nullptr;   // device status word
-    int* cursor = nullptr;   // device work-queue cursor
+    int* cursor = nullptr;   // device work-queue cursors (8 ints)
+    unsigned long long generation = 0;  // bumped whenever scratch is reallocated
+    int stage_bps[4] = {0, 0, 0, 0};
     DevBuf trk_event, wbeg, wcnt, keys, ntrip, cands, ev_count, tmp, big_list;
     struct GraphEntry {
         cudaGraphExec_t exec = nullptr;
@@ -71,6 +74,7 @@ lf_status fail(lf_ctx* c, lf_status s, const char* fmt, ...) {
 lf_status ensure(lf_ctx* c, DevBuf& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.cap >= bytes) return LF_OK;
+    ++c->generation;
     if (b.p) {
         cudaError_t e = cudaFree(b.p);  // synchronises: no call of this context is in flight
         if (e != cudaSuccess) return fail(c, LF_ERR_CUDA, "cudaFree: %s", cudaGetErrorString(e));
@@ -241,7 +245,7 @@ lf_status lf_create(const lf_geometry* geometry, const lf_params* params, lf_ctx
         delete c;
         return LF_ERR_CUDA;
     }
-    if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess || cudaMalloc(&c->cursor, sizeof(int)) != cudaSuccess ||
+    if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess || cudaMalloc(&c->cursor, 8 * sizeof(int)) != cudaSuccess ||
         cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) {
         cudaFree(c->status);
         cudaFree(c->cursor);
@@ -291,7 +295,7 @@ lf_status lf_pack_hits(lf_ctx* c, const lf_raw_hits* raw, const lf_packed* pk, v
     cudaStream_t s = (cudaStream_t)stream;
     lf_status st;
     if ((st = ensure(c, c->tmp, (size_t)raw->n_hits * 4)) != LF_OK) return st;
-    if ((st = ensure(c, c->big_list, ((size_t)raw->n_events * NB + 1) * 4)) != LF_OK) return st;
+    if ((st = ensure(c, c->big_list, 2 * ((size_t)raw->n_events * NB + 1) * 4)) != LF_OK) return st;
     LF_CUDA(c, launch_pack(raw->raw_offsets, raw->x, raw->z, raw->dxdy, raw->w, raw->plane, raw->n_events,
                            raw->n_hits, pk->hit_offsets, pk->x, pk->z, pk->dxdy, pk->w, pk->layer, pk->perm,
                            (int*)c->tmp.p, (int*)c->big_list.p, c->status, c->n_sm, s));
@@ -321,31 +325,81 @@ lf_status lf_find_tracks(lf_ctx* c, const lf_batch* b, const lf_output* o, void*
 namespace {
 
 struct Shape {
-    int wpb, bps, grain;
+    int wpb, bps, grain, queue;
 };
 
 lf_status resolve_shape(lf_ctx* c, const lf_tuning* tuning, Shape& sh) {
+    sh.queue = tuning ? tuning->queue : 0;
+    if (sh.queue < 0 || sh.queue > 2) return fail(c, LF_ERR_ARG, "queue mode %d outside 0..2", sh.queue);
     sh.wpb = tuning && tuning->warps_per_block > 0 ? tuning->warps_per_block : 8;
-    sh.grain = tuning && tuning->grain > 0 ? tuning->grain : 4;
+    sh.grain = (tuning && tuning->grain > 0 ? (tuning->grain & 15) : 0) + (sh.queue == 1 ? 16 : 0);
     if (sh.wpb > 16) return fail(c, LF_ERR_ARG, "warps_per_block %d above 16", sh.wpb);
+    if (sh.queue == 0) {
+        if (!c->stage_bps[0]) LF_CUDA(c, stage_blocks_per_sm(c->kp, c->stage_bps));
+        sh.bps = tuning && tuning->blocks_per_sm > 0 ? tuning->blocks_per_sm : 0;
+        return LF_OK;
+    }
     int max_bps = 0;
-    LF_CUDA(c, fused_max_blocks_per_sm(c->kp, sh.wpb, &max_bps));
+    LF_CUDA(c, fused_max_blocks_per_sm(c->kp, sh.wpb, sh.grain, &max_bps));
     if (max_bps < 1) return fail(c, LF_ERR_ARG, "launch shape does not fit on an SM");
     sh.bps = tuning && tuning->blocks_per_sm > 0 ? tuning->blocks_per_sm : max_bps;
     if (sh.bps > max_bps) sh.bps = max_bps;
     return LF_OK;
 }
 
-// persistent form without a graph: queue reset, fused kernel, compaction
-lf_status batched_direct(lf_ctx* c, const lf_batch* b, const lf_output* o, const Shape& sh, cudaStream_t s) {
+// scratch of the persistent form, allocated before any capture
+lf_status prepare_batched(lf_ctx* c, const lf_batch* b, const Shape& sh) {
     lf_status st;
     if ((st = ensure(c, c->ev_count, (size_t)b->n_events * 4)) != LF_OK) return st;
-    LF_CUDA(c, cudaMemsetAsync(c->cursor, 0, sizeof(int), s));
-    if (b->n_tracks > 0)
-        LF_CUDA(c, launch_fused(c->kp, to_kbatch(b), to_kout(o), c->cursor, sh.grain, sh.wpb, sh.bps * c->n_sm, s));
+    if (sh.queue == 0) {
+        const size_t nt = (size_t)b->n_tracks, NT = (size_t)(c->p.n_triplets > 0 ? c->p.n_triplets : 1);
+        if ((st = ensure(c, c->trk_event, nt * 4)) != LF_OK) return st;
+        if ((st = ensure(c, c->wbeg, nt * NL * 4)) != LF_OK) return st;
+        if ((st = ensure(c, c->wcnt, nt * NL)) != LF_OK) return st;
+        if ((st = ensure(c, c->keys, nt * NT * 8)) != LF_OK) return st;
+        if ((st = ensure(c, c->ntrip, nt)) != LF_OK) return st;
+        if ((st = ensure(c, c->cands, nt * NT * sizeof(CandRec))) != LF_OK) return st;
+    }
+    return LF_OK;
+}
+
+int stage_grid(lf_ctx* c, const Shape& sh, int i) {
+    int bps = sh.bps > 0 && sh.bps < c->stage_bps[i] ? sh.bps : c->stage_bps[i];
+    return (bps > 0 ? bps : 1) * c->n_sm;
+}
+
+// persistent form, launches only (scratch prepared): queue reset, the stage
+// pipeline or the tile kernel, compaction
+lf_status launch_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const Shape& sh, cudaStream_t s) {
+    KBatch kb = to_kbatch(b);
+    KOut ko = to_kout(o);
+    LF_CUDA(c, cudaMemsetAsync(c->cursor, 0, 8 * sizeof(int), s));
+    if (b->n_tracks > 0) {
+        if (sh.queue == 0) {
+            auto* te = (int*)c->trk_event.p;
+            auto* wb = (int*)c->wbeg.p;
+            auto* wc = (uint8_t*)c->wcnt.p;
+            auto* ky = (uint64_t*)c->keys.p;
+            auto* nt = (uint8_t*)c->ntrip.p;
+            auto* cd = (CandRec*)c->cands.p;
+            LF_CUDA(c, launch_track_event(kb, te, s));
+            LF_CUDA(c, launch_windows(c->kp, kb, te, wb, wc, s, c->cursor + 0, stage_grid(c, sh, 0)));
+            LF_CUDA(c, launch_triplets(c->kp, kb, te, wb, wc, ky, nt, s, c->cursor + 1, stage_grid(c, sh, 1)));
+            LF_CUDA(c, launch_extend(c->kp, kb, te, wb, wc, ky, nt, cd, s, c->cursor + 2, stage_grid(c, sh, 2)));
+            LF_CUDA(c, launch_select(c->kp, kb, wb, nt, cd, ko, s, c->cursor + 3, stage_grid(c, sh, 3)));
+        } else {
+            LF_CUDA(c, launch_fused(c->kp, kb, ko, c->cursor, sh.grain, sh.wpb, sh.bps * c->n_sm, s));
+        }
+    }
     LF_CUDA(c, launch_compact(b->trk_offsets, o->found, b->n_events, (int*)c->ev_count.p, o->out_offsets, o->out_trk,
                               o->n_out, s));
     return LF_OK;
+}
+
+lf_status batched_direct(lf_ctx* c, const lf_batch* b, const lf_output* o, const Shape& sh, cudaStream_t s) {
+    lf_status st = prepare_batched(c, b, sh);
+    if (st != LF_OK) return st;
+    return launch_batched(c, b, o, sh, s);
 }
 
 }  // namespace
@@ -357,41 +411,30 @@ lf_status lf_find_tracks_batched(lf_ctx* c, const lf_batch* b, const lf_output* 
     if ((st = check_batch(c, b)) != LF_OK) return st;
     if ((st = check_out(c, o, b->n_tracks)) != LF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    int wpb = tuning && tuning->warps_per_block > 0 ? tuning->warps_per_block : 8;
-    int grain = tuning && tuning->grain > 0 ? tuning->grain : 4;
-    if (wpb > 16) return fail(c, LF_ERR_ARG, "warps_per_block %d above 16", wpb);
-    int max_bps = 0;
-    LF_CUDA(c, fused_max_blocks_per_sm(c->kp, wpb, &max_bps));
-    if (max_bps < 1) return fail(c, LF_ERR_ARG, "launch shape does not fit on an SM");
-    int bps = tuning && tuning->blocks_per_sm > 0 ? tuning->blocks_per_sm : max_bps;
-    if (bps > max_bps) bps = max_bps;
-    if ((st = ensure(c, c->ev_count, (size_t)b->n_events * 4)) != LF_OK) return st;
+    Shape sh;
+    if ((st = resolve_shape(c, tuning, sh)) != LF_OK) return st;
+    if ((st = prepare_batched(c, b, sh)) != LF_OK) return st;
 
     GraphKey key;
-    key.v = std::make_tuple(wpb, bps, grain, b->n_events, b->n_tracks, b->n_hits, (const void*)b->hit_offsets,
-                            (const void*)b->x, (const void*)b->trk_offsets, (const void*)b->sx, (const void*)o->found,
-                            (const void*)o->out_trk, (const void*)c->ev_count.p);
+    key.v = std::make_tuple(sh.wpb, sh.bps, sh.grain + 64 * sh.queue, b->n_events, b->n_tracks, b->n_hits,
+                            (const void*)b->hit_offsets, (const void*)b->x, (const void*)b->trk_offsets,
+                            (const void*)b->sx, (const void*)o->found, (const void*)o->out_trk,
+                            (const void*)(uintptr_t)c->generation);
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
-        // capture: queue reset, persistent kernel, compaction
         cudaStream_t cap;
         LF_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->cursor, 0, sizeof(int), cap);
-        KBatch kb = to_kbatch(b);
-        KOut ko = to_kout(o);
-        if (e == cudaSuccess && b->n_tracks > 0)
-            e = launch_fused(c->kp, kb, ko, c->cursor, grain, wpb, bps * c->n_sm, cap);
-        if (e == cudaSuccess)
-            e = launch_compact(b->trk_offsets, o->found, b->n_events, (int*)c->ev_count.p, o->out_offsets, o->out_trk,
-                               o->n_out, cap);
+        lf_status ls = LF_OK;
+        if (e == cudaSuccess) ls = launch_batched(c, b, o, sh, cap);
         cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
         if (e == cudaSuccess) e = e2;
         cudaGraphExec_t exec = nullptr;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess && ls == LF_OK) e = cudaGraphInstantiate(&exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         cudaStreamDestroy(cap);
+        if (ls != LF_OK) return ls;
         if (e != cudaSuccess) return fail(c, LF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
         // keep a bounded cache of shapes
         if (c->graphs.size() >= 64) {
@@ -449,12 +492,12 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
     if (hb->n_events == 0) return LF_OK;
     if (chunk_hits <= 0) chunk_hits = (int64_t)1 << 26;
     lf_status st;
-    Shape sh;
-    if ((st = resolve_shape(c, tuning, sh)) != LF_OK) return st;
+    Shape shs[2];
     for (int i = 0; i < 2; ++i) {
         if (!c->sub[i] && (st = lf_create(&c->g, &c->p, &c->sub[i])) != LF_OK)
             return fail(c, st, "sub-context creation failed");
         if (!c->pipe_stream[i]) LF_CUDA(c, cudaStreamCreateWithFlags(&c->pipe_stream[i], cudaStreamNonBlocking));
+        if ((st = resolve_shape(c->sub[i], tuning, shs[i])) != LF_OK) return fail(c, st, "%s", c->sub[i]->err);
     }
     // chunk boundaries at event boundaries
     std::vector<int> cut{0};
@@ -488,7 +531,7 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
     }
     // device arena per slot
     auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
-    size_t off_raw = 0, sz = 0;
+    size_t sz = 0;
     size_t o_x = sz; sz += al(4 * H);
     size_t o_z = sz; sz += al(4 * H);
     size_t o_d = sz; sz += al(4 * H);
@@ -512,7 +555,6 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
     size_t o_oo = sz; sz += al(4 * (E + 1));
     size_t o_ot = sz; sz += al(4 * (T + 1));
     size_t o_no = sz; sz += al(4);
-    (void)off_raw;
     for (int i = 0; i < 2; ++i) {
         if ((st = ensure(c, c->arena[i], sz)) != LF_OK) {
             cudaFreeHost(pin);
@@ -554,7 +596,7 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
                     (const float*)(A + o_st + 12 * T), (const float*)(A + o_st + 16 * T)};
         lf_output out{(uint8_t*)(A + o_fd), (uint8_t*)(A + o_nh), (int32_t*)(A + o_hi), (float*)(A + o_sv),
                       (float*)(A + o_q), (int32_t*)(A + o_oo), (int32_t*)(A + o_ot), (int32_t*)(A + o_no)};
-        if ((rc = batched_direct(sc, &bt, &out, sh, s)) != LF_OK) break;
+        if ((rc = batched_direct(sc, &bt, &out, shs[slot], s)) != LF_OK) break;
         ce = launch_hits_to_raw(out.found, out.hit_idx, pk.perm, nt, h0, s);
         auto back = [&](void* dst, size_t src, size_t bytes) {
             if (ce == cudaSuccess && bytes && dst) ce = cudaMemcpyAsync(dst, A + src, bytes, cudaMemcpyDeviceToHost, s);

@@ -59,19 +59,30 @@ struct CandRec {
 };
 static_assert(sizeof(CandRec) == 48, "CandRec layout");
 
-// Per-warp shared-memory block: window descriptors, the flattened doublet
-// enumeration, then the staged window hits (x, z, dxdy, w), 12 x cap each.
-struct WarpHead {
+constexpr int PAIR_CAP = 512;   // (h0, h2) pairs materialised at a time per warp
+constexpr int CAND_CAP = 64;    // passing triplet keys buffered per warp before a selection
+
+// Shared-memory block of one track: window descriptors, then the staged
+// window hits (x and z), 12 x cap each.  dxdy and w of the hits a candidate
+// uses are read from global memory (L2) by the extension.
+struct SlotHead {
     int wbeg[NL];
     int wcnt[NL];
     int zuni[NL];
-    int pre[2 * MAX_CAP];   // exclusive prefix of the h2-interval sizes, per (cfg, h0) item
-    int aa[2 * MAX_CAP];    // first h2 of each item's interval
+    int pad[4];
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
-__host__ __device__ inline size_t warp_smem_bytes(int cap) {
-    return align16(sizeof(WarpHead)) + size_t(4) * NL * cap * sizeof(float);
+__host__ __device__ inline size_t slot_bytes(int cap) {
+    return align16(sizeof(SlotHead)) + size_t(2) * NL * cap * sizeof(float);
+}
+// per-warp scratch of the triplet stage: key buffer and materialised pairs
+__host__ __device__ inline size_t scratch_bytes() {
+    return align16(CAND_CAP * sizeof(unsigned long long) + PAIR_CAP * sizeof(unsigned short));
+}
+// shared memory of a block of nw warps holding tpw tracks per warp
+__host__ __device__ inline size_t block_smem_bytes(int cap, int nw, int tpw) {
+    return size_t(nw) * tpw * slot_bytes(cap) + size_t(nw) * scratch_bytes();
 }
 
 // ---- launchers (defined in the .cu files) ----
@@ -81,18 +92,25 @@ cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, 
                         int* perm, int* tmp, int* big_list, int* status, int n_sm, cudaStream_t s);
 
 cudaError_t launch_track_event(const KBatch& b, int* trk_event, cudaStream_t s);
+// stage kernels: cursor == nullptr launches the plain one-pass grid,
+// otherwise a persistent grid of `blocks` blocks draining the stage's queue
 cudaError_t launch_windows(const KParams& k, const KBatch& b, const int* trk_event, int* wbeg, uint8_t* wcnt,
-                           cudaStream_t s);
+                           cudaStream_t s, int* cursor = nullptr, int blocks = 0);
 cudaError_t launch_triplets(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
-                            const uint8_t* wcnt, uint64_t* keys, uint8_t* ntrip, cudaStream_t s);
+                            const uint8_t* wcnt, uint64_t* keys, uint8_t* ntrip, cudaStream_t s,
+                            int* cursor = nullptr, int blocks = 0);
 cudaError_t launch_extend(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
                           const uint8_t* wcnt, const uint64_t* keys, const uint8_t* ntrip, CandRec* cands,
-                          cudaStream_t s);
+                          cudaStream_t s, int* cursor = nullptr, int blocks = 0);
 cudaError_t launch_select(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* ntrip,
-                          const CandRec* cands, const KOut& o, cudaStream_t s);
+                          const CandRec* cands, const KOut& o, cudaStream_t s, int* cursor = nullptr,
+                          int blocks = 0);
+cudaError_t stage_blocks_per_sm(const KParams& k, int* out4);
+// persistent tile kernel: grain = tracks per warp per tile (1 or 2; 0 picks 2
+// when n_triplets <= 16)
 cudaError_t launch_fused(const KParams& k, const KBatch& b, const KOut& o, int* cursor, int grain,
                          int warps_per_block, int n_blocks, cudaStream_t s);
-cudaError_t fused_max_blocks_per_sm(const KParams& k, int warps_per_block, int* out);
+cudaError_t fused_max_blocks_per_sm(const KParams& k, int warps_per_block, int grain, int* out);
 cudaError_t launch_hits_to_raw(const uint8_t* found, int* hit_idx, const int* perm, int n_tracks, int base,
                               cudaStream_t s);
 cudaError_t launch_compact(const int* trk_offsets, const uint8_t* found, int n_events, int* ev_count,

@@ -1,17 +1,22 @@
 // Hit packing for sm_103a: per event, bucket the raw hits by (zone, layer),
 // then sort every bucket by x (ties by raw index) and write the SoA.
 //
-//   k_pack_bucket   one block per event (grid-stride): shared-memory
-//                   histogram of the plane codes, exclusive scan into the
-//                   bucket offsets, scatter of raw indices into their bucket
-//                   (order inside a bucket is fixed by the sort that follows).
-//   k_pack_sort     one warp per bucket of at most WARP_SORT_MAX hits, one
-//                   block per larger bucket: a bin sort in shared memory.
-//                   Keys are the x values; bins split [min, max] of the bucket
-//                   into as many equal parts as hits (the bin index is a
-//                   monotone function of x), each bin is then ordered by
-//                   (x, raw index) with an insertion sort, so the result is
-//                   the exact (x, raw index) order whatever the data.
+//   k_pack_bucket   one block per event (grid-stride): each warp counts the
+//                   plane codes of its slice of the event (ranked with
+//                   __match_any_sync), a per-bucket prefix over buckets and
+//                   warps gives the bucket offsets and each warp's cursors,
+//                   and each warp scatters its slice in order: a STABLE
+//                   scatter, so inside a bucket raw indices stay ascending.
+//   k_pack_sort     one block per event (grid-stride), so the event's raw
+//                   hits stay hot in L1/L2 while all its buckets are sorted:
+//                   buckets of at most 1024 hits by one warp each, larger
+//                   ones (at most 8192) by the whole block; a bin sort in
+//                   shared memory.
+//                   Bins split [min, max] of the bucket into as many equal
+//                   parts as hits (the bin is a monotone function of x); each
+//                   bin is then ordered by (x, position) with an insertion
+//                   sort; positions follow raw order, so the result is the
+//                   exact (x, raw index) order whatever the data.
 //   The sorted bucket is written out coalesced: x, z, dxdy, w, layer, perm.
 #include <cstdint>
 
@@ -22,6 +27,10 @@ namespace lfk {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int BUCKET_THREADS = 256;
+constexpr int BUCKET_WARPS = BUCKET_THREADS / 32;
+constexpr int WARP_MAX = 1024;      // bucket size sorted by one warp
+constexpr int SORT_THREADS = 256;   // 8 warps: 8 warp areas of WARP_MAX == one block area of BLOCK_SORT_MAX
 
 __device__ __forceinline__ int wscan_incl(int v, int lane) {
 #pragma unroll
@@ -32,58 +41,71 @@ __device__ __forceinline__ int wscan_incl(int v, int lane) {
     return v;
 }
 
-__global__ void k_pack_bucket(const int* __restrict__ raw_offsets, const uint8_t* __restrict__ plane, int n_events,
-                              int* hit_offsets, int* tmp, int* big_list, int* status) {
-    __shared__ int cnt[NB], cur[NB];
-    const int tid = threadIdx.x;
+__global__ void __launch_bounds__(BUCKET_THREADS) k_pack_bucket(
+    const int* __restrict__ raw_offsets, const uint8_t* __restrict__ plane, int n_events, int* hit_offsets,
+    int* tmp, int* status) {
+    __shared__ int wc[BUCKET_WARPS][NB];   // per-warp counts, then per-warp cursors
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = blockIdx.x; e < n_events; e += gridDim.x) {
-        if (tid < NB) cnt[tid] = 0;
-        __syncthreads();
         const int rb = raw_offsets[e], re = raw_offsets[e + 1];
-        for (int i = rb + tid; i < re; i += blockDim.x) {
-            int p = plane[i];
-            if (p >= NB) {
-                atomicOr(status, 0x2);
-                p = NB - 1;
+        const int slice = ((re - rb + BUCKET_WARPS - 1) / BUCKET_WARPS + 31) & ~31;
+        const int s0 = min(rb + warp * slice, re), s1 = min(s0 + slice, re);
+        if (lane < NB) wc[warp][lane] = 0;
+        __syncwarp();
+        for (int base = s0; base < s1; base += 32) {
+            int i = base + lane;
+            int p = -1;
+            if (i < s1) {
+                p = plane[i];
+                if (p >= NB) {
+                    atomicOr(status, 0x2);
+                    p = NB - 1;
+                }
             }
-            atomicAdd(&cnt[p], 1);
+            unsigned peers = __match_any_sync(FULL, p);
+            if (p >= 0 && lane == __ffs(peers) - 1) wc[warp][p] += __popc(peers);
+            __syncwarp();
         }
         __syncthreads();
-        if (tid == 0) {
-            int acc = rb;
-            for (int q = 0; q < NB; ++q) {
-                hit_offsets[(size_t)e * NB + q] = acc;
-                cur[q] = acc;
-                int c = cnt[q];
-                if (c > BLOCK_SORT_MAX) atomicOr(status, 0x1);
-                else if (c > WARP_SORT_MAX) big_list[1 + atomicAdd(big_list, 1)] = e * NB + q;
-                acc += c;
+        if (tid < 32) {
+            // bucket totals, their exclusive scan, then each warp's cursor
+            int tot = 0;
+            if (lane < NB)
+                for (int w = 0; w < BUCKET_WARPS; ++w) tot += wc[w][lane];
+            int inc = wscan_incl(tot, lane);
+            int start = rb + inc - tot;
+            if (lane < NB) {
+                hit_offsets[(size_t)e * NB + lane] = start;
+                if (tot > BLOCK_SORT_MAX) atomicOr(status, 0x1);
+                int acc = start;
+                for (int w = 0; w < BUCKET_WARPS; ++w) {
+                    int c = wc[w][lane];
+                    wc[w][lane] = acc;
+                    acc += c;
+                }
             }
         }
         __syncthreads();
-        for (int i = rb + tid; i < re; i += blockDim.x) {
-            int p = plane[i];
-            if (p >= NB) p = NB - 1;
-            int pos = atomicAdd(&cur[p], 1);
-            tmp[pos] = i;
+        for (int base = s0; base < s1; base += 32) {
+            int i = base + lane;
+            int p = -1;
+            if (i < s1) {
+                p = plane[i];
+                if (p >= NB) p = NB - 1;
+            }
+            unsigned peers = __match_any_sync(FULL, p);
+            int rank = __popc(peers & ((1u << lane) - 1u));
+            int cur = p >= 0 ? wc[warp][p] : 0;
+            __syncwarp();
+            if (p >= 0) {
+                tmp[cur + rank] = i;
+                if (rank == 0) wc[warp][p] = cur + __popc(peers);
+            }
+            __syncwarp();
         }
         __syncthreads();
     }
     if (blockIdx.x == 0 && tid == 0) hit_offsets[(size_t)n_events * NB] = raw_offsets[n_events];
-}
-
-// Work area of one bucket sort: keys (x), raw indices, their sorted copies
-// and the bin counters, n entries each.
-struct SortArea {
-    float* xa;
-    int* ra;
-    float* xb;
-    int* rb;
-    int* bins;
-};
-
-__device__ __forceinline__ bool before(float xa, int ra, float xb, int rb) {
-    return xa < xb || (xa == xb && ra < rb);
 }
 
 __device__ __forceinline__ int bin_of(float x, float xmin, float scale, int nb) {
@@ -93,25 +115,30 @@ __device__ __forceinline__ int bin_of(float x, float xmin, float scale, int nb) 
     return (int)f;
 }
 
-// Group-cooperative bin sort; G is a warp (32 lanes, __syncwarp) or a block.
 template <bool BLOCK>
 __device__ __forceinline__ void gsync() {
     if (BLOCK) __syncthreads(); else __syncwarp();
 }
 
+// Work area of one bucket sort (m entries each): keys x, bin counters, and
+// the positions (0..m-1, raw order inside the bucket) in sorted order.
+struct SortArea {
+    float* xa;
+    int* bins;
+    uint16_t* pos;
+};
+
+// Cooperative bin sort of one bucket by a warp (BLOCK = false) or a block.
 template <bool BLOCK>
 __device__ void sort_bucket(const float* __restrict__ x, const float* __restrict__ z, const float* __restrict__ dxdy,
                             const float* __restrict__ w, const int* __restrict__ tmp, int b0, int m, int layer,
                             float* ox, float* oz, float* od, float* ow, uint8_t* ol, int* perm, SortArea a,
                             int rank, int size, float* red_f, int* red_i) {
     const int lane = rank & 31, wid = rank >> 5, nw = size >> 5;
-    // load keys, min / max
     float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
     for (int i = rank; i < m; i += size) {
-        int r = tmp[b0 + i];
-        float xv = __ldg(x + r) + 0.0f;
+        float xv = __ldg(x + tmp[b0 + i]) + 0.0f;
         a.xa[i] = xv;
-        a.ra[i] = r;
         lo = fminf(lo, xv);
         hi = fmaxf(hi, xv);
     }
@@ -139,8 +166,8 @@ __device__ void sort_bucket(const float* __restrict__ x, const float* __restrict
     gsync<BLOCK>();
     for (int i = rank; i < m; i += size) atomicAdd(&a.bins[bin_of(a.xa[i], lo, scale, nb)], 1);
     gsync<BLOCK>();
-    // exclusive scan of the bin counts: contiguous chunk per thread
     {
+        // exclusive scan of the bin counts: a contiguous chunk per thread
         const int per = (nb + size - 1) / size;
         const int s0 = min(rank * per, nb), s1 = min(s0 + per, nb);
         int sum = 0;
@@ -161,33 +188,31 @@ __device__ void sort_bucket(const float* __restrict__ x, const float* __restrict
         }
     }
     gsync<BLOCK>();
-    for (int i = rank; i < m; i += size) {
-        int pos = atomicAdd(&a.bins[bin_of(a.xa[i], lo, scale, nb)], 1);
-        a.xb[pos] = a.xa[i];
-        a.rb[pos] = a.ra[i];
-    }
+    for (int i = rank; i < m; i += size) a.pos[atomicAdd(&a.bins[bin_of(a.xa[i], lo, scale, nb)], 1)] = (uint16_t)i;
     gsync<BLOCK>();
-    // bins[b] is now the end of bin b; order each bin by (x, raw index)
+    // bins[b] is now the end of bin b; order each bin by (x, position)
     for (int bn = rank; bn < nb; bn += size) {
         int s = bn ? a.bins[bn - 1] : 0, e = a.bins[bn];
         for (int i = s + 1; i < e; ++i) {
-            float xv = a.xb[i];
-            int rv = a.rb[i];
+            int pv = a.pos[i];
+            float xv = a.xa[pv];
             int j = i - 1;
-            while (j >= s && before(xv, rv, a.xb[j], a.rb[j])) {
-                a.xb[j + 1] = a.xb[j];
-                a.rb[j + 1] = a.rb[j];
+            while (j >= s) {
+                int pj = a.pos[j];
+                float xj = a.xa[pj];
+                if (!(xv < xj || (xv == xj && pv < pj))) break;
+                a.pos[j + 1] = (uint16_t)pj;
                 --j;
             }
-            a.xb[j + 1] = xv;
-            a.rb[j + 1] = rv;
+            a.pos[j + 1] = (uint16_t)pv;
         }
     }
     gsync<BLOCK>();
     for (int i = rank; i < m; i += size) {
-        int r = a.rb[i];
+        int pv = a.pos[i];
+        int r = tmp[b0 + pv];
         size_t o = (size_t)b0 + i;
-        ox[o] = a.xb[i];
+        ox[o] = a.xa[pv];
         oz[o] = __ldg(z + r);
         od[o] = __ldg(dxdy + r);
         ow[o] = __ldg(w + r);
@@ -197,49 +222,45 @@ __device__ void sort_bucket(const float* __restrict__ x, const float* __restrict
     gsync<BLOCK>();
 }
 
-constexpr int SORT_WARPS = 4;
+__host__ __device__ constexpr size_t area_bytes(int n) { return (size_t)n * 4 + (size_t)n * 4 + (((size_t)n * 2 + 15) & ~size_t(15)); }
 
-__global__ void __launch_bounds__(SORT_WARPS * 32) k_pack_sort_warp(
-    const float* __restrict__ x, const float* __restrict__ z, const float* __restrict__ dxdy,
-    const float* __restrict__ w, const int* __restrict__ hit_offsets, const int* __restrict__ tmp, int n_buckets,
-    float* ox, float* oz, float* od, float* ow, uint8_t* ol, int* perm) {
-    extern __shared__ __align__(16) char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    char* base = smem + (size_t)warp * WARP_SORT_MAX * 20;
+__device__ __forceinline__ SortArea area_at(char* p, int n) {
     SortArea a;
-    a.xa = reinterpret_cast<float*>(base);
-    a.ra = reinterpret_cast<int*>(base + WARP_SORT_MAX * 4);
-    a.xb = reinterpret_cast<float*>(base + WARP_SORT_MAX * 8);
-    a.rb = reinterpret_cast<int*>(base + WARP_SORT_MAX * 12);
-    a.bins = reinterpret_cast<int*>(base + WARP_SORT_MAX * 16);
-    const int gw = blockIdx.x * SORT_WARPS + warp, nwarps = gridDim.x * SORT_WARPS;
-    for (int q = gw; q < n_buckets; q += nwarps) {
-        int b0 = hit_offsets[q], m = hit_offsets[q + 1] - b0;
-        if (m == 0 || m > WARP_SORT_MAX) continue;
-        sort_bucket<false>(x, z, dxdy, w, tmp, b0, m, (q % NB) % NL, ox, oz, od, ow, ol, perm, a, lane, 32, nullptr,
-                           nullptr);
-    }
+    a.xa = reinterpret_cast<float*>(p);
+    a.bins = reinterpret_cast<int*>(p + (size_t)n * 4);
+    a.pos = reinterpret_cast<uint16_t*>(p + (size_t)n * 8);
+    return a;
 }
 
-__global__ void __launch_bounds__(BLOCK_SORT_THREADS) k_pack_sort_block(
+// One block per event: small buckets by the block's warps (each with its own
+// shared-memory area), then the large ones by the whole block (the union of
+// the warps' areas), so the event's raw hits are read while hot.
+__global__ void __launch_bounds__(SORT_THREADS) k_pack_sort(
     const float* __restrict__ x, const float* __restrict__ z, const float* __restrict__ dxdy,
-    const float* __restrict__ w, const int* __restrict__ hit_offsets, const int* __restrict__ tmp,
-    const int* __restrict__ big_list, float* ox, float* oz, float* od, float* ow, uint8_t* ol, int* perm) {
+    const float* __restrict__ w, const int* __restrict__ hit_offsets, const int* __restrict__ tmp, int n_events,
+    float* ox, float* oz, float* od, float* ow, uint8_t* ol, int* perm) {
     extern __shared__ __align__(16) char smem[];
     __shared__ float red_f[64];
     __shared__ int red_i[32];
-    SortArea a;
-    a.xa = reinterpret_cast<float*>(smem);
-    a.ra = reinterpret_cast<int*>(smem + BLOCK_SORT_MAX * 4);
-    a.xb = reinterpret_cast<float*>(smem + BLOCK_SORT_MAX * 8);
-    a.rb = reinterpret_cast<int*>(smem + BLOCK_SORT_MAX * 12);
-    a.bins = reinterpret_cast<int*>(smem + BLOCK_SORT_MAX * 16);
-    const int n_big = big_list[0];
-    for (int k = blockIdx.x; k < n_big; k += gridDim.x) {
-        int q = big_list[1 + k];
-        int b0 = hit_offsets[q], m = hit_offsets[q + 1] - b0;
-        sort_bucket<true>(x, z, dxdy, w, tmp, b0, m, (q % NB) % NL, ox, oz, od, ow, ol, perm, a, threadIdx.x,
-                          blockDim.x, red_f, red_i);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const SortArea wa = area_at(smem + (size_t)warp * area_bytes(WARP_MAX), WARP_MAX);
+    const SortArea ba = area_at(smem, BLOCK_SORT_MAX);
+    for (int e = blockIdx.x; e < n_events; e += gridDim.x) {
+        const int* off = hit_offsets + (size_t)e * NB;
+        for (int q = warp; q < NB; q += SORT_THREADS / 32) {
+            int b0 = off[q], m = off[q + 1] - b0;
+            if (m >= 1 && m <= WARP_MAX)
+                sort_bucket<false>(x, z, dxdy, w, tmp, b0, m, q % NL, ox, oz, od, ow, ol, perm, wa, lane, 32,
+                                   nullptr, nullptr);
+        }
+        __syncthreads();
+        for (int q = 0; q < NB; ++q) {
+            int b0 = off[q], m = off[q + 1] - b0;
+            if (m > WARP_MAX && m <= BLOCK_SORT_MAX)
+                sort_bucket<true>(x, z, dxdy, w, tmp, b0, m, q % NL, ox, oz, od, ow, ol, perm, ba, tid,
+                                  SORT_THREADS, red_f, red_i);
+        }
+        __syncthreads();
     }
 }
 
@@ -250,30 +271,19 @@ cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, 
                         int* hit_offsets, float* ox, float* oz, float* odxdy, float* ow, uint8_t* olayer,
                         int* perm, int* tmp, int* big_list, int* status, int n_sm, cudaStream_t s) {
     (void)n_hits;
-    cudaError_t err = cudaMemsetAsync(big_list, 0, sizeof(int), s);
-    if (err != cudaSuccess) return err;
-    if (n_events <= 0) {
-        return cudaMemsetAsync(hit_offsets, 0, sizeof(int), s);
-    }
+    (void)big_list;
+    if (n_events <= 0) return cudaMemsetAsync(hit_offsets, 0, sizeof(int), s);
     int grid = n_events < n_sm * 8 ? n_events : n_sm * 8;
-    k_pack_bucket<<<grid, 256, 0, s>>>(raw_offsets, plane, n_events, hit_offsets, tmp, big_list, status);
-    err = cudaGetLastError();
+    k_pack_bucket<<<grid, BUCKET_THREADS, 0, s>>>(raw_offsets, plane, n_events, hit_offsets, tmp, status);
+    cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    const int n_buckets = n_events * NB;
-    size_t smw = (size_t)SORT_WARPS * WARP_SORT_MAX * 20;
-    err = cudaFuncSetAttribute(k_pack_sort_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
-    if (err != cudaSuccess) return err;
-    int gw = (n_buckets + SORT_WARPS - 1) / SORT_WARPS;
-    if (gw > n_sm * 16) gw = n_sm * 16;
-    k_pack_sort_warp<<<gw, SORT_WARPS * 32, smw, s>>>(x, z, dxdy, w, hit_offsets, tmp, n_buckets, ox, oz, odxdy, ow,
-                                                      olayer, perm);
-    err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
-    size_t smb = (size_t)BLOCK_SORT_MAX * 20;
-    err = cudaFuncSetAttribute(k_pack_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
-    if (err != cudaSuccess) return err;
-    k_pack_sort_block<<<n_sm, BLOCK_SORT_THREADS, smb, s>>>(x, z, dxdy, w, hit_offsets, tmp, big_list, ox, oz, odxdy,
-                                                            ow, olayer, perm);
+    const size_t sm = area_bytes(BLOCK_SORT_MAX);
+    if ((err = cudaFuncSetAttribute(k_pack_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+        cudaSuccess)
+        return err;
+    int gs = n_events < n_sm * 2 ? n_events : n_sm * 2;
+    k_pack_sort<<<gs, SORT_THREADS, sm, s>>>(x, z, dxdy, w, hit_offsets, tmp, n_events, ox, oz, odxdy, ow, olayer,
+                                             perm);
     return cudaGetLastError();
 }
 

@@ -113,11 +113,11 @@ extern "C" lf_status lf_find_tracks_static(const lf_geometry* geometry, const lf
     cudaStream_t s = (cudaStream_t)stream;
     const lfk::KParams k = kparams(geometry, params);
     int dev = 0, n_sm = 0, bps = 0;
-    const int wpb = 8, grain = 4;
+    const int wpb = 8, grain = 16;  // block tiles, stage barriers, two tracks per warp
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return LF_ERR_CUDA;
-    if (lfk::fused_max_blocks_per_sm(k, wpb, &bps) != cudaSuccess || bps < 1) return LF_ERR_CUDA;
+    if (lfk::fused_max_blocks_per_sm(k, wpb, grain, &bps) != cudaSuccess || bps < 1) return LF_ERR_CUDA;
     int* cursor = scratch;
     int* ev_count = scratch + kScratchHead;
     if (cudaMemsetAsync(cursor, 0, sizeof(int), s) != cudaSuccess) return LF_ERR_CUDA;

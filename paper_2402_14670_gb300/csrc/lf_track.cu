@@ -1,15 +1,17 @@
 // Forward-tracking kernels for sm_103a.
 //
-// One warp follows one input track.  The stages are device functions shared
-// by the plain form (one kernel per stage, results in scratch) and the
-// persistent form (all stages in one kernel, results in shared memory and
-// registers, input-track grains taken from a device work queue).
+// A warp follows an input track.  The stages are device functions shared by
+// the plain form (one kernel per stage, results in scratch) and the
+// persistent form (k_tile: blocks take tiles of consecutive input tracks from
+// a device work queue and run the stages on them with results in shared
+// memory and registers; the warps of a block step through the stages
+// together, and the extension runs two tracks per warp).
 //
 //   windows    Sec. "Defining the search windows": lanes 0..11 each open one
 //              layer's window with binary searches in the x-sorted bucket.
-//   staging    the window hits (x, z, dxdy, w; <= n_hits_window per layer)
-//              are copied into the warp's shared-memory block with coalesced
-//              loads, once per track.
+//   staging    x and z of the window hits (<= n_hits_window per layer) are
+//              copied into the track's shared-memory slot, once per track;
+//              dxdy and w are read from L2 for the hits a candidate uses.
 //   triplets   Sec. "Triplet Seeding": for each h0 the h2 candidates that can
 //              pass the magnet-opening filter form an interval of the sorted
 //              window (bounded with the largest tolerance plus slack); the
@@ -20,14 +22,16 @@
 //              one per lane.  The exact filters on a superset give the same
 //              triplet set as enumerating every pair.
 //   extension  Sec. "Extending triplets to other layers" and "Quality Filter":
-//              lane r extends triplet r (three-point solution, missing x
-//              layers, weighted x refit, u/v layers, y line fit, Q).
+//              lane r of a 16- or 32-lane group extends triplet r
+//              (three-point solution, missing x layers, weighted x refit,
+//              u/v layers, y line fit, Q).
 //   selection  lowest Q among accepted candidates by a warp-wide minimum of
 //              (Q bits, rank); the winner's hits and state go out coalesced.
 //
 // Arithmetic: binary32, no contraction (built with -fmad=false), IEEE
 // division; every expression is written in the evaluation order of the
 // method's definition so that results do not depend on the launch shape.
+#include <climits>
 #include <cstdint>
 
 #include "lf_internal.h"
@@ -140,12 +144,10 @@ __device__ __forceinline__ float x_extrap(const KParams& k, const TState& s, int
     return (x_mag + t1) + t2 * t3;
 }
 
-// Window of layer l: [begin, begin+count) in packed hit indices.
-__device__ __forceinline__ void layer_window(const KParams& k, const KBatch& b, const TState& s, int e, int l,
-                                             int& begin, int& count) {
-    const int zone = (s.tys >= 0.0f) ? 1 : 0;
+// Limits and centre of the window of layer l.
+__device__ __forceinline__ void window_limits(const KParams& k, const TState& s, int l, float& xmin, float& xmax,
+                                              float& centre) {
     const float pmom = 1.0f / fabsf(s.qop);
-    float centre, xmin, xmax;
     if (is_x(l)) {
         float x_tol = k.xtol_c + k.xtol_p / pmom;
         bool qpos = s.qop >= 0.0f;
@@ -164,20 +166,39 @@ __device__ __forceinline__ void layer_window(const KParams& k, const KBatch& b, 
         xmin = centre - k.uv_tol;
         xmax = centre + k.uv_tol;
     }
+}
+
+// Windows of all twelve layers, [begin, begin+count) in packed hit indices,
+// returned on lanes 0..11: lanes 0..11 search the lower bounds and lanes
+// 12..23 the upper bounds in parallel, then lanes 0..11 apply the cap.
+__device__ __forceinline__ void warp_windows(const KParams& k, const KBatch& b, const TState& s, int e, int lane,
+                                             int& begin, int& count) {
+    const int zone = (s.tys >= 0.0f) ? 1 : 0;
+    const int l = lane < NL ? lane : (lane < 2 * NL ? lane - NL : 0);
+    float xmin, xmax, centre;
+    window_limits(k, s, l, xmin, xmax, centre);
     const int* off = b.hit_offsets + (size_t)e * NB + zone * NL + l;
-    int bb = __ldg(off), be = __ldg(off + 1);
-    int lo = lb_global(b.x, bb, be, xmin);
-    int hi = ub_global(b.x, lo, be, xmax);
-    int cnt = hi - lo, start = lo;
-    if (cnt > k.cap) {
-        int c = lb_global(b.x, lo, hi, centre);
-        start = c - k.cap / 2;
-        if (start > hi - k.cap) start = hi - k.cap;
-        if (start < lo) start = lo;
-        cnt = k.cap;
+    const int bb = __ldg(off), be = __ldg(off + 1);
+    int v = 0;
+    if (lane < NL) v = lb_global(b.x, bb, be, xmin);
+    else if (lane < 2 * NL) v = ub_global(b.x, bb, be, xmax);
+    int hi = __shfl_sync(FULL, v, (lane + NL) & 31);
+    begin = 0;
+    count = 0;
+    if (lane < NL) {
+        const int lo = v;
+        if (hi < lo) hi = lo;
+        int cnt = hi - lo, start = lo;
+        if (cnt > k.cap) {
+            int c = lb_global(b.x, lo, hi, centre);
+            start = c - k.cap / 2;
+            if (start > hi - k.cap) start = hi - k.cap;
+            if (start < lo) start = lo;
+            cnt = k.cap;
+        }
+        begin = start;
+        count = cnt;
     }
-    begin = start;
-    count = cnt;
 }
 
 __device__ __forceinline__ TState load_state(const KBatch& b, int t) {
@@ -190,43 +211,105 @@ __device__ __forceinline__ TState load_state(const KBatch& b, int t) {
     return s;
 }
 
-struct WarpSmem {
-    WarpHead* h;
-    float *wx, *wz, *wd, *ww;
+// ------------------------------------------------------- shared-memory slots
+
+struct Slot {
+    SlotHead* h;
+    float* wx;
+    float* wz;
 };
 
-__device__ __forceinline__ WarpSmem warp_smem(char* base, int warp, int cap) {
-    char* p = base + (size_t)warp * warp_smem_bytes(cap);
-    WarpSmem m;
-    m.h = reinterpret_cast<WarpHead*>(p);
-    float* f = reinterpret_cast<float*>(p + align16(sizeof(WarpHead)));
-    m.wx = f;
-    m.wz = f + NL * cap;
-    m.wd = f + 2 * NL * cap;
-    m.ww = f + 3 * NL * cap;
-    return m;
+struct Scratch {
+    unsigned long long* cand;
+    unsigned short* pairs;
+};
+
+__device__ __forceinline__ Slot slot_at(char* base, int i, int cap) {
+    char* p = base + (size_t)i * slot_bytes(cap);
+    Slot s;
+    s.h = reinterpret_cast<SlotHead*>(p);
+    s.wx = reinterpret_cast<float*>(p + align16(sizeof(SlotHead)));
+    s.wz = s.wx + NL * cap;
+    return s;
 }
 
-// Copy the window hits into shared memory (coalesced, one layer at a time)
-// and note which windows hold hits of a single z.
-__device__ __forceinline__ void stage_windows(const KParams& k, const KBatch& b, const WarpSmem& m, int lane) {
+__device__ __forceinline__ Scratch scratch_at(char* base, int i) {
+    char* p = base + (size_t)i * scratch_bytes();
+    Scratch s;
+    s.cand = reinterpret_cast<unsigned long long*>(p);
+    s.pairs = reinterpret_cast<unsigned short*>(p + CAND_CAP * sizeof(unsigned long long));
+    return s;
+}
+
+// Copy x and z of the window hits into the slot: the (layer, hit) pairs of
+// all twelve windows are flattened over the lanes so that several loads are
+// in flight per lane; a window whose hits do not all share one z is flagged.
+__device__ __forceinline__ void stage_windows(const KParams& k, const KBatch& b, const Slot& m, int lane) {
     const int cap = k.cap;
-#pragma unroll 1
-    for (int l = 0; l < NL; ++l) {
-        int beg = m.h->wbeg[l], cnt = m.h->wcnt[l];
-        bool same = true;
-        for (int j = lane; j < cnt; j += 32) {
-            float zz = __ldg(b.z + beg + j);
-            m.wx[l * cap + j] = __ldg(b.x + beg + j);
-            m.wz[l * cap + j] = zz;
-            m.wd[l * cap + j] = __ldg(b.dxdy + beg + j);
-            m.ww[l * cap + j] = __ldg(b.w + beg + j);
-            same = same && (zz == __ldg(b.z + beg));
-        }
-        unsigned all = __ballot_sync(FULL, same);
-        if (lane == 0) m.h->zuni[l] = (all == FULL);
+    int off[NL + 1];
+    off[0] = 0;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) off[l + 1] = off[l] + m.h->wcnt[l];
+    if (lane < NL) m.h->zuni[lane] = 1;
+    __syncwarp();
+    const int total = off[NL];
+#pragma unroll 4
+    for (int q = lane; q < total; q += 32) {
+        int l = 0;
+#pragma unroll
+        for (int i = 1; i < NL; ++i) l += (q >= off[i]) ? 1 : 0;
+        int j = q - off[l];
+        int src = m.h->wbeg[l] + j;
+        float zz = __ldg(b.z + src);
+        m.wx[l * cap + j] = __ldg(b.x + src);
+        m.wz[l * cap + j] = zz;
+        if (zz != __ldg(b.z + m.h->wbeg[l])) m.h->zuni[l] = 0;
     }
     __syncwarp();
+}
+
+__device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
+    unsigned lo = __shfl_xor_sync(FULL, (unsigned)v, m), hi = __shfl_xor_sync(FULL, (unsigned)(v >> 32), m);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// Bitonic sort of 64 keys held two per lane (element lane in a, lane+32 in
+// b), ascending.
+__device__ __forceinline__ void warp_sort64(uint64_t& a, uint64_t& b, int lane) {
+#pragma unroll
+    for (int kk = 2; kk <= 64; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            if (j == 32) {
+                uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+                a = lo;
+                b = hi;
+            } else {
+                uint64_t pa = shfl_xor64(a, j), pb = shfl_xor64(b, j);
+                bool lower = (lane & j) == 0;
+                bool up_a = (lane & kk) == 0, up_b = ((lane + 32) & kk) == 0;
+                a = (lower == up_a) ? (a < pa ? a : pa) : (a < pa ? pa : a);
+                b = (lower == up_b) ? (b < pb ? b : pb) : (b < pb ? pb : b);
+            }
+        }
+    }
+}
+
+// Sort the buffered keys; keep the NT smallest at the front of the buffer.
+// Returns the new buffer size; thr becomes the NT-th smallest key once the
+// buffer holds NT keys (no later key at or above it can be kept).
+__device__ __forceinline__ int select_buffer(const Scratch& sc, int nb, int NT, uint64_t& thr, int lane,
+                                             uint64_t& mine) {
+    uint64_t a = lane < nb ? sc.cand[lane] : NOKEY;
+    uint64_t b = lane + 32 < nb ? sc.cand[lane + 32] : NOKEY;
+    __syncwarp();
+    warp_sort64(a, b, lane);
+    int keep = nb < NT ? nb : NT;
+    if (lane < keep) sc.cand[lane] = a;
+    mine = lane < keep ? a : NOKEY;
+    if (keep == NT) thr = shfl64(a, NT - 1);
+    __syncwarp();
+    return keep;
 }
 
 // ---------------------------------------------------------- stage: triplets
@@ -235,10 +318,13 @@ __device__ __forceinline__ void stage_windows(const KParams& k, const KBatch& b,
 // (lane r holds rank r; NOKEY past the end) and the list length.
 // key = chi2 bits << 32 | cfg << 18 | j0 << 12 | j2 << 6 | j1 (window-local
 // indices), which orders by (chi2, cfg, h0, h2).
-__device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState& s, const WarpSmem& m, int lane,
-                                                 int& n_trip) {
+template <int NIT>
+__device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState& s, const Slot& m, const Scratch& sc,
+                                                 int lane, int& n_trip) {
     const int cap = k.cap;
     const int NT = k.n_trip;
+    n_trip = 0;
+    if (NT <= 0) return NOKEY;
     const float pmom = 1.0f / fabsf(s.qop);
     const float x_mag_in = s.xs + s.txs * (k.z_magnet - k.z_state);
     const float bend = (s.qop > 0.0f) ? k.pol_f : -k.pol_f;
@@ -247,29 +333,40 @@ __device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState&
     const int c0 = m.h->wcnt[0], c1 = m.h->wcnt[3];
     const int n_items = c0 + c1;
 
-    // h2 interval of each h0 item (items lane, lane+32, lane+64, lane+96)
-    constexpr int NIT = (2 * MAX_CAP) / 32;
-    int n_it[NIT], a_it[NIT];
+    // h2 interval of each (cfg, h0) item: items lane + 32*part (NIT*32 >= 2*cap)
+    int n_it[NIT], a_it[NIT], code_it[NIT];
 #pragma unroll
     for (int part = 0; part < NIT; ++part) {
         int i = lane + 32 * part;
-        int n = 0, a = 0;
+        int n = 0, a = 0, code = 0;
         if (i < n_items) {
             int cfg = i < c0 ? 0 : 1;
             int j0 = cfg ? i - c0 : i;
             int L0 = cfg ? 3 : 0, L2 = cfg ? 11 : 8;
+            code = (cfg << 12) | (j0 << 6);
             float x0 = m.wx[L0 * cap + j0], z0 = m.wz[L0 * cap + j0];
             int n2 = m.h->wcnt[L2];
             n = n2;
             if (n2 > 0 && m.h->zuni[L2]) {
-                float z2 = m.wz[L2 * cap];
-                float r = (k.z_magnet - z0) / (z2 - z0);
-                if (z2 > z0 && r < 0.0f) {
-                    // |x0 + (x2 - x0) r - x_mag_in| < magtol_max, widened by a
-                    // slack far above the rounding of the exact test
+                float dzl = m.wz[L2 * cap] - z0;
+                if (dzl > 0.0f && z0 > k.z_magnet) {
+                    // x2 with |x0 + (x2 - x0) r - x_mag_in| < tol form an interval
+                    // (r < 0); bound it first with the largest tolerance, then
+                    // with the largest tolerance the slopes inside allow, and
+                    // below p_bend with the bending sign; widen by a slack far
+                    // above the rounding of the exact tests applied later
+                    float r = (k.z_magnet - z0) / dzl;
                     float slack = 0.5f + 1e-4f * (fabsf(x0) + fabsf(x_mag_in));
                     float lo = x0 + (x_mag_in - x0 + k.magtol_max) / r - slack;
                     float hi = x0 + (x_mag_in - x0 - k.magtol_max) / r + slack;
+                    float txm = fmaxf(fabsf(lo - x0), fabsf(hi - x0)) / dzl;
+                    float t2 = fminf(fmaxf(tol_base + k.magtol_tx * txm, k.magtol_min), k.magtol_max);
+                    lo = x0 + (x_mag_in - x0 + t2) / r - slack;
+                    hi = x0 + (x_mag_in - x0 - t2) / r + slack;
+                    if (f1) {
+                        float xb = x0 + s.txs * dzl;
+                        if (bend > 0.0f) lo = fmaxf(lo, xb - slack); else hi = fminf(hi, xb + slack);
+                    }
                     const float* x2w = m.wx + L2 * cap;
                     a = lb_smem(x2w, n2, lo);
                     int bnd = ub_smem(x2w, n2, hi);
@@ -279,84 +376,86 @@ __device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState&
         }
         n_it[part] = n;
         a_it[part] = a;
+        code_it[part] = code;
     }
+    int pre_it[NIT];
     int P = 0;
 #pragma unroll
     for (int part = 0; part < NIT; ++part) {
         int inc = warp_incl_scan(n_it[part], lane);
-        m.h->pre[lane + 32 * part] = P + inc - n_it[part];
-        m.h->aa[lane + 32 * part] = a_it[part];
+        pre_it[part] = P + inc - n_it[part];
         P += __shfl_sync(FULL, inc, 31);
     }
-    __syncwarp();
 
-    uint64_t top = NOKEY;
+    int nb = 0;            // keys in the buffer
+    uint64_t thr = NOKEY;  // keys at or above thr cannot be kept
+    uint64_t mine = NOKEY;
 #pragma unroll 1
-    for (int base = 0; base < P; base += 32) {
-        int p = base + lane;
-        bool valid = false;
-        uint64_t key = NOKEY;
-        if (p < P) {
-            int lo = 0, hi = 2 * MAX_CAP;
-            while (lo < hi) {
-                int mid = lo + ((hi - lo) >> 1);
-                if (m.h->pre[mid] <= p) lo = mid + 1; else hi = mid;
-            }
-            int item = lo - 1;
-            int cfg = item < c0 ? 0 : 1;
-            int j0 = cfg ? item - c0 : item;
-            int L0 = cfg ? 3 : 0, L1 = cfg ? 7 : 4, L2 = cfg ? 11 : 8;
-            int j2 = m.h->aa[item] + (p - m.h->pre[item]);
-            float x0 = m.wx[L0 * cap + j0], z0 = m.wz[L0 * cap + j0];
-            float x2 = m.wx[L2 * cap + j2], z2 = m.wz[L2 * cap + j2];
-            float tx_d = (x2 - x0) / (z2 - z0);
-            bool ok = true;
-            if (f1) {
-                float d = tx_d - s.txs;
-                ok = (bend > 0.0f) ? (d > 0.0f) : (d < 0.0f);
-            }
-            if (ok) {
-                float x_mag_d = x0 + tx_d * (k.z_magnet - z0);
-                float tol = tol_base + k.magtol_tx * fabsf(tx_d);
-                tol = fminf(fmaxf(tol, k.magtol_min), k.magtol_max);
-                ok = fabsf(x_mag_d - x_mag_in) < tol;
-            }
-            if (ok) {
-                float K = cfg ? k.K_last : k.K_first;
-                float x1_exp = k.z[L1] * tx_d + (x0 - tx_d * z0) * K;
-                int j1 = closest_smem(m.wx + L1 * cap, m.h->wcnt[L1], x1_exp);
-                if (j1 >= 0) {
-                    float dx = m.wx[L1 * cap + j1] - x1_exp;
-                    float chi2 = dx * dx;
-                    if (chi2 < k.T_triplet) {
-                        valid = true;
-                        key = ((uint64_t)__float_as_uint(chi2) << 32) | ((uint64_t)cfg << 18) |
-                              ((uint64_t)j0 << 12) | ((uint64_t)j2 << 6) | (uint64_t)j1;
+    for (int seg = 0; seg < P; seg += PAIR_CAP) {
+        // materialise the pairs of this segment
+#pragma unroll
+        for (int part = 0; part < NIT; ++part) {
+            int q0 = max(pre_it[part], seg), q1 = min(pre_it[part] + n_it[part], seg + PAIR_CAP);
+            for (int q = q0; q < q1; ++q)
+                sc.pairs[q - seg] = (unsigned short)(code_it[part] | (a_it[part] + (q - pre_it[part])));
+        }
+        __syncwarp();
+        const int np = min(P - seg, PAIR_CAP);
+#pragma unroll 1
+        for (int base = 0; base < np; base += 32) {
+            int q = base + lane;
+            bool valid = false;
+            uint64_t key = NOKEY;
+            if (q < np) {
+                unsigned code = sc.pairs[q];
+                int cfg = (int)(code >> 12), j0 = (int)((code >> 6) & 63), j2 = (int)(code & 63);
+                int L0 = cfg ? 3 : 0, L1 = cfg ? 7 : 4, L2 = cfg ? 11 : 8;
+                float x0 = m.wx[L0 * cap + j0], z0 = m.wz[L0 * cap + j0];
+                float x2 = m.wx[L2 * cap + j2], z2 = m.wz[L2 * cap + j2];
+                float tx_d = (x2 - x0) / (z2 - z0);
+                bool ok = true;
+                if (f1) {
+                    float d = tx_d - s.txs;
+                    ok = (bend > 0.0f) ? (d > 0.0f) : (d < 0.0f);
+                }
+                if (ok) {
+                    float x_mag_d = x0 + tx_d * (k.z_magnet - z0);
+                    float tol = tol_base + k.magtol_tx * fabsf(tx_d);
+                    tol = fminf(fmaxf(tol, k.magtol_min), k.magtol_max);
+                    ok = fabsf(x_mag_d - x_mag_in) < tol;
+                }
+                if (ok) {
+                    float K = cfg ? k.K_last : k.K_first;
+                    float x1_exp = k.z[L1] * tx_d + (x0 - tx_d * z0) * K;
+                    int j1 = closest_smem(m.wx + L1 * cap, m.h->wcnt[L1], x1_exp);
+                    if (j1 >= 0) {
+                        float dx = m.wx[L1 * cap + j1] - x1_exp;
+                        float chi2 = dx * dx;
+                        if (chi2 < k.T_triplet) {
+                            key = ((uint64_t)__float_as_uint(chi2) << 32) | ((uint64_t)cfg << 18) |
+                                  ((uint64_t)j0 << 12) | ((uint64_t)j2 << 6) | (uint64_t)j1;
+                            valid = key < thr;
+                        }
                     }
                 }
             }
-        }
-        if (NT > 0) {
-            uint64_t thr = shfl64(top, NT - 1);
-            valid = valid && key < thr;
             unsigned msk = __ballot_sync(FULL, valid);
-            while (msk) {
-                int src = __ffs(msk) - 1;
-                msk &= msk - 1;
-                uint64_t kk = shfl64(key, src);
-                uint64_t last = shfl64(top, NT - 1);
-                if (kk < last) {
-                    unsigned lt = __ballot_sync(FULL, lane < NT && top < kk);
-                    int pos = __popc(lt);
-                    uint64_t up = shfl64_up(top, 1);
-                    if (lane == pos) top = kk;
-                    else if (lane > pos && lane < NT) top = up;
+            if (msk) {
+                if (nb + __popc(msk) > CAND_CAP) {
+                    nb = select_buffer(sc, nb, NT, thr, lane, mine);
+                    valid = valid && key < thr;
+                    msk = __ballot_sync(FULL, valid);
                 }
+                if (valid) sc.cand[nb + __popc(msk & ((1u << lane) - 1u))] = key;
+                nb += __popc(msk);
+                __syncwarp();
             }
         }
+        __syncwarp();
     }
-    n_trip = __popc(__ballot_sync(FULL, lane < NT && top != NOKEY));
-    return top;
+    nb = select_buffer(sc, nb, NT, thr, lane, mine);
+    n_trip = nb;
+    return mine;
 }
 
 // --------------------------------------------------- stage: extension + fit
@@ -374,8 +473,11 @@ __device__ __forceinline__ float model_x(float A, float T, float C, float u, flo
     return (A + T * u) + C * f2_of(u, D);
 }
 
-__device__ __noinline__ void extend_fit(const KParams& k, const TState& s, const WarpSmem& m, uint64_t key,
-                                        Cand& cd) {
+// Extension and fit of one triplet (Sec. "Extending triplets to other
+// layers", "Quality Filter"); x and z of the window hits come from the
+// slot, dxdy and w of the hits used from global memory.
+__device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, const TState& s, const Slot& m,
+                                           uint64_t key, Cand& cd) {
     const int cap = k.cap;
     const float D = k.D;
     const int cfg = (int)((key >> 18) & 1);
@@ -425,7 +527,7 @@ __device__ __noinline__ void extend_fit(const KParams& k, const TState& s, const
         float u = (m.wz[q] - k.z_ref) * 1e-3f;
         float f = f2_of(u, D);
         float r = m.wx[q] - model_x(A, T, C, u, D);
-        float wt = m.ww[q];
+        float wt = __ldg(b.w + m.h->wbeg[l] + hl[l]);
         float wu = wt * u, wf = wt * f;
         S00 = S00 + wt; S01 = S01 + wu; S02 = S02 + wf;
         S11 = S11 + wu * u; S12 = S12 + wu * f; S22 = S22 + wf * f;
@@ -484,16 +586,20 @@ __device__ __noinline__ void extend_fit(const KParams& k, const TState& s, const
 
     // y line fit from the stereo hits
     float Y0s = 0.0f, Y1s = 0.0f, Y2s = 0.0f, yb0 = 0.0f, yb1 = 0.0f;
-    float yv[NL];
+    float yv[NL], dv[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
         yv[l] = 0.0f;
+        dv[l] = 0.0f;
         if (is_x(l) || hl[l] < 0) continue;
         int q = l * cap + hl[l];
+        int g = m.h->wbeg[l] + hl[l];
         float u = (m.wz[q] - k.z_ref) * 1e-3f;
-        float y = (model_x(A, T, C, u, D) - m.wx[q]) / m.wd[q];
+        float dd = __ldg(b.dxdy + g);
+        dv[l] = dd;
+        float y = (model_x(A, T, C, u, D) - m.wx[q]) / dd;
         yv[l] = y;
-        float wt = m.ww[q];
+        float wt = __ldg(b.w + g);
         float wu = wt * u;
         Y0s = Y0s + wt; Y1s = Y1s + wu; Y2s = Y2s + wu * u;
         yb0 = yb0 + wt * y; yb1 = yb1 + wu * y;
@@ -524,7 +630,7 @@ __device__ __noinline__ void extend_fit(const KParams& k, const TState& s, const
             qx = qx + (r * r) / k.T_x;
         } else {
             float yf = Y0 + TY * u;
-            float r = m.wx[q] - (xf - yf * m.wd[q]);
+            float r = m.wx[q] - (xf - yf * dv[l]);
             qx = qx + (r * r) / T_uv;
             float ry = yv[l] - yf;
             qy = qy + (ry * ry) / k.T_y;
@@ -549,40 +655,36 @@ __device__ __noinline__ void extend_fit(const KParams& k, const TState& s, const
 
 // ---------------------------------------------------------- stage: selection
 
-// Warp-wide choice of the lowest Q among accepted candidates (ties to the
-// lower rank) and coalesced output of the winner.
-__device__ __forceinline__ void select_and_write(const KOut& o, int t, int lane, bool have, float Q, int n,
-                                                 const int* hl_glob, const float* st) {
-    uint64_t key = have ? (((uint64_t)__float_as_uint(Q) << 32) | (unsigned)lane) : NOKEY;
-    uint64_t best = warp_min64(key);
+// Lowest Q among the accepted candidates of a group of G consecutive lanes
+// (G = 16 or 32; candidate rank = lane within the group; ties to the lower
+// rank).  The winner writes the track's output; without a winner the
+// group's first lane writes found = 0.
+template <int G>
+__device__ __forceinline__ void group_select_write(const KOut& o, int t, bool live, int rank, bool have, float Q,
+                                                   int n, const int* hglob, const float* st) {
+    uint64_t key = have ? (((uint64_t)__float_as_uint(Q) << 32) | (unsigned)rank) : NOKEY;
+    uint64_t best = key;
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        uint64_t u = shfl_xor64(best, off);
+        best = u < best ? u : best;
+    }
+    if (!live) return;
     if (best == NOKEY) {
-        if (lane == 0) {
+        if (rank == 0) {
             o.found[t] = 0;
             o.nhits[t] = 0;
         }
         return;
     }
-    int w = (int)(best & 31u);
-    int mine = -1;
-    float stv = 0.0f;
+    if (have && key == best) {
 #pragma unroll
-    for (int l = 0; l < NL; ++l) {
-        int v = __shfl_sync(FULL, hl_glob[l], w);
-        if (lane == l) mine = v;
-    }
+        for (int l = 0; l < NL; ++l) o.hit_idx[(size_t)t * NL + l] = hglob[l];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        float v = __shfl_sync(FULL, st[q], w);
-        if (lane == NL + q) stv = v;
-    }
-    float Qw = __shfl_sync(FULL, Q, w);
-    int nw = __shfl_sync(FULL, n, w);
-    if (lane < NL) o.hit_idx[(size_t)t * NL + lane] = mine;
-    else if (lane < NL + 6) o.state[(size_t)t * 6 + (lane - NL)] = stv;
-    else if (lane == NL + 6) o.quality[t] = Qw;
-    else if (lane == NL + 7) {
+        for (int q = 0; q < 6; ++q) o.state[(size_t)t * 6 + q] = st[q];
+        o.quality[t] = Q;
+        o.nhits[t] = (uint8_t)n;
         o.found[t] = 1;
-        o.nhits[t] = (uint8_t)nw;
     }
 }
 
@@ -607,22 +709,46 @@ __global__ void k_track_event(KBatch b, int* trk_event) {
     }
 }
 
-// plain form, stage 1: windows (warp per track, lanes 0..11 one layer each)
-__global__ void k_windows(KParams k, KBatch b, const int* __restrict__ trk_event, int* wbeg, uint8_t* wcnt) {
-    int lane = threadIdx.x & 31;
-    int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= b.n_tracks) return;
+// Stage kernels.  Each stage's per-track work is a device function; the
+// plain kernel (P = false) calls it once for the tracks given by its global
+// warp index, the persistent kernel (P = true) is sized to the GPU and its
+// warps take tracks from the stage's device work queue (an atomic cursor)
+// until it is empty.
+__device__ __forceinline__ int queue_take(int* cursor, int n, int lane) {
+    int v = 0;
+    if (lane == 0) v = atomicAdd(cursor, n);
+    return __shfl_sync(FULL, v, 0);
+}
+
+__device__ __forceinline__ void windows_track(const KParams& k, const KBatch& b, const int* __restrict__ trk_event,
+                                              int* wbeg, uint8_t* wcnt, int t, int lane) {
+    TState s = load_state(b, t);
+    int beg, cnt;
+    warp_windows(k, b, s, __ldg(trk_event + t), lane, beg, cnt);
     if (lane < NL) {
-        TState s = load_state(b, t);
-        int beg, cnt;
-        layer_window(k, b, s, __ldg(trk_event + t), lane, beg, cnt);
         wbeg[(size_t)t * NL + lane] = beg;
         wcnt[(size_t)t * NL + lane] = (uint8_t)cnt;
     }
 }
 
-__device__ __forceinline__ void load_windows(const int* wbeg, const uint8_t* wcnt, int t, const WarpSmem& m,
-                                             int lane) {
+// stage 1: windows (warp per track)
+template <bool P>
+__global__ void k_windows(KParams k, KBatch b, const int* __restrict__ trk_event, int* wbeg, uint8_t* wcnt,
+                          int* cursor) {
+    const int lane = threadIdx.x & 31;
+    if (!P) {
+        const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        if (t < b.n_tracks) windows_track(k, b, trk_event, wbeg, wcnt, t, lane);
+        return;
+    }
+    for (;;) {
+        const int t = queue_take(cursor, 1, lane);
+        if (t >= b.n_tracks) break;
+        windows_track(k, b, trk_event, wbeg, wcnt, t, lane);
+    }
+}
+
+__device__ __forceinline__ void load_windows(const int* wbeg, const uint8_t* wcnt, int t, const Slot& m, int lane) {
     if (lane < NL) {
         m.h->wbeg[lane] = wbeg[(size_t)t * NL + lane];
         m.h->wcnt[lane] = wcnt[(size_t)t * NL + lane];
@@ -630,58 +756,105 @@ __device__ __forceinline__ void load_windows(const int* wbeg, const uint8_t* wcn
     __syncwarp();
 }
 
-// plain form, stage 2: triplet seeding
-__global__ void k_triplets(KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ wcnt,
-                           uint64_t* keys, uint8_t* ntrip) {
-    extern __shared__ __align__(16) char smem[];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int t = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (t >= b.n_tracks) return;
-    WarpSmem m = warp_smem(smem, warp, k.cap);
+constexpr int PLAIN_WARPS = 8;
+
+template <int NIT>
+__device__ __forceinline__ void triplets_track(const KParams& k, const KBatch& b, const int* __restrict__ wbeg,
+                                               const uint8_t* __restrict__ wcnt, uint64_t* keys, uint8_t* ntrip,
+                                               const Slot& m, const Scratch& sc, int t, int lane) {
     load_windows(wbeg, wcnt, t, m, lane);
     stage_windows(k, b, m, lane);
     TState s = load_state(b, t);
     int nt;
-    uint64_t top = triplet_scan(k, s, m, lane, nt);
+    uint64_t top = triplet_scan<NIT>(k, s, m, sc, lane, nt);
     if (lane < nt) keys[(size_t)t * k.n_trip + lane] = top;
     if (lane == 0) ntrip[t] = (uint8_t)nt;
+    __syncwarp();
 }
 
-// plain form, stage 3: extension and fit of every kept triplet
-__global__ void k_extend(KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ wcnt,
-                         const uint64_t* __restrict__ keys, const uint8_t* __restrict__ ntrip, CandRec* cands) {
+// stage 2: triplet seeding (warp per track)
+template <int NIT, bool P>
+__global__ void k_triplets(KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ wcnt,
+                           uint64_t* keys, uint8_t* ntrip, int* cursor) {
     extern __shared__ __align__(16) char smem[];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int t = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (t >= b.n_tracks) return;
-    int nt = ntrip[t];
-    if (nt == 0) return;
-    WarpSmem m = warp_smem(smem, warp, k.cap);
-    load_windows(wbeg, wcnt, t, m, lane);
-    stage_windows(k, b, m, lane);
-    if (lane < nt) {
-        TState s = load_state(b, t);
-        Cand cd;
-        extend_fit(k, s, m, keys[(size_t)t * k.n_trip + lane], cd);
-        CandRec r;
-        r.Q = cd.Q;
-        r.status = (int8_t)cd.status;
-        r.n = (int8_t)cd.n;
-#pragma unroll
-        for (int l = 0; l < NL; ++l) r.hl[l] = (int8_t)(cd.status == 0 ? cd.hl[l] : -1);
-        for (int q = 0; q < 6; ++q) r.pad[q] = 0;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) r.st[q] = cd.status == 0 ? cd.st[q] : 0.0f;
-        cands[(size_t)t * k.n_trip + lane] = r;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Slot m = slot_at(smem, warp, k.cap);
+    const Scratch sc = scratch_at(smem + PLAIN_WARPS * slot_bytes(k.cap), warp);
+    if (!P) {
+        const int t = blockIdx.x * PLAIN_WARPS + warp;
+        if (t < b.n_tracks) triplets_track<NIT>(k, b, wbeg, wcnt, keys, ntrip, m, sc, t, lane);
+        return;
+    }
+    for (;;) {
+        const int t = queue_take(cursor, 1, lane);
+        if (t >= b.n_tracks) break;
+        triplets_track<NIT>(k, b, wbeg, wcnt, keys, ntrip, m, sc, t, lane);
     }
 }
 
-// plain form, stage 4: warp-vote selection and output
-__global__ void k_select(KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ ntrip,
-                         const CandRec* __restrict__ cands, KOut o) {
-    int lane = threadIdx.x & 31;
-    int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= b.n_tracks) return;
+template <int TPW>
+__device__ __forceinline__ void extend_tracks(const KParams& k, const KBatch& b, const int* __restrict__ wbeg,
+                                              const uint8_t* __restrict__ wcnt, const uint64_t* __restrict__ keys,
+                                              const uint8_t* __restrict__ ntrip, CandRec* cands, const Slot* sl,
+                                              int t0, int lane) {
+#pragma unroll
+    for (int qq = 0; qq < TPW; ++qq) {
+        int tq = t0 + qq;
+        if (tq < b.n_tracks) {
+            load_windows(wbeg, wcnt, tq, sl[qq], lane);
+            stage_windows(k, b, sl[qq], lane);
+        }
+    }
+    constexpr int G = 32 / TPW;
+    const int q = lane / G, r = lane % G;
+    const int t = t0 + q;
+    Slot mq = sl[0];
+    if (TPW == 2 && q == 1) mq = sl[TPW - 1];
+    if (t < b.n_tracks && r < ntrip[t]) {
+        TState s = load_state(b, t);
+        Cand cd;
+        extend_fit(k, b, s, mq, keys[(size_t)t * k.n_trip + r], cd);
+        CandRec rec;
+        rec.Q = cd.Q;
+        rec.status = (int8_t)cd.status;
+        rec.n = (int8_t)cd.n;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) rec.hl[l] = (int8_t)(cd.status == 0 ? cd.hl[l] : -1);
+#pragma unroll
+        for (int p = 0; p < 6; ++p) rec.pad[p] = 0;
+#pragma unroll
+        for (int p = 0; p < 6; ++p) rec.st[p] = cd.status == 0 ? cd.st[p] : 0.0f;
+        cands[(size_t)t * k.n_trip + r] = rec;
+    }
+    __syncwarp();
+}
+
+// stage 3: extension and fit of every kept triplet; TPW tracks per warp
+// (two when n_triplets <= 16: lanes 0..15 and 16..31)
+template <int TPW, bool P>
+__global__ void __launch_bounds__(PLAIN_WARPS * 32, 4) k_extend(KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ wcnt,
+                         const uint64_t* __restrict__ keys, const uint8_t* __restrict__ ntrip, CandRec* cands,
+                         int* cursor) {
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Slot sl[TPW];
+#pragma unroll
+    for (int q = 0; q < TPW; ++q) sl[q] = slot_at(smem, warp * TPW + q, k.cap);
+    if (!P) {
+        const int t0 = (blockIdx.x * PLAIN_WARPS + warp) * TPW;
+        if (t0 < b.n_tracks) extend_tracks<TPW>(k, b, wbeg, wcnt, keys, ntrip, cands, sl, t0, lane);
+        return;
+    }
+    for (;;) {
+        const int t0 = queue_take(cursor, TPW, lane);
+        if (t0 >= b.n_tracks) break;
+        extend_tracks<TPW>(k, b, wbeg, wcnt, keys, ntrip, cands, sl, t0, lane);
+    }
+}
+
+__device__ __forceinline__ void select_track(const KParams& k, const int* __restrict__ wbeg,
+                                             const uint8_t* __restrict__ ntrip, const CandRec* __restrict__ cands,
+                                             const KOut& o, int t, int lane) {
     int nt = ntrip[t];
     bool have = false;
     float Q = 0.0f;
@@ -702,60 +875,134 @@ __global__ void k_select(KParams k, KBatch b, const int* __restrict__ wbeg, cons
 #pragma unroll
         for (int q = 0; q < 6; ++q) st[q] = r.st[q];
     }
-    select_and_write(o, t, lane, have, Q, n, hg, st);
+    group_select_write<32>(o, t, true, lane, have, Q, n, hg, st);
 }
 
-// One track through every stage, inside the persistent kernel.
-__device__ __forceinline__ void follow_track(const KParams& k, const KBatch& b, const KOut& o, int t, int e,
-                                             const WarpSmem& m, int lane) {
-    TState s = load_state(b, t);
-    if (lane < NL) {
-        int beg, cnt;
-        layer_window(k, b, s, e, lane, beg, cnt);
-        m.h->wbeg[lane] = beg;
-        m.h->wcnt[lane] = cnt;
+// stage 4: warp-vote selection and output (warp per track)
+template <bool P>
+__global__ void k_select(KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ ntrip,
+                         const CandRec* __restrict__ cands, KOut o, int* cursor) {
+    const int lane = threadIdx.x & 31;
+    if (!P) {
+        const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        if (t < b.n_tracks) select_track(k, wbeg, ntrip, cands, o, t, lane);
+        return;
     }
-    __syncwarp();
-    stage_windows(k, b, m, lane);
-    int nt;
-    uint64_t top = triplet_scan(k, s, m, lane, nt);
-    Cand cd;
-    cd.status = 9;
-    cd.Q = 0.0f;
-    cd.n = 0;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) cd.st[q] = 0.0f;
-#pragma unroll
-    for (int l = 0; l < NL; ++l) cd.hl[l] = -1;
-    if (lane < nt) extend_fit(k, s, m, top, cd);
-    int hg[NL];
-#pragma unroll
-    for (int l = 0; l < NL; ++l) hg[l] = (lane < nt && cd.status == 0 && cd.hl[l] >= 0) ? m.h->wbeg[l] + cd.hl[l] : -1;
-    select_and_write(o, t, lane, lane < nt && cd.status == 0, cd.Q, cd.n, hg, cd.st);
-    __syncwarp();
-}
-
-// persistent form: warps take grains of consecutive input tracks from a
-// device work queue until it is empty
-__global__ void k_fused(KParams k, KBatch b, KOut o, int* cursor, int grain) {
-    extern __shared__ __align__(16) char smem[];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpSmem m = warp_smem(smem, warp, k.cap);
     for (;;) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(cursor, grain);
-        base = __shfl_sync(FULL, base, 0);
-        if (base >= b.n_tracks) break;
-        int end = min(base + grain, b.n_tracks);
-        int e = event_of(b.trk_offsets, b.n_events, base);
-        for (int t = base; t < end; ++t) {
-            while (t >= __ldg(b.trk_offsets + e + 1)) ++e;
-            follow_track(k, b, o, t, e, m, lane);
-        }
+        const int t = queue_take(cursor, 1, lane);
+        if (t >= b.n_tracks) break;
+        select_track(k, wbeg, ntrip, cands, o, t, lane);
     }
 }
 
-// debug dump of the plain form's triplet stage in packed hit indices
+// persistent form.  SYNC: blocks take tiles of (warps x TPW) consecutive
+// input tracks from the device work queue and their warps step through the
+// stages together (block barriers between windows + staging, triplet
+// seeding, extension + selection).  !SYNC: every warp takes its own TPW
+// tracks from the queue and runs on without waiting for the others.
+template <int NIT, int TPW, bool SYNC>
+__global__ void __launch_bounds__(512, 1) k_tile(KParams k, KBatch b, KOut o, int* cursor) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ int s_base, s_ev;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    Slot sl[TPW];
+#pragma unroll
+    for (int q = 0; q < TPW; ++q) sl[q] = slot_at(smem, warp * TPW + q, k.cap);
+    const Scratch sc = scratch_at(smem + (size_t)nw * TPW * slot_bytes(k.cap), warp);
+    for (;;) {
+        int first, e;
+        if (SYNC) {
+            if (threadIdx.x == 0) {
+                int base = atomicAdd(cursor, nw * TPW);
+                s_base = base;
+                s_ev = base < b.n_tracks ? event_of(b.trk_offsets, b.n_events, base) : 0;
+            }
+            __syncthreads();
+            const int base = s_base;
+            e = s_ev;
+            __syncthreads();
+            if (base >= b.n_tracks) break;
+            first = base + warp * TPW;
+        } else {
+            int v = 0;
+            if (lane == 0) v = atomicAdd(cursor, TPW);
+            first = __shfl_sync(FULL, v, 0);
+            if (first >= b.n_tracks) break;
+            e = event_of(b.trk_offsets, b.n_events, first);
+        }
+
+        TState st[TPW];
+        bool live[TPW];
+#pragma unroll
+        for (int q = 0; q < TPW; ++q) {
+            const int t = first + q;
+            live[q] = t < b.n_tracks;
+            if (live[q]) {
+                while (t >= __ldg(b.trk_offsets + e + 1)) ++e;
+                st[q] = load_state(b, t);
+                int beg, cnt;
+                warp_windows(k, b, st[q], e, lane, beg, cnt);
+                if (lane < NL) {
+                    sl[q].h->wbeg[lane] = beg;
+                    sl[q].h->wcnt[lane] = cnt;
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < TPW; ++q)
+            if (live[q]) stage_windows(k, b, sl[q], lane);
+        if (SYNC) __syncthreads();
+
+        uint64_t top[TPW];
+        int nt[TPW];
+#pragma unroll
+        for (int q = 0; q < TPW; ++q) {
+            nt[q] = 0;
+            top[q] = NOKEY;
+            if (live[q]) top[q] = triplet_scan<NIT>(k, st[q], sl[q], sc, lane, nt[q]);
+        }
+        if (SYNC) __syncthreads();
+
+        constexpr int G = 32 / TPW;
+        const int qg = lane / G, r = lane % G;
+        uint64_t key = NOKEY;
+#pragma unroll
+        for (int q = 0; q < TPW; ++q) {
+            uint64_t kq = shfl64(top[q], r);
+            if (q == qg) key = kq;
+        }
+        bool lv = false;
+        int ntq = 0;
+        TState sq = st[0];
+#pragma unroll
+        for (int q = 0; q < TPW; ++q)
+            if (q == qg) {
+                lv = live[q];
+                ntq = nt[q];
+                sq = st[q];
+            }
+        Cand cd;
+        cd.status = 9;
+        cd.Q = 0.0f;
+        cd.n = 0;
+#pragma unroll
+        for (int p = 0; p < 6; ++p) cd.st[p] = 0.0f;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) cd.hl[l] = -1;
+        const bool act = lv && r < ntq;
+        Slot mq = sl[0];
+        if (TPW == 2 && qg == 1) mq = sl[TPW - 1];
+        if (act) extend_fit(k, b, sq, mq, key, cd);
+        int hg[NL];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) hg[l] = (act && cd.status == 0 && cd.hl[l] >= 0) ? mq.h->wbeg[l] + cd.hl[l] : -1;
+        group_select_write<G>(o, first + qg, lv, r, act && cd.status == 0, cd.Q, cd.n, hg, cd.st);
+        if (SYNC) __syncthreads(); else __syncwarp();
+    }
+}
+
+// debug dump of the plain form's windows and triplet stage in packed indices
 __global__ void k_debug_triplets(KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ wcnt,
                                  const uint64_t* __restrict__ keys, const uint8_t* __restrict__ ntrip,
                                  int* win_count_out, int* n_trip_out, int* trip_out, float* chi2_out) {
@@ -855,7 +1102,10 @@ __global__ void k_compact_scatter(const int* __restrict__ trk_offsets, const uin
 // ================================================================ launchers
 
 static inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
-constexpr int PLAIN_WARPS = 8;
+
+static cudaError_t set_smem(const void* fn, size_t bytes) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 cudaError_t launch_track_event(const KBatch& b, int* trk_event, cudaStream_t s) {
     if (b.n_events <= 0) return cudaSuccess;
@@ -863,61 +1113,137 @@ cudaError_t launch_track_event(const KBatch& b, int* trk_event, cudaStream_t s) 
     return cudaGetLastError();
 }
 
+// Stage launches.  cursor == nullptr: plain grid (one pass); otherwise a
+// persistent grid of `blocks` blocks that drains the stage's work queue.
 cudaError_t launch_windows(const KParams& k, const KBatch& b, const int* trk_event, int* wbeg, uint8_t* wcnt,
-                           cudaStream_t s) {
+                           cudaStream_t s, int* cursor, int blocks) {
     if (b.n_tracks <= 0) return cudaSuccess;
-    k_windows<<<cdiv((long)b.n_tracks * 32, 256), 256, 0, s>>>(k, b, trk_event, wbeg, wcnt);
+    if (cursor) k_windows<true><<<blocks, 256, 0, s>>>(k, b, trk_event, wbeg, wcnt, cursor);
+    else k_windows<false><<<cdiv((long)b.n_tracks * 32, 256), 256, 0, s>>>(k, b, trk_event, wbeg, wcnt, nullptr);
     return cudaGetLastError();
 }
 
-static cudaError_t set_smem(const void* fn, size_t bytes) {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+template <int NIT, bool P>
+static cudaError_t launch_triplets_t(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* wcnt,
+                                     uint64_t* keys, uint8_t* ntrip, cudaStream_t s, int* cursor, int blocks) {
+    size_t sm = block_smem_bytes(k.cap, PLAIN_WARPS, 1);
+    cudaError_t err = set_smem((const void*)k_triplets<NIT, P>, sm);
+    if (err != cudaSuccess) return err;
+    const int grid = P ? blocks : cdiv(b.n_tracks, PLAIN_WARPS);
+    k_triplets<NIT, P><<<grid, PLAIN_WARPS * 32, sm, s>>>(k, b, wbeg, wcnt, keys, ntrip, cursor);
+    return cudaGetLastError();
+}
+
+template <bool P>
+static cudaError_t launch_triplets_p(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* wcnt,
+                                     uint64_t* keys, uint8_t* ntrip, cudaStream_t s, int* cursor, int blocks) {
+    if (k.cap <= 16) return launch_triplets_t<1, P>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
+    if (k.cap <= 32) return launch_triplets_t<2, P>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
+    return launch_triplets_t<4, P>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
 }
 
 cudaError_t launch_triplets(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
-                            const uint8_t* wcnt, uint64_t* keys, uint8_t* ntrip, cudaStream_t s) {
+                            const uint8_t* wcnt, uint64_t* keys, uint8_t* ntrip, cudaStream_t s, int* cursor,
+                            int blocks) {
     (void)trk_event;
     if (b.n_tracks <= 0) return cudaSuccess;
-    size_t sm = warp_smem_bytes(k.cap) * PLAIN_WARPS;
-    cudaError_t err = set_smem((const void*)k_triplets, sm);
+    if (cursor) return launch_triplets_p<true>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
+    return launch_triplets_p<false>(k, b, wbeg, wcnt, keys, ntrip, s, nullptr, 0);
+}
+
+template <int TPW, bool P>
+static cudaError_t launch_extend_t(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* wcnt,
+                                   const uint64_t* keys, const uint8_t* ntrip, CandRec* cands, cudaStream_t s,
+                                   int* cursor, int blocks) {
+    size_t sm = (size_t)PLAIN_WARPS * TPW * slot_bytes(k.cap);
+    cudaError_t err = set_smem((const void*)k_extend<TPW, P>, sm);
     if (err != cudaSuccess) return err;
-    k_triplets<<<cdiv(b.n_tracks, PLAIN_WARPS), PLAIN_WARPS * 32, sm, s>>>(k, b, wbeg, wcnt, keys, ntrip);
+    const int grid = P ? blocks : cdiv(b.n_tracks, PLAIN_WARPS * TPW);
+    k_extend<TPW, P><<<grid, PLAIN_WARPS * 32, sm, s>>>(k, b, wbeg, wcnt, keys, ntrip, cands, cursor);
     return cudaGetLastError();
 }
 
 cudaError_t launch_extend(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
                           const uint8_t* wcnt, const uint64_t* keys, const uint8_t* ntrip, CandRec* cands,
-                          cudaStream_t s) {
+                          cudaStream_t s, int* cursor, int blocks) {
     (void)trk_event;
     if (b.n_tracks <= 0) return cudaSuccess;
-    size_t sm = warp_smem_bytes(k.cap) * PLAIN_WARPS;
-    cudaError_t err = set_smem((const void*)k_extend, sm);
-    if (err != cudaSuccess) return err;
-    k_extend<<<cdiv(b.n_tracks, PLAIN_WARPS), PLAIN_WARPS * 32, sm, s>>>(k, b, wbeg, wcnt, keys, ntrip, cands);
-    return cudaGetLastError();
+    if (k.n_trip <= 16) {
+        if (cursor) return launch_extend_t<2, true>(k, b, wbeg, wcnt, keys, ntrip, cands, s, cursor, blocks);
+        return launch_extend_t<2, false>(k, b, wbeg, wcnt, keys, ntrip, cands, s, nullptr, 0);
+    }
+    if (cursor) return launch_extend_t<1, true>(k, b, wbeg, wcnt, keys, ntrip, cands, s, cursor, blocks);
+    return launch_extend_t<1, false>(k, b, wbeg, wcnt, keys, ntrip, cands, s, nullptr, 0);
 }
 
 cudaError_t launch_select(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* ntrip,
-                          const CandRec* cands, const KOut& o, cudaStream_t s) {
+                          const CandRec* cands, const KOut& o, cudaStream_t s, int* cursor, int blocks) {
     if (b.n_tracks <= 0) return cudaSuccess;
-    k_select<<<cdiv((long)b.n_tracks * 32, 256), 256, 0, s>>>(k, b, wbeg, ntrip, cands, o);
+    if (cursor) k_select<true><<<blocks, 256, 0, s>>>(k, b, wbeg, ntrip, cands, o, cursor);
+    else k_select<false><<<cdiv((long)b.n_tracks * 32, 256), 256, 0, s>>>(k, b, wbeg, ntrip, cands, o, nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t fused_max_blocks_per_sm(const KParams& k, int warps_per_block, int* out) {
-    size_t sm = warp_smem_bytes(k.cap) * warps_per_block;
-    cudaError_t err = set_smem((const void*)k_fused, sm);
+// resident blocks per SM of each persistent stage kernel (for grid sizing)
+cudaError_t stage_blocks_per_sm(const KParams& k, int* out4) {
+    cudaError_t err;
+    size_t smt = block_smem_bytes(k.cap, PLAIN_WARPS, 1);
+    const int tpw = k.n_trip <= 16 ? 2 : 1;
+    size_t sme = (size_t)PLAIN_WARPS * tpw * slot_bytes(k.cap);
+    const void* ft = k.cap <= 16 ? (const void*)k_triplets<1, true>
+                                 : (k.cap <= 32 ? (const void*)k_triplets<2, true> : (const void*)k_triplets<4, true>);
+    const void* fe = tpw == 2 ? (const void*)k_extend<2, true> : (const void*)k_extend<1, true>;
+    if ((err = set_smem(ft, smt)) != cudaSuccess) return err;
+    if ((err = set_smem(fe, sme)) != cudaSuccess) return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out4[0], k_windows<true>, 256, 0)) != cudaSuccess)
+        return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out4[1], ft, PLAIN_WARPS * 32, smt)) != cudaSuccess)
+        return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out4[2], fe, PLAIN_WARPS * 32, sme)) != cudaSuccess)
+        return err;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out4[3], k_select<true>, 256, 0);
+}
+
+static int tile_tpw(const KParams& k, int grain) {
+    if (grain == 1) return 1;
+    return k.n_trip <= 16 ? 2 : 1;
+}
+
+// grain: tracks per warp (1, 2; 0 = 2 when n_triplets <= 16); queue: 0 warp
+// fetch, 1 block tiles with stage barriers (both carried in `grain`:
+// grain + 16 * queue)
+template <int NIT>
+static const void* tile_fn_nit(int tpw, bool sync) {
+    if (tpw == 2) return sync ? (const void*)k_tile<NIT, 2, true> : (const void*)k_tile<NIT, 2, false>;
+    return sync ? (const void*)k_tile<NIT, 1, true> : (const void*)k_tile<NIT, 1, false>;
+}
+
+static const void* tile_fn(const KParams& k, int tpw, bool sync) {
+    if (k.cap <= 16) return tile_fn_nit<1>(tpw, sync);
+    if (k.cap <= 32) return tile_fn_nit<2>(tpw, sync);
+    return tile_fn_nit<4>(tpw, sync);
+}
+
+cudaError_t fused_max_blocks_per_sm(const KParams& k, int warps_per_block, int grain, int* out) {
+    const int tpw = tile_tpw(k, grain & 15);
+    const bool sync = (grain >> 4) & 1;
+    size_t sm = block_smem_bytes(k.cap, warps_per_block, tpw);
+    const void* fn = tile_fn(k, tpw, sync);
+    cudaError_t err = set_smem(fn, sm);
     if (err != cudaSuccess) return err;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_fused, warps_per_block * 32, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fn, warps_per_block * 32, sm);
 }
 
 cudaError_t launch_fused(const KParams& k, const KBatch& b, const KOut& o, int* cursor, int grain,
                          int warps_per_block, int n_blocks, cudaStream_t s) {
-    size_t sm = warp_smem_bytes(k.cap) * warps_per_block;
-    cudaError_t err = set_smem((const void*)k_fused, sm);
+    const int tpw = tile_tpw(k, grain & 15);
+    const bool sync = (grain >> 4) & 1;
+    size_t sm = block_smem_bytes(k.cap, warps_per_block, tpw);
+    const void* fn = tile_fn(k, tpw, sync);
+    cudaError_t err = set_smem(fn, sm);
     if (err != cudaSuccess) return err;
-    k_fused<<<n_blocks, warps_per_block * 32, sm, s>>>(k, b, o, cursor, grain);
-    return cudaGetLastError();
+    void* args[] = {(void*)&k, (void*)&b, (void*)&o, (void*)&cursor};
+    return cudaLaunchKernel(fn, dim3(n_blocks), dim3(warps_per_block * 32), args, sm, s);
 }
 
 cudaError_t launch_hits_to_raw(const uint8_t* found, int* hit_idx, const int* perm, int n_tracks, int base,

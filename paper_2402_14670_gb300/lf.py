@@ -84,7 +84,7 @@ class lf_host_output(C.Structure):
 
 class lf_tuning(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("grain", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("queue", C.c_int32)]
 
 
 _lib.lf_create.argtypes = [C.POINTER(lf_geometry), C.POINTER(lf_params), C.POINTER(_P)]
@@ -330,7 +330,7 @@ class Tracker:
             tu = None
             if tuning:
                 tu = lf_tuning(int(tuning.get("warps_per_block", 0)), int(tuning.get("blocks_per_sm", 0)),
-                               int(tuning.get("grain", 0)), 0)
+                               int(tuning.get("grain", 0)), int(tuning.get("queue", 0)))
             lf_find_tracks_batched(self.ctx, b, o, tu, _stream(stream))
         else:
             raise ValueError(mode)
@@ -384,7 +384,7 @@ class Tracker:
         tu = None
         if tuning:
             tu = lf_tuning(int(tuning.get("warps_per_block", 0)), int(tuning.get("blocks_per_sm", 0)),
-                           int(tuning.get("grain", 0)), 0)
+                           int(tuning.get("grain", 0)), int(tuning.get("queue", 0)))
         lf_process_host(self.ctx, hb, ho, tu, int(chunk_hits))
         return out
 

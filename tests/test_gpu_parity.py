@@ -81,10 +81,13 @@ def test_parameter_edges(lfm, cap, nt):
         run_both(tr, b, mode=mode, params=p, stages=(mode == "plain" and nt > 0))
 
 
-@pytest.mark.parametrize("tuning", [dict(warps_per_block=1, grain=1, blocks_per_sm=1),
-                                    dict(warps_per_block=4, grain=3),
-                                    dict(warps_per_block=16, grain=16),
-                                    dict(warps_per_block=8, grain=64, blocks_per_sm=2)])
+@pytest.mark.parametrize("tuning", [dict(queue=0, blocks_per_sm=1),
+                                    dict(queue=0),
+                                    dict(queue=2, warps_per_block=1, grain=1, blocks_per_sm=1),
+                                    dict(queue=2, warps_per_block=4, grain=2),
+                                    dict(queue=1, warps_per_block=16, grain=2),
+                                    dict(queue=1, warps_per_block=8, grain=1, blocks_per_sm=2),
+                                    dict(queue=1, warps_per_block=8, grain=2)])
 def test_launch_shapes_identical(lfm, tuning):
     b = synth.generate(1, n_events=120).to("cuda")
     tr = _tracker(lfm)
