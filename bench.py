@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--cpu-events", type=int, default=3000, help="oracle sample size (events)")
     ap.add_argument("--tuning", type=str, default=None, help="json of warps_per_block/blocks_per_sm/grain")
     return ap.parse_args()
@@ -432,6 +433,29 @@ def main():
         n_hits, n_trk = batch.n_hits, batch.n_tracks
         cpu_src = None
 
+    # ---------------- served stream: continuous batching over the pinned pool
+    served = None
+    if not args.no_serve and e2e is not None:
+        from paper_2402_14670_gb300 import serve
+        srv = serve.Server(host, n_slots=4, max_events=2048, budget_bytes=16 << 30)
+        n_sat = min(n_ev, 60000)
+        sat = srv.run(np.zeros(n_sat))
+        points = []
+        for frac in (0.25, 0.5, 0.8):
+            rate = frac * sat.events_per_s
+            n_pt = int(min(n_ev, max(2000, rate * 1.0)))
+            st = srv.run(serve.poisson_arrivals(n_pt, rate, seed=int(frac * 100)))
+            points.append({"offered_rate": rate, "offered_frac_of_served_peak": frac,
+                           "offered_frac_of_batched": rate / value, "events_per_s": st.events_per_s,
+                           "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_batch_events": st.mean_batch_events,
+                           "events": st.n_events})
+        served = {"saturation_events_per_s": sat.events_per_s, "saturation_p50_ms": sat.p50_ms,
+                  "saturation_p99_ms": sat.p99_ms, "slots": len(srv.slots), "budget_bytes": 16 << 30,
+                  "points": points,
+                  "note": "events arrive in pinned host memory; each batch is copied in, packed, followed "
+                          "and its per-track results copied back; latency = arrival to results on host"}
+        srv.close()
+
     # ---------------- roofline of the dominant kernel (persistent find)
     peak, peak_kind = peaks()
     find_avg = statistics.mean(find_ms)
@@ -479,7 +503,7 @@ def main():
                        "tuning": tuning or "defaults",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "single"},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-            "roofline": roof, "roofline_pack": roof_pack, "plain": plain, "cpu_baseline": cpu,
+            "roofline": roof, "roofline_pack": roof_pack, "plain": plain, "served": served, "cpu_baseline": cpu,
             "stage_ms": {"pack": pack_avg, "find": find_avg}, "found_tracks": n_found,
         }
         print(json.dumps(line), flush=True)

@@ -1,0 +1,91 @@
+"""Autotuner of the persistent form's launch shape.
+
+For a batch it times a small set of lf_tuning candidates (queue mode, warps
+per block, tracks per warp, resident blocks per SM) with CUDA events on the
+current stream, keeps the fastest, and caches the choice per (GPU name,
+batch bucket).  The bucket is the event-size class of the batch (mean input
+tracks per event: 1-32, 33-64, 65-128, 129-256, 257+) and its event-count
+scale (log2), the shape classes of the uneven and served workloads.  Every
+candidate gives identical results; only the launch shape differs.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import threading
+from typing import Dict, Optional, Tuple
+
+import torch
+
+CANDIDATES = [
+    dict(queue=0),                                        # persistent stage kernels
+    dict(queue=0, blocks_per_sm=2),
+    dict(queue=1, warps_per_block=8, grain=2),            # block-synchronous tile kernel
+    dict(queue=1, warps_per_block=16, grain=2),
+    dict(queue=1, warps_per_block=8, grain=1),
+]
+TRACK_EDGES = (32, 64, 128, 256)
+
+_lock = threading.Lock()
+
+
+def bucket_of(n_events: int, n_tracks: int) -> Tuple[int, int]:
+    mean = n_tracks / max(n_events, 1)
+    size_class = sum(mean > e for e in TRACK_EDGES)
+    scale = int(math.log2(max(n_events, 1)))
+    return size_class, scale
+
+
+class Autotuner:
+    def __init__(self, cache_path: Optional[str] = None, reps: int = 3):
+        self.cache_path = cache_path
+        self.reps = reps
+        self.table: Dict[str, dict] = {}
+        self.timings: Dict[str, dict] = {}
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                self.table = json.load(f)
+
+    @staticmethod
+    def _key(bucket) -> str:
+        name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+        return "%s|%d|%d" % (name, bucket[0], bucket[1])
+
+    def lookup(self, n_events: int, n_tracks: int) -> Optional[dict]:
+        return self.table.get(self._key(bucket_of(n_events, n_tracks)))
+
+    def tune(self, tracker, packed: dict, batch, n_events: int, out: Optional[dict] = None) -> dict:
+        """Time every candidate on this batch and cache the fastest."""
+        key = self._key(bucket_of(n_events, int(batch.sx.numel())))
+        stream = torch.cuda.current_stream()
+        if out is None:
+            out = tracker.alloc_output(int(batch.sx.numel()), n_events, packed["x"].device)
+        times = {}
+        for cand in CANDIDATES:
+            tracker.find(packed, batch, n_events, "batched", cand, out=out)   # capture + warm
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(self.reps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                tracker.find(packed, batch, n_events, "batched", cand, out=out)
+                b.record(stream)
+                torch.cuda.synchronize()
+                best = min(best, a.elapsed_time(b))
+            times[json.dumps(cand, sort_keys=True)] = best
+        choice = json.loads(min(times, key=times.get))
+        with _lock:
+            self.table[key] = choice
+            self.timings[key] = times
+            if self.cache_path:
+                tmp = self.cache_path + ".tmp"
+                with open(tmp, "w") as f:
+                    json.dump(self.table, f, indent=1, sort_keys=True)
+                os.replace(tmp, self.cache_path)
+        return choice
+
+    def choose(self, tracker, packed: dict, batch, n_events: int, out: Optional[dict] = None) -> dict:
+        t = self.lookup(n_events, int(batch.sx.numel()))
+        return t if t is not None else self.tune(tracker, packed, batch, n_events, out)
