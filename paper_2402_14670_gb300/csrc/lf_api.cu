@@ -294,7 +294,7 @@ lf_status lf_pack_hits(lf_ctx* c, const lf_raw_hits* raw, const lf_packed* pk, v
         return fail(c, LF_ERR_ARG, "a hit array is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     lf_status st;
-    if ((st = ensure(c, c->tmp, (size_t)raw->n_hits * 4)) != LF_OK) return st;
+    if ((st = ensure(c, c->tmp, (size_t)raw->n_hits * 20)) != LF_OK) return st;  // bucket-ordered staging
     if ((st = ensure(c, c->big_list, 2 * ((size_t)raw->n_events * NB + 1) * 4)) != LF_OK) return st;
     LF_CUDA(c, launch_pack(raw->raw_offsets, raw->x, raw->z, raw->dxdy, raw->w, raw->plane, raw->n_events,
                            raw->n_hits, pk->hit_offsets, pk->x, pk->z, pk->dxdy, pk->w, pk->layer, pk->perm,
@@ -315,7 +315,7 @@ lf_status lf_find_tracks(lf_ctx* c, const lf_batch* b, const lf_output* o, void*
     KBatch kb = to_kbatch(b);
     KOut ko = to_kout(o);
     LF_CUDA(c, launch_extend(c->kp, kb, (int*)c->trk_event.p, (int*)c->wbeg.p, (uint8_t*)c->wcnt.p,
-                             (uint64_t*)c->keys.p, (uint8_t*)c->ntrip.p, (CandRec*)c->cands.p, s));
+                             (uint64_t*)c->keys.p, (uint8_t*)c->ntrip.p, (CandRec*)c->cands.p, ko, s));
     LF_CUDA(c, launch_select(c->kp, kb, (int*)c->wbeg.p, (uint8_t*)c->ntrip.p, (CandRec*)c->cands.p, ko, s));
     LF_CUDA(c, launch_compact(b->trk_offsets, o->found, b->n_events, (int*)c->ev_count.p, o->out_offsets,
                               o->out_trk, o->n_out, s));
@@ -358,7 +358,6 @@ lf_status prepare_batched(lf_ctx* c, const lf_batch* b, const Shape& sh) {
         if ((st = ensure(c, c->wcnt, nt * NL)) != LF_OK) return st;
         if ((st = ensure(c, c->keys, nt * NT * 8)) != LF_OK) return st;
         if ((st = ensure(c, c->ntrip, nt)) != LF_OK) return st;
-        if ((st = ensure(c, c->cands, nt * NT * sizeof(CandRec))) != LF_OK) return st;
     }
     return LF_OK;
 }
@@ -385,8 +384,8 @@ lf_status launch_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const
             LF_CUDA(c, launch_track_event(kb, te, s));
             LF_CUDA(c, launch_windows(c->kp, kb, te, wb, wc, s, c->cursor + 0, stage_grid(c, sh, 0)));
             LF_CUDA(c, launch_triplets(c->kp, kb, te, wb, wc, ky, nt, s, c->cursor + 1, stage_grid(c, sh, 1)));
-            LF_CUDA(c, launch_extend(c->kp, kb, te, wb, wc, ky, nt, cd, s, c->cursor + 2, stage_grid(c, sh, 2)));
-            LF_CUDA(c, launch_select(c->kp, kb, wb, nt, cd, ko, s, c->cursor + 3, stage_grid(c, sh, 3)));
+            // the persistent extension selects and writes the output itself
+            LF_CUDA(c, launch_extend(c->kp, kb, te, wb, wc, ky, nt, cd, ko, s, c->cursor + 2, stage_grid(c, sh, 2)));
         } else {
             LF_CUDA(c, launch_fused(c->kp, kb, ko, c->cursor, sh.grain, sh.wpb, sh.bps * c->n_sm, s));
         }

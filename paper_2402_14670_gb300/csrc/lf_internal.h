@@ -99,9 +99,10 @@ cudaError_t launch_windows(const KParams& k, const KBatch& b, const int* trk_eve
 cudaError_t launch_triplets(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
                             const uint8_t* wcnt, uint64_t* keys, uint8_t* ntrip, cudaStream_t s,
                             int* cursor = nullptr, int blocks = 0);
+// with a cursor (persistent) the extension also selects and writes `o`
 cudaError_t launch_extend(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
                           const uint8_t* wcnt, const uint64_t* keys, const uint8_t* ntrip, CandRec* cands,
-                          cudaStream_t s, int* cursor = nullptr, int blocks = 0);
+                          const KOut& o, cudaStream_t s, int* cursor = nullptr, int blocks = 0);
 cudaError_t launch_select(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* ntrip,
                           const CandRec* cands, const KOut& o, cudaStream_t s, int* cursor = nullptr,
                           int blocks = 0);

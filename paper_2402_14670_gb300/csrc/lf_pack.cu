@@ -6,12 +6,14 @@
 //                   __match_any_sync), a per-bucket prefix over buckets and
 //                   warps gives the bucket offsets and each warp's cursors,
 //                   and each warp scatters its slice in order: a STABLE
-//                   scatter, so inside a bucket raw indices stay ascending.
-//   k_pack_sort     one block per event (grid-stride), so the event's raw
-//                   hits stay hot in L1/L2 while all its buckets are sorted:
-//                   buckets of at most 1024 hits by one warp each, larger
-//                   ones (at most 8192) by the whole block; a bin sort in
-//                   shared memory.
+//                   scatter of raw indices into bucket order, so inside a
+//                   bucket raw indices stay ascending.
+//   k_pack_gather   walks the packed positions in order and copies x (with
+//                   -0 -> +0), z, dxdy, w into bucket order (coalesced
+//                   writes; the raw reads stay inside the events in flight).
+//   k_pack_sort_*   buckets of at most 1024 hits by one warp each, larger
+//                   ones (at most 8192) by one block each; a bin sort in
+//                   shared memory on the contiguous bucket-ordered copy.
 //                   Bins split [min, max] of the bucket into as many equal
 //                   parts as hits (the bin is a monotone function of x); each
 //                   bin is then ordered by (x, position) with an insertion
@@ -41,9 +43,16 @@ __device__ __forceinline__ int wscan_incl(int v, int lane) {
     return v;
 }
 
+// Staging of one batch in bucket order: raw index, x (with -0 -> +0), z,
+// dxdy, w.
+struct Staged {
+    int* idx;
+    float *x, *z, *d, *w;
+};
+
 __global__ void __launch_bounds__(BUCKET_THREADS) k_pack_bucket(
     const int* __restrict__ raw_offsets, const uint8_t* __restrict__ plane, int n_events, int* hit_offsets,
-    int* tmp, int* status) {
+    int* tmp, int* big_list, int* status) {
     __shared__ int wc[BUCKET_WARPS][NB];   // per-warp counts, then per-warp cursors
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = blockIdx.x; e < n_events; e += gridDim.x) {
@@ -77,6 +86,7 @@ __global__ void __launch_bounds__(BUCKET_THREADS) k_pack_bucket(
             if (lane < NB) {
                 hit_offsets[(size_t)e * NB + lane] = start;
                 if (tot > BLOCK_SORT_MAX) atomicOr(status, 0x1);
+                else if (tot > WARP_MAX) big_list[1 + atomicAdd(big_list, 1)] = e * NB + lane;
                 int acc = start;
                 for (int w = 0; w < BUCKET_WARPS; ++w) {
                     int c = wc[w][lane];
@@ -108,6 +118,22 @@ __global__ void __launch_bounds__(BUCKET_THREADS) k_pack_bucket(
     if (blockIdx.x == 0 && tid == 0) hit_offsets[(size_t)n_events * NB] = raw_offsets[n_events];
 }
 
+// Bucket-ordered copy of the hit data: packed positions are walked in order
+// (coalesced writes); the raw reads stay inside the few events in flight, so
+// they are served by L2.
+__global__ void k_pack_gather(const float* __restrict__ x, const float* __restrict__ z,
+                              const float* __restrict__ dxdy, const float* __restrict__ w, int n_hits, Staged sg) {
+    const int stride = gridDim.x * blockDim.x;
+#pragma unroll 4
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_hits; j += stride) {
+        const int r = sg.idx[j];
+        sg.x[j] = __ldg(x + r) + 0.0f;
+        sg.z[j] = __ldg(z + r);
+        sg.d[j] = __ldg(dxdy + r);
+        sg.w[j] = __ldg(w + r);
+    }
+}
+
 __device__ __forceinline__ int bin_of(float x, float xmin, float scale, int nb) {
     float f = (x - xmin) * scale;   // monotone in x; NaN only when x == xmin and scale is infinite
     if (!(f > 0.0f)) return 0;
@@ -125,19 +151,19 @@ __device__ __forceinline__ void gsync() {
 struct SortArea {
     float* xa;
     int* bins;
-    uint16_t* pos;
+    uint16_t* pos;    // slot of each element inside its bin
+    uint16_t* pos2;   // positions in sorted order
 };
 
 // Cooperative bin sort of one bucket by a warp (BLOCK = false) or a block.
 template <bool BLOCK>
-__device__ void sort_bucket(const float* __restrict__ x, const float* __restrict__ z, const float* __restrict__ dxdy,
-                            const float* __restrict__ w, const int* __restrict__ tmp, int b0, int m, int layer,
-                            float* ox, float* oz, float* od, float* ow, uint8_t* ol, int* perm, SortArea a,
-                            int rank, int size, float* red_f, int* red_i) {
+__device__ void sort_bucket(const Staged& sg, int b0, int m, int layer, float* ox, float* oz, float* od, float* ow,
+                            uint8_t* ol, int* perm, SortArea a, int rank, int size, float* red_f, int* red_i) {
     const int lane = rank & 31, wid = rank >> 5, nw = size >> 5;
     float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+#pragma unroll 8
     for (int i = rank; i < m; i += size) {
-        float xv = __ldg(x + tmp[b0 + i]) + 0.0f;
+        float xv = sg.x[b0 + i];
         a.xa[i] = xv;
         lo = fminf(lo, xv);
         hi = fmaxf(hi, xv);
@@ -164,7 +190,8 @@ __device__ void sort_bucket(const float* __restrict__ x, const float* __restrict
     const float scale = hi > lo ? (float)nb / (hi - lo) : 0.0f;
     for (int i = rank; i < nb; i += size) a.bins[i] = 0;
     gsync<BLOCK>();
-    for (int i = rank; i < m; i += size) atomicAdd(&a.bins[bin_of(a.xa[i], lo, scale, nb)], 1);
+    // counting pass; the returned count is the element's slot inside its bin
+    for (int i = rank; i < m; i += size) a.pos[i] = (uint16_t)atomicAdd(&a.bins[bin_of(a.xa[i], lo, scale, nb)], 1);
     gsync<BLOCK>();
     {
         // exclusive scan of the bin counts: a contiguous chunk per thread
@@ -188,79 +215,86 @@ __device__ void sort_bucket(const float* __restrict__ x, const float* __restrict
         }
     }
     gsync<BLOCK>();
-    for (int i = rank; i < m; i += size) a.pos[atomicAdd(&a.bins[bin_of(a.xa[i], lo, scale, nb)], 1)] = (uint16_t)i;
+    // placement: bins[b] is the start of bin b; slot from the counting pass
+    // (positions go to a second array: the first still holds the slots)
+    for (int i = rank; i < m; i += size) {
+        int d = a.bins[bin_of(a.xa[i], lo, scale, nb)] + a.pos[i];
+        a.pos2[d] = (uint16_t)i;
+    }
     gsync<BLOCK>();
-    // bins[b] is now the end of bin b; order each bin by (x, position)
+    // order each bin by (x, position); bin b ends where bin b+1 starts
     for (int bn = rank; bn < nb; bn += size) {
-        int s = bn ? a.bins[bn - 1] : 0, e = a.bins[bn];
+        int s = a.bins[bn], e = bn + 1 < nb ? a.bins[bn + 1] : m;
         for (int i = s + 1; i < e; ++i) {
-            int pv = a.pos[i];
+            int pv = a.pos2[i];
             float xv = a.xa[pv];
             int j = i - 1;
             while (j >= s) {
-                int pj = a.pos[j];
+                int pj = a.pos2[j];
                 float xj = a.xa[pj];
                 if (!(xv < xj || (xv == xj && pv < pj))) break;
-                a.pos[j + 1] = (uint16_t)pj;
+                a.pos2[j + 1] = (uint16_t)pj;
                 --j;
             }
-            a.pos[j + 1] = (uint16_t)pv;
+            a.pos2[j + 1] = (uint16_t)pv;
         }
     }
     gsync<BLOCK>();
+#pragma unroll 4
     for (int i = rank; i < m; i += size) {
-        int pv = a.pos[i];
-        int r = tmp[b0 + pv];
-        size_t o = (size_t)b0 + i;
+        int pv = a.pos2[i];
+        size_t o = (size_t)b0 + i, q = (size_t)b0 + pv;
         ox[o] = a.xa[pv];
-        oz[o] = __ldg(z + r);
-        od[o] = __ldg(dxdy + r);
-        ow[o] = __ldg(w + r);
+        oz[o] = sg.z[q];
+        od[o] = sg.d[q];
+        ow[o] = sg.w[q];
         ol[o] = (uint8_t)layer;
-        perm[o] = r;
+        perm[o] = sg.idx[q];
     }
     gsync<BLOCK>();
 }
 
-__host__ __device__ constexpr size_t area_bytes(int n) { return (size_t)n * 4 + (size_t)n * 4 + (((size_t)n * 2 + 15) & ~size_t(15)); }
+__host__ __device__ constexpr size_t area_bytes(int n) { return (size_t)n * 12; }
 
 __device__ __forceinline__ SortArea area_at(char* p, int n) {
     SortArea a;
     a.xa = reinterpret_cast<float*>(p);
     a.bins = reinterpret_cast<int*>(p + (size_t)n * 4);
     a.pos = reinterpret_cast<uint16_t*>(p + (size_t)n * 8);
+    a.pos2 = reinterpret_cast<uint16_t*>(p + (size_t)n * 10);
     return a;
 }
 
-// One block per event: small buckets by the block's warps (each with its own
-// shared-memory area), then the large ones by the whole block (the union of
-// the warps' areas), so the event's raw hits are read while hot.
-__global__ void __launch_bounds__(SORT_THREADS) k_pack_sort(
-    const float* __restrict__ x, const float* __restrict__ z, const float* __restrict__ dxdy,
-    const float* __restrict__ w, const int* __restrict__ hit_offsets, const int* __restrict__ tmp, int n_events,
-    float* ox, float* oz, float* od, float* ow, uint8_t* ol, int* perm) {
+constexpr int SMALL_WARPS = 4;   // warps per block of the small-bucket kernel
+
+// Buckets of at most WARP_MAX hits: one warp each (grid-stride over buckets).
+__global__ void __launch_bounds__(SMALL_WARPS * 32) k_pack_sort_small(
+    const int* __restrict__ hit_offsets, Staged sg, int n_buckets, float* ox, float* oz, float* od, float* ow,
+    uint8_t* ol, int* perm) {
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const SortArea wa = area_at(smem + (size_t)warp * area_bytes(WARP_MAX), WARP_MAX);
+    for (int q = blockIdx.x * SMALL_WARPS + warp; q < n_buckets; q += gridDim.x * SMALL_WARPS) {
+        int b0 = hit_offsets[q], m = hit_offsets[q + 1] - b0;
+        if (m >= 1 && m <= WARP_MAX)
+            sort_bucket<false>(sg, b0, m, (q % NB) % NL, ox, oz, od, ow, ol, perm, wa, lane, 32, nullptr, nullptr);
+    }
+}
+
+// Buckets above WARP_MAX hits (listed by k_pack_bucket): one block each.
+__global__ void __launch_bounds__(SORT_THREADS) k_pack_sort_large(
+    const int* __restrict__ hit_offsets, const int* __restrict__ list, Staged sg, float* ox, float* oz, float* od,
+    float* ow, uint8_t* ol, int* perm) {
     extern __shared__ __align__(16) char smem[];
     __shared__ float red_f[64];
     __shared__ int red_i[32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SortArea wa = area_at(smem + (size_t)warp * area_bytes(WARP_MAX), WARP_MAX);
     const SortArea ba = area_at(smem, BLOCK_SORT_MAX);
-    for (int e = blockIdx.x; e < n_events; e += gridDim.x) {
-        const int* off = hit_offsets + (size_t)e * NB;
-        for (int q = warp; q < NB; q += SORT_THREADS / 32) {
-            int b0 = off[q], m = off[q + 1] - b0;
-            if (m >= 1 && m <= WARP_MAX)
-                sort_bucket<false>(x, z, dxdy, w, tmp, b0, m, q % NL, ox, oz, od, ow, ol, perm, wa, lane, 32,
-                                   nullptr, nullptr);
-        }
-        __syncthreads();
-        for (int q = 0; q < NB; ++q) {
-            int b0 = off[q], m = off[q + 1] - b0;
-            if (m > WARP_MAX && m <= BLOCK_SORT_MAX)
-                sort_bucket<true>(x, z, dxdy, w, tmp, b0, m, q % NL, ox, oz, od, ow, ol, perm, ba, tid,
-                                  SORT_THREADS, red_f, red_i);
-        }
-        __syncthreads();
+    const int n = list[0];
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        int q = list[1 + k];
+        int b0 = hit_offsets[q], m = hit_offsets[q + 1] - b0;
+        sort_bucket<true>(sg, b0, m, (q % NB) % NL, ox, oz, od, ow, ol, perm, ba, threadIdx.x, SORT_THREADS, red_f,
+                          red_i);
     }
 }
 
@@ -270,20 +304,41 @@ cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, 
                         const float* w, const uint8_t* plane, int n_events, int n_hits,
                         int* hit_offsets, float* ox, float* oz, float* odxdy, float* ow, uint8_t* olayer,
                         int* perm, int* tmp, int* big_list, int* status, int n_sm, cudaStream_t s) {
-    (void)n_hits;
-    (void)big_list;
     if (n_events <= 0) return cudaMemsetAsync(hit_offsets, 0, sizeof(int), s);
-    int grid = n_events < n_sm * 8 ? n_events : n_sm * 8;
-    k_pack_bucket<<<grid, BUCKET_THREADS, 0, s>>>(raw_offsets, plane, n_events, hit_offsets, tmp, status);
-    cudaError_t err = cudaGetLastError();
+    // tmp holds 5 arrays of n_hits 4-byte words: the bucket-ordered staging
+    Staged sg;
+    sg.idx = tmp;
+    sg.x = reinterpret_cast<float*>(tmp + (size_t)n_hits);
+    sg.z = sg.x + (size_t)n_hits;
+    sg.d = sg.z + (size_t)n_hits;
+    sg.w = sg.d + (size_t)n_hits;
+    cudaError_t err = cudaMemsetAsync(big_list, 0, sizeof(int), s);
     if (err != cudaSuccess) return err;
-    const size_t sm = area_bytes(BLOCK_SORT_MAX);
-    if ((err = cudaFuncSetAttribute(k_pack_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+    int grid = n_events < n_sm * 8 ? n_events : n_sm * 8;
+    k_pack_bucket<<<grid, BUCKET_THREADS, 0, s>>>(raw_offsets, plane, n_events, hit_offsets, tmp, big_list, status);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (n_hits > 0) {
+        int gg = (int)(((long)n_hits + 255) / 256);
+        if (gg > n_sm * 32) gg = n_sm * 32;
+        k_pack_gather<<<gg, 256, 0, s>>>(x, z, dxdy, w, n_hits, sg);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    const int n_buckets = n_events * NB;
+    const size_t sms = (size_t)SMALL_WARPS * area_bytes(WARP_MAX);
+    if ((err = cudaFuncSetAttribute(k_pack_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms)) !=
         cudaSuccess)
         return err;
-    int gs = n_events < n_sm * 2 ? n_events : n_sm * 2;
-    k_pack_sort<<<gs, SORT_THREADS, sm, s>>>(x, z, dxdy, w, hit_offsets, tmp, n_events, ox, oz, odxdy, ow, olayer,
-                                             perm);
+    int gsm = (n_buckets + SMALL_WARPS - 1) / SMALL_WARPS;
+    if (gsm > n_sm * 32) gsm = n_sm * 32;
+    k_pack_sort_small<<<gsm, SMALL_WARPS * 32, sms, s>>>(hit_offsets, sg, n_buckets, ox, oz, odxdy, ow, olayer,
+                                                         perm);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const size_t sml = area_bytes(BLOCK_SORT_MAX);
+    if ((err = cudaFuncSetAttribute(k_pack_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sml)) !=
+        cudaSuccess)
+        return err;
+    k_pack_sort_large<<<n_sm * 2, SORT_THREADS, sml, s>>>(hit_offsets, big_list, sg, ox, oz, odxdy, ow, olayer,
+                                                          perm);
     return cudaGetLastError();
 }
 

@@ -792,11 +792,13 @@ __global__ void k_triplets(KParams k, KBatch b, const int* __restrict__ wbeg, co
     }
 }
 
-template <int TPW>
+// SEL = false: write every candidate for the selection kernel; SEL = true:
+// select inside the 16/32-lane group and write the track's output directly.
+template <int TPW, bool SEL>
 __device__ __forceinline__ void extend_tracks(const KParams& k, const KBatch& b, const int* __restrict__ wbeg,
                                               const uint8_t* __restrict__ wcnt, const uint64_t* __restrict__ keys,
-                                              const uint8_t* __restrict__ ntrip, CandRec* cands, const Slot* sl,
-                                              int t0, int lane) {
+                                              const uint8_t* __restrict__ ntrip, CandRec* cands, const KOut& o,
+                                              const Slot* sl, int t0, int lane) {
 #pragma unroll
     for (int qq = 0; qq < TPW; ++qq) {
         int tq = t0 + qq;
@@ -810,10 +812,26 @@ __device__ __forceinline__ void extend_tracks(const KParams& k, const KBatch& b,
     const int t = t0 + q;
     Slot mq = sl[0];
     if (TPW == 2 && q == 1) mq = sl[TPW - 1];
-    if (t < b.n_tracks && r < ntrip[t]) {
+    const bool live = t < b.n_tracks;
+    const bool act = live && r < ntrip[t];
+    Cand cd;
+    cd.status = 9;
+    cd.Q = 0.0f;
+    cd.n = 0;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) cd.st[p] = 0.0f;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) cd.hl[l] = -1;
+    if (act) {
         TState s = load_state(b, t);
-        Cand cd;
         extend_fit(k, b, s, mq, keys[(size_t)t * k.n_trip + r], cd);
+    }
+    if (SEL) {
+        int hg[NL];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) hg[l] = (act && cd.status == 0 && cd.hl[l] >= 0) ? mq.h->wbeg[l] + cd.hl[l] : -1;
+        group_select_write<G>(o, t, live, r, act && cd.status == 0, cd.Q, cd.n, hg, cd.st);
+    } else if (act) {
         CandRec rec;
         rec.Q = cd.Q;
         rec.status = (int8_t)cd.status;
@@ -830,11 +848,12 @@ __device__ __forceinline__ void extend_tracks(const KParams& k, const KBatch& b,
 }
 
 // stage 3: extension and fit of every kept triplet; TPW tracks per warp
-// (two when n_triplets <= 16: lanes 0..15 and 16..31)
+// (two when n_triplets <= 16: lanes 0..15 and 16..31).  The persistent
+// variant also selects and writes the output (no candidate round trip).
 template <int TPW, bool P>
-__global__ void __launch_bounds__(PLAIN_WARPS * 32, 4) k_extend(KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ wcnt,
-                         const uint64_t* __restrict__ keys, const uint8_t* __restrict__ ntrip, CandRec* cands,
-                         int* cursor) {
+__global__ void __launch_bounds__(PLAIN_WARPS * 32, 4) k_extend(
+    KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ wcnt,
+    const uint64_t* __restrict__ keys, const uint8_t* __restrict__ ntrip, CandRec* cands, KOut o, int* cursor) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Slot sl[TPW];
@@ -842,13 +861,13 @@ __global__ void __launch_bounds__(PLAIN_WARPS * 32, 4) k_extend(KParams k, KBatc
     for (int q = 0; q < TPW; ++q) sl[q] = slot_at(smem, warp * TPW + q, k.cap);
     if (!P) {
         const int t0 = (blockIdx.x * PLAIN_WARPS + warp) * TPW;
-        if (t0 < b.n_tracks) extend_tracks<TPW>(k, b, wbeg, wcnt, keys, ntrip, cands, sl, t0, lane);
+        if (t0 < b.n_tracks) extend_tracks<TPW, false>(k, b, wbeg, wcnt, keys, ntrip, cands, o, sl, t0, lane);
         return;
     }
     for (;;) {
         const int t0 = queue_take(cursor, TPW, lane);
         if (t0 >= b.n_tracks) break;
-        extend_tracks<TPW>(k, b, wbeg, wcnt, keys, ntrip, cands, sl, t0, lane);
+        extend_tracks<TPW, true>(k, b, wbeg, wcnt, keys, ntrip, cands, o, sl, t0, lane);
     }
 }
 
@@ -1153,27 +1172,27 @@ cudaError_t launch_triplets(const KParams& k, const KBatch& b, const int* trk_ev
 
 template <int TPW, bool P>
 static cudaError_t launch_extend_t(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* wcnt,
-                                   const uint64_t* keys, const uint8_t* ntrip, CandRec* cands, cudaStream_t s,
-                                   int* cursor, int blocks) {
+                                   const uint64_t* keys, const uint8_t* ntrip, CandRec* cands, const KOut& o,
+                                   cudaStream_t s, int* cursor, int blocks) {
     size_t sm = (size_t)PLAIN_WARPS * TPW * slot_bytes(k.cap);
     cudaError_t err = set_smem((const void*)k_extend<TPW, P>, sm);
     if (err != cudaSuccess) return err;
     const int grid = P ? blocks : cdiv(b.n_tracks, PLAIN_WARPS * TPW);
-    k_extend<TPW, P><<<grid, PLAIN_WARPS * 32, sm, s>>>(k, b, wbeg, wcnt, keys, ntrip, cands, cursor);
+    k_extend<TPW, P><<<grid, PLAIN_WARPS * 32, sm, s>>>(k, b, wbeg, wcnt, keys, ntrip, cands, o, cursor);
     return cudaGetLastError();
 }
 
 cudaError_t launch_extend(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
                           const uint8_t* wcnt, const uint64_t* keys, const uint8_t* ntrip, CandRec* cands,
-                          cudaStream_t s, int* cursor, int blocks) {
+                          const KOut& o, cudaStream_t s, int* cursor, int blocks) {
     (void)trk_event;
     if (b.n_tracks <= 0) return cudaSuccess;
     if (k.n_trip <= 16) {
-        if (cursor) return launch_extend_t<2, true>(k, b, wbeg, wcnt, keys, ntrip, cands, s, cursor, blocks);
-        return launch_extend_t<2, false>(k, b, wbeg, wcnt, keys, ntrip, cands, s, nullptr, 0);
+        if (cursor) return launch_extend_t<2, true>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, cursor, blocks);
+        return launch_extend_t<2, false>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, nullptr, 0);
     }
-    if (cursor) return launch_extend_t<1, true>(k, b, wbeg, wcnt, keys, ntrip, cands, s, cursor, blocks);
-    return launch_extend_t<1, false>(k, b, wbeg, wcnt, keys, ntrip, cands, s, nullptr, 0);
+    if (cursor) return launch_extend_t<1, true>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, cursor, blocks);
+    return launch_extend_t<1, false>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, nullptr, 0);
 }
 
 cudaError_t launch_select(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* ntrip,

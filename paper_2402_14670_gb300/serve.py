@@ -32,9 +32,9 @@ from . import lf
 from .autotune import Autotuner
 
 NL = 12
-# device bytes per hit (raw 17 + packed 21 + pack scratch 4) and per input
+# device bytes per hit (raw 17 + packed 21 + pack staging 20) and per input
 # track (states 20, outputs 81, stage-pipeline scratch ~733)
-BYTES_PER_HIT = 42
+BYTES_PER_HIT = 58
 BYTES_PER_TRACK = 834
 
 
