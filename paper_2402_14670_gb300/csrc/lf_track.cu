@@ -242,14 +242,16 @@ __device__ __forceinline__ Scratch scratch_at(char* base, int i) {
 }
 
 // Copy x and z of the window hits into the slot: the (layer, hit) pairs of
-// all twelve windows are flattened over the lanes so that several loads are
-// in flight per lane; a window whose hits do not all share one z is flagged.
+// the windows (all twelve, or the six x layers when XONLY) are flattened over
+// the lanes so that several loads are in flight per lane; a window whose
+// hits do not all share one z is flagged.
+template <bool XONLY = false>
 __device__ __forceinline__ void stage_windows(const KParams& k, const KBatch& b, const Slot& m, int lane) {
     const int cap = k.cap;
     int off[NL + 1];
     off[0] = 0;
 #pragma unroll
-    for (int l = 0; l < NL; ++l) off[l + 1] = off[l] + m.h->wcnt[l];
+    for (int l = 0; l < NL; ++l) off[l + 1] = off[l] + ((XONLY && !is_x(l)) ? 0 : m.h->wcnt[l]);
     if (lane < NL) m.h->zuni[lane] = 1;
     __syncwarp();
     const int total = off[NL];
@@ -295,15 +297,35 @@ __device__ __forceinline__ void warp_sort64(uint64_t& a, uint64_t& b, int lane) 
     }
 }
 
+// Bitonic sort of 32 keys, one per lane, ascending.
+__device__ __forceinline__ uint64_t warp_sort32(uint64_t v, int lane) {
+#pragma unroll
+    for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            uint64_t o = shfl_xor64(v, j);
+            bool lower = (lane & j) == 0;
+            bool up = (lane & kk) == 0;
+            v = (lower == up) ? (v < o ? v : o) : (v < o ? o : v);
+        }
+    }
+    return v;
+}
+
 // Sort the buffered keys; keep the NT smallest at the front of the buffer.
 // Returns the new buffer size; thr becomes the NT-th smallest key once the
 // buffer holds NT keys (no later key at or above it can be kept).
 __device__ __forceinline__ int select_buffer(const Scratch& sc, int nb, int NT, uint64_t& thr, int lane,
                                              uint64_t& mine) {
     uint64_t a = lane < nb ? sc.cand[lane] : NOKEY;
-    uint64_t b = lane + 32 < nb ? sc.cand[lane + 32] : NOKEY;
     __syncwarp();
-    warp_sort64(a, b, lane);
+    if (nb <= 32) {
+        a = warp_sort32(a, lane);
+    } else {
+        uint64_t b = lane + 32 < nb ? sc.cand[lane + 32] : NOKEY;
+        __syncwarp();
+        warp_sort64(a, b, lane);
+    }
     int keep = nb < NT ? nb : NT;
     if (lane < keep) sc.cand[lane] = a;
     mine = lane < keep ? a : NOKEY;
@@ -355,14 +377,15 @@ __device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState&
                     // with the largest tolerance the slopes inside allow, and
                     // below p_bend with the bending sign; widen by a slack far
                     // above the rounding of the exact tests applied later
-                    float r = (k.z_magnet - z0) / dzl;
+                    // (bounds only: approximate division, far inside the slack)
+                    float ir = __fdividef(dzl, k.z_magnet - z0);     // 1/r
                     float slack = 0.5f + 1e-4f * (fabsf(x0) + fabsf(x_mag_in));
-                    float lo = x0 + (x_mag_in - x0 + k.magtol_max) / r - slack;
-                    float hi = x0 + (x_mag_in - x0 - k.magtol_max) / r + slack;
-                    float txm = fmaxf(fabsf(lo - x0), fabsf(hi - x0)) / dzl;
+                    float lo = x0 + (x_mag_in - x0 + k.magtol_max) * ir - slack;
+                    float hi = x0 + (x_mag_in - x0 - k.magtol_max) * ir + slack;
+                    float txm = __fdividef(fmaxf(fabsf(lo - x0), fabsf(hi - x0)), dzl);
                     float t2 = fminf(fmaxf(tol_base + k.magtol_tx * txm, k.magtol_min), k.magtol_max);
-                    lo = x0 + (x_mag_in - x0 + t2) / r - slack;
-                    hi = x0 + (x_mag_in - x0 - t2) / r + slack;
+                    lo = x0 + (x_mag_in - x0 + t2) * ir - slack;
+                    hi = x0 + (x_mag_in - x0 - t2) * ir + slack;
                     if (f1) {
                         float xb = x0 + s.txs * dzl;
                         if (bend > 0.0f) lo = fmaxf(lo, xb - slack); else hi = fminf(hi, xb + slack);
@@ -763,7 +786,7 @@ __device__ __forceinline__ void triplets_track(const KParams& k, const KBatch& b
                                                const uint8_t* __restrict__ wcnt, uint64_t* keys, uint8_t* ntrip,
                                                const Slot& m, const Scratch& sc, int t, int lane) {
     load_windows(wbeg, wcnt, t, m, lane);
-    stage_windows(k, b, m, lane);
+    stage_windows<true>(k, b, m, lane);
     TState s = load_state(b, t);
     int nt;
     uint64_t top = triplet_scan<NIT>(k, s, m, sc, lane, nt);
