@@ -97,6 +97,24 @@ typedef struct {
     float magtol_min, magtol_max, magtol_c, magtol_tx; /* clamp(min + c/p + tx*|t_x|, min, max) */
     float T_triplet, T_x, T_uv_scale, T_uv_min, T_ty, T_y, T_Q;
     float C_n[4];              /* C(9), C(10), C(11), C(12) */
+    /* Sec. "No-UT tuning": input tracks without a momentum estimate.
+     * no_ut = 0: VELO-UT input, sqop is used.  no_ut = 1: sqop is ignored; the
+     * windows assume the momentum 1/ip with ip = min(1/p_min, sin(theta)/pt_min)
+     * (the tighter threshold), x_tol = ip*(c0 + tx(c1 + c2 tx) + ty^2(c3 +
+     * tx(c4 + c5 tx)) + ip(c6 tx + c7 ip)) (Eq. tol_noUT), and every input
+     * track gets two window sets (Eq. noUT_size_window): side 0 =
+     * [x - x_tol, x + x_overlap], side 1 = [x - x_overlap, x + x_tol] around
+     * the straight-line extrapolation x (u/v: uv_tol around the
+     * stereo-corrected line).  Triplets are seeded per side and the
+     * n_triplets smallest of both sides are kept, ordered by (chi2, side,
+     * configuration, h0, h2); a triplet is extended in its own side's
+     * windows.  Supported by lf_find_tracks and lf_find_tracks_batched with
+     * queue 0; the tile kernel (queue 1, 2) and lf_find_tracks_static
+     * return LF_ERR_ARG. */
+    int32_t no_ut;             /* 0 or 1 */
+    float p_min, pt_min;       /* GeV, > 0 */
+    float x_overlap;           /* mm, >= 0 */
+    float tol_c[8];            /* c0..c7 (Table poly_tol) */
 } lf_params;
 
 /* Raw hits of n_events events, unsorted inside each event (device). */

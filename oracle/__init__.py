@@ -45,6 +45,10 @@ def default_geometry() -> dict:
         kappa=1.2, gamma=2.4e-9, dratio=4e-4, polarity=1)
 
 
+#: Table poly_tol: c0..c7 of Eq. tol_noUT.
+TOL_C = (4824.3, 426.3, 7071.1, 12080.4, 14077.8, 13909.3, 9315.3, 3209.5)
+
+
 #: "Forward" column of Table tolerances and Table C_nhits.
 def default_params(paper_K: bool = False) -> dict:
     return dict(
@@ -64,7 +68,25 @@ def default_params(paper_K: bool = False) -> dict:
         T_triplet=8.0, T_x=2.0,
         T_uv_scale=50.0, T_uv_min=2.0,     # T_uv = max(2, 50 (|t_x| + |t_y|))
         T_ty=0.02, T_y=800.0, T_Q=0.5,
-        C_n=[5.0, 1.0, 0.8, 0.5])
+        C_n=[5.0, 1.0, 0.8, 0.5],
+        # Sec. "No-UT tuning" (used when no_ut = 1): assumed momentum from
+        # p >= 5 GeV or pT >= 1 GeV, whichever is tighter; 5 mm overlap of
+        # the two one-sided windows; c0..c7 of Table poly_tol
+        no_ut=0, p_min=5.0, pt_min=1.0, x_overlap=5.0,
+        tol_c=list(TOL_C))
+
+
+#: "Forward no-UT" column of Table tolerances with the no-UT window and
+#: seeding constants of Sec. "No-UT tuning": 1200 mm u/v tolerance, a fixed
+#: 10 mm tolerance at the magnet, 64 hits per window, 20 triplets.
+def no_ut_params() -> dict:
+    p = default_params()
+    p.update(no_ut=1, uv_tol=1200.0, n_hits_window=64, n_triplets=20,
+             magtol_min=10.0, magtol_max=10.0, magtol_c=0.0, magtol_tx=0.0,
+             T_triplet=2.0, T_x=0.5,
+             T_uv_scale=15.0, T_uv_min=0.5,    # T_uv = max(T_x, 15 (|t_x| + |t_y|))
+             T_ty=0.003, T_y=800.0, T_Q=0.5)
+    return p
 
 
 # ------------------------------------------------------------------ ctypes
@@ -84,7 +106,8 @@ class _Par(C.Structure):
                 ("magtol_c", C.c_float), ("magtol_tx", C.c_float), ("T_triplet", C.c_float),
                 ("T_x", C.c_float), ("T_uv_scale", C.c_float), ("T_uv_min", C.c_float),
                 ("T_ty", C.c_float), ("T_y", C.c_float), ("T_Q", C.c_float),
-                ("C_n", C.c_float * 4)]
+                ("C_n", C.c_float * 4), ("no_ut", C.c_int32), ("p_min", C.c_float),
+                ("pt_min", C.c_float), ("x_overlap", C.c_float), ("tol_c", C.c_float * 8)]
 
 
 _P = C.c_void_p
@@ -141,8 +164,8 @@ def _geo(g: dict) -> _Geo:
 def _par(p: dict) -> _Par:
     s = _Par()
     for name, _ in _Par._fields_:
-        if name == "C_n":
-            s.C_n[:] = [float(v) for v in p["C_n"]]
+        if name in ("C_n", "tol_c"):
+            getattr(s, name)[:] = [float(v) for v in p[name]]
         else:
             setattr(s, name, p[name])
     return s
@@ -158,14 +181,15 @@ def _c(a, dt):
 
 # ------------------------------------------------------------------ API
 
-def _alloc_out(n_trk: int, dumps: bool):
+def _alloc_out(n_trk: int, dumps: bool, n_sides: int = 1):
+    nw = n_trk * n_sides * NL
     o = dict(found=np.zeros(n_trk, np.uint8), nhits=np.zeros(n_trk, np.uint8),
              hit_idx=np.zeros(n_trk * NL, np.int32), state=np.zeros(n_trk * 6, np.float32),
              quality=np.zeros(n_trk, np.float32))
     if dumps:
-        o.update(win_begin=np.zeros(n_trk * NL, np.int32), win_count=np.zeros(n_trk * NL, np.int32),
-                 win_xmin=np.zeros(n_trk * NL, np.float32), win_xmax=np.zeros(n_trk * NL, np.float32),
-                 win_centre=np.zeros(n_trk * NL, np.float32), n_trip=np.zeros(n_trk, np.int32),
+        o.update(win_begin=np.zeros(nw, np.int32), win_count=np.zeros(nw, np.int32),
+                 win_xmin=np.zeros(nw, np.float32), win_xmax=np.zeros(nw, np.float32),
+                 win_centre=np.zeros(nw, np.float32), n_trip=np.zeros(n_trk, np.int32),
                  trip=np.full(n_trk * MAX_TRIP * 4, -1, np.int32),
                  trip_chi2=np.zeros(n_trk * MAX_TRIP, np.float32),
                  cand_status=np.full(n_trk * MAX_TRIP, -1, np.int32),
@@ -177,13 +201,14 @@ def _alloc_out(n_trk: int, dumps: bool):
     return o, st
 
 
-def _shape(o: dict, n_trk: int) -> dict:
+def _shape(o: dict, n_trk: int, n_sides: int = 1) -> dict:
+    """Per-track views; window dumps are (n_trk, n_sides*12), side-major."""
     r = dict(o)
     r["hit_idx"] = o["hit_idx"].reshape(n_trk, NL)
     r["state"] = o["state"].reshape(n_trk, 6)
     if "win_begin" in o:
         for k in ("win_begin", "win_count", "win_xmin", "win_xmax", "win_centre"):
-            r[k] = o[k].reshape(n_trk, NL)
+            r[k] = o[k].reshape(n_trk, n_sides * NL)
         r["trip"] = o["trip"].reshape(n_trk, MAX_TRIP, 4)
         r["trip_chi2"] = o["trip_chi2"].reshape(n_trk, MAX_TRIP)
         r["cand_status"] = o["cand_status"].reshape(n_trk, MAX_TRIP)
@@ -228,14 +253,16 @@ class Oracle:
         and sx, sy, stx, sty, sqop.  Returns per-track outputs (and, single
         threaded, the stage dumps)."""
         g = _geo(geometry or default_geometry())
-        p = _par(params or default_params())
+        params = params or default_params()
+        n_sides = 2 if params.get("no_ut", 0) else 1
+        p = _par(params)
         ho = _c(packed["hit_offsets"], np.int32)
         n_ev = (ho.size - 1) // NB
         hx, hz, hd, hw = (_c(packed[k], np.float32) for k in ("x", "z", "dxdy", "w"))
         to = _c(states["trk_offsets"], np.int32)
         s = [_c(states[k], np.float32) for k in ("sx", "sy", "stx", "sty", "sqop")]
         n_trk = s[0].size
-        o, st = _alloc_out(n_trk, dumps and n_threads == 1)
+        o, st = _alloc_out(n_trk, dumps and n_threads == 1, n_sides)
         if n_threads == 1:
             x64a = None if x64 is None else _c(x64, np.float64)
             rc = self.lib.lfo_find_tracks(C.byref(g), C.byref(p), C.c_int32(n_ev), _ptr(ho), _ptr(hx),
@@ -248,7 +275,7 @@ class Oracle:
                                              *[_ptr(a) for a in s], C.byref(st), C.c_int32(n_threads))
         if rc != 0:
             raise ValueError("lfo_find_tracks failed (%d)" % rc)
-        return _shape(o, n_trk)
+        return _shape(o, n_trk, n_sides)
 
     def compact(self, trk_offsets, found):
         to = _c(trk_offsets, np.int32)

@@ -12,6 +12,10 @@
  *   quality      Sec. "Quality Filter" (y fit, T_ty, Q_x, Q_y, Q, C(n_hits)
  *                from Table C_nhits, T_Q)
  *   state        Sec. "Calculation of momentum and track states", linear kick.
+ *   no-UT        Sec. "No-UT tuning": straight-line extrapolation of a VELO
+ *                track, assumed minimum momentum, Eq. tol_noUT window
+ *                tolerance, the two one-sided windows of Eq.
+ *                noUT_size_window, seeding per charge assumption.
  * Where the paper leaves a choice open the reading used is stated inline.
  *
  * Searches are plain linear scans and the triplet stage enumerates every
@@ -137,6 +141,29 @@ static int32_t first_gt(const float* x, int32_t lo, int32_t hi, float v)
     return i;
 }
 
+/* Hits of bucket [b, e) inside [xmin, xmax]; above n_hits^window of them,
+ * the n_hits^window placed symmetrically around the centre are kept. */
+static void fill_window(const float* hx, int32_t b, int32_t e, float xmin, float xmax, float centre,
+                        int cap, win_t* W, int l)
+{
+    int32_t lo = first_ge(hx, b, e, xmin);
+    int32_t hi = first_gt(hx, lo, e, xmax);
+    int32_t cnt = hi - lo;
+    int32_t start = lo;
+    if (cnt > cap) {
+        int32_t c = first_ge(hx, lo, hi, centre);
+        start = c - cap / 2;
+        if (start > hi - cap) start = hi - cap;
+        if (start < lo) start = lo;
+        cnt = cap;
+    }
+    W->begin[l] = start;
+    W->count[l] = cnt;
+    W->xmin[l] = xmin;
+    W->xmax[l] = xmax;
+    W->centre[l] = centre;
+}
+
 static void track_windows(const lfo_geometry* g, const lfo_params* p, const int32_t* ev_off,
                           const float* hx, const state_t* s, win_t* W)
 {
@@ -150,7 +177,6 @@ static void track_windows(const lfo_geometry* g, const lfo_params* p, const int3
     float a_right = ((!qpos && mu) || (qpos && !mu)) ? p->x_asym : 0.0f;
     float pol = (float)g->polarity;
     float tx_f = s->txs + (pol * g->kappa) * s->qop;
-    int cap = p->n_hits_window;
 
     for (int l = 0; l < LFO_NL; ++l) {
         float centre, xmin, xmax;
@@ -166,24 +192,62 @@ static void track_windows(const lfo_geometry* g, const lfo_params* p, const int3
             xmin = centre - p->uv_tol;
             xmax = centre + p->uv_tol;
         }
-        int32_t b = ev_off[zone * LFO_NL + l], e = ev_off[zone * LFO_NL + l + 1];
-        int32_t lo = first_ge(hx, b, e, xmin);
-        int32_t hi = first_gt(hx, lo, e, xmax);
-        int32_t cnt = hi - lo;
-        int32_t start = lo;
-        if (cnt > cap) {
-            /* keep n_hits^window hits placed symmetrically around the centre */
-            int32_t c = first_ge(hx, lo, hi, centre);
-            start = c - cap / 2;
-            if (start > hi - cap) start = hi - cap;
-            if (start < lo) start = lo;
-            cnt = cap;
+        fill_window(hx, ev_off[zone * LFO_NL + l], ev_off[zone * LFO_NL + l + 1], xmin, xmax, centre,
+                    p->n_hits_window, W, l);
+    }
+}
+
+/* Sec. "No-UT tuning": the momentum is unknown, so the windows assume the
+ * lowest one searched for.  Of the two thresholds (p_min, and pt_min turned
+ * into a momentum with the track's polar angle, p = pt_min / sin(theta)) the
+ * tighter, i.e. the higher momentum, is used; returned as 1/p. */
+static float assumed_inv_p(const lfo_params* p, const state_t* s)
+{
+    float t2 = s->txs * s->txs + s->tys * s->tys;
+    float sin_theta = sqrtf(t2) / sqrtf(1.0f + t2);
+    float ip_pt = sin_theta / p->pt_min;
+    float ip_p = 1.0f / p->p_min;
+    return fminf(ip_p, ip_pt);
+}
+
+/* Eq. tol_noUT with the coefficients of Table poly_tol, ip = 1/p_Velo */
+static float no_ut_xtol(const lfo_params* p, float ip, float tx, float ty)
+{
+    const float* c = p->tol_c;
+    float a = c[0] + tx * (c[1] + c[2] * tx);
+    float b = (ty * ty) * (c[3] + tx * (c[4] + c[5] * tx));
+    float d = ip * (c[6] * tx + c[7] * ip);
+    return ip * ((a + b) + d);
+}
+
+/* Windows of one charge assumption (Eq. noUT_size_window): side 0 reaches
+ * x_tol below the straight-line extrapolation and x_overlap above it, side 1
+ * the mirror image.  The u/v windows are built the same way around the
+ * stereo-corrected straight line from the neighbouring x layer, with the u/v
+ * tolerance.  The window centre, around which a full window is capped, is
+ * the extrapolated position (as for VELO-UT input). */
+static void track_windows_no_ut(const lfo_geometry* g, const lfo_params* p, const int32_t* ev_off,
+                                const float* hx, const state_t* s, int side, win_t* W)
+{
+    int zone = (s->tys >= 0.0f) ? 1 : 0;
+    float ip = assumed_inv_p(p, s);
+    float x_tol = no_ut_xtol(p, ip, s->txs, s->tys);
+    for (int l = 0; l < LFO_NL; ++l) {
+        float centre, tol;
+        if (IS_X[l]) {
+            centre = s->xs + s->txs * (g->z[l] - g->z_state);
+            tol = x_tol;
+        } else {
+            int n = neighbour_x(l);
+            float xn = s->xs + s->txs * (g->z[n] - g->z_state);
+            float yl = s->ys + s->tys * (g->z[l] - g->z_state);
+            centre = (xn + s->txs * (g->z[l] - g->z[n])) - yl * g->dxdy[l];
+            tol = p->uv_tol;
         }
-        W->begin[l] = start;
-        W->count[l] = cnt;
-        W->xmin[l] = xmin;
-        W->xmax[l] = xmax;
-        W->centre[l] = centre;
+        float xmin = side ? centre - p->x_overlap : centre - tol;
+        float xmax = side ? centre + tol : centre + p->x_overlap;
+        fill_window(hx, ev_off[zone * LFO_NL + l], ev_off[zone * LFO_NL + l + 1], xmin, xmax, centre,
+                    p->n_hits_window, W, l);
     }
 }
 
@@ -201,7 +265,7 @@ static int32_t closest(const float* hx, int32_t b, int32_t n, float e)
 
 /* -------------------------------------------------------------- triplets */
 
-typedef struct { float chi2; int32_t cfg, h0, h1, h2; } trip_t;
+typedef struct { float chi2; int32_t side, cfg, h0, h1, h2; } trip_t;
 
 static int trip_cmp(const void* a, const void* b)
 {
@@ -209,58 +273,71 @@ static int trip_cmp(const void* a, const void* b)
     const trip_t* q = (const trip_t*)b;
     if (p->chi2 < q->chi2) return -1;
     if (p->chi2 > q->chi2) return 1;
+    if (p->side != q->side) return p->side < q->side ? -1 : 1;
     if (p->cfg != q->cfg) return p->cfg < q->cfg ? -1 : 1;
     if (p->h0 != q->h0) return p->h0 < q->h0 ? -1 : 1;
     return (p->h2 > q->h2) - (p->h2 < q->h2);
 }
 
 /* All triplets passing the doublet filters and chi2_triplet < T_triplet, then
- * the n_triplets smallest by (chi2, configuration, h0, h2). */
+ * the n_triplets smallest by (chi2, side, configuration, h0, h2).  With
+ * VELO-UT input there is one window set (side 0); the no-UT variant seeds
+ * each charge assumption in its own window set and pools the triplets. */
 static int track_triplets(const lfo_geometry* g, const lfo_params* p, const float* hx,
-                          const float* hz, const state_t* s, const win_t* W,
+                          const float* hz, const state_t* s, const win_t* Ws, int n_sides,
                           trip_t* buf, trip_t* out)
 {
-    float pmom = 1.0f / fabsf(s->qop);
     float x_mag_in = s->xs + s->txs * (g->z_magnet - g->z_state);
     float pol = (float)g->polarity;
-    float bend = (s->qop > 0.0f) ? pol : -pol;  /* sign of the expected slope change */
-    float tol_base = p->magtol_min + p->magtol_c / pmom;
     int nb = 0;
-    for (int cfg = 0; cfg < 2; ++cfg) {
-        int L0 = CFG_L[cfg][0], L1 = CFG_L[cfg][1], L2 = CFG_L[cfg][2];
-        float K = cfg == 0 ? p->K_first : p->K_last;
-        float z1 = g->z[L1];
-        for (int32_t i0 = 0; i0 < W->count[L0]; ++i0) {
-            int32_t h0 = W->begin[L0] + i0;
-            float x0 = hx[h0], z0 = hz[h0];
-            for (int32_t i2 = 0; i2 < W->count[L2]; ++i2) {
-                int32_t h2 = W->begin[L2] + i2;
-                float x2 = hx[h2], z2 = hz[h2];
-                float tx_d = (x2 - x0) / (z2 - z0);
-                /* filter 1: below p_bend the doublet must bend the way the charge says */
-                if (pmom < p->p_bend) {
-                    float d = tx_d - s->txs;
-                    int ok = (bend > 0.0f) ? (d > 0.0f) : (d < 0.0f);
-                    if (!ok) continue;
+    for (int side = 0; side < n_sides; ++side) {
+        const win_t* W = &Ws[side];
+        float pmom, bend;  /* momentum, and the sign of the expected slope change */
+        if (p->no_ut) {
+            pmom = 1.0f / assumed_inv_p(p, s);
+            bend = side ? 1.0f : -1.0f;  /* side 1 holds the tracks bending to larger x */
+        } else {
+            pmom = 1.0f / fabsf(s->qop);
+            bend = (s->qop > 0.0f) ? pol : -pol;
+        }
+        float tol_base = p->magtol_min + p->magtol_c / pmom;
+        for (int cfg = 0; cfg < 2; ++cfg) {
+            int L0 = CFG_L[cfg][0], L1 = CFG_L[cfg][1], L2 = CFG_L[cfg][2];
+            float K = cfg == 0 ? p->K_first : p->K_last;
+            float z1 = g->z[L1];
+            for (int32_t i0 = 0; i0 < W->count[L0]; ++i0) {
+                int32_t h0 = W->begin[L0] + i0;
+                float x0 = hx[h0], z0 = hz[h0];
+                for (int32_t i2 = 0; i2 < W->count[L2]; ++i2) {
+                    int32_t h2 = W->begin[L2] + i2;
+                    float x2 = hx[h2], z2 = hz[h2];
+                    float tx_d = (x2 - x0) / (z2 - z0);
+                    /* filter 1: below p_bend the doublet must bend the way the charge says */
+                    if (pmom < p->p_bend) {
+                        float d = tx_d - s->txs;
+                        int ok = (bend > 0.0f) ? (d > 0.0f) : (d < 0.0f);
+                        if (!ok) continue;
+                    }
+                    /* filter 2: x opening at the magnet centre within a p- and slope-dependent tolerance */
+                    float x_mag_d = x0 + tx_d * (g->z_magnet - z0);
+                    float tol = tol_base + p->magtol_tx * fabsf(tx_d);
+                    tol = fminf(fmaxf(tol, p->magtol_min), p->magtol_max);
+                    if (!(fabsf(x_mag_d - x_mag_in) < tol)) continue;
+                    /* upgrade to a triplet with the closest hit to x1_expected */
+                    float x1_exp = z1 * tx_d + (x0 - tx_d * z0) * K;
+                    int32_t h1 = closest(hx, W->begin[L1], W->count[L1], x1_exp);
+                    if (h1 < 0) continue;
+                    float dx = hx[h1] - x1_exp;
+                    float chi2 = dx * dx;
+                    if (!(chi2 < p->T_triplet)) continue;
+                    buf[nb].chi2 = chi2;
+                    buf[nb].side = side;
+                    buf[nb].cfg = cfg;
+                    buf[nb].h0 = h0;
+                    buf[nb].h1 = h1;
+                    buf[nb].h2 = h2;
+                    ++nb;
                 }
-                /* filter 2: x opening at the magnet centre within a p- and slope-dependent tolerance */
-                float x_mag_d = x0 + tx_d * (g->z_magnet - z0);
-                float tol = tol_base + p->magtol_tx * fabsf(tx_d);
-                tol = fminf(fmaxf(tol, p->magtol_min), p->magtol_max);
-                if (!(fabsf(x_mag_d - x_mag_in) < tol)) continue;
-                /* upgrade to a triplet with the closest hit to x1_expected */
-                float x1_exp = z1 * tx_d + (x0 - tx_d * z0) * K;
-                int32_t h1 = closest(hx, W->begin[L1], W->count[L1], x1_exp);
-                if (h1 < 0) continue;
-                float dx = hx[h1] - x1_exp;
-                float chi2 = dx * dx;
-                if (!(chi2 < p->T_triplet)) continue;
-                buf[nb].chi2 = chi2;
-                buf[nb].cfg = cfg;
-                buf[nb].h0 = h0;
-                buf[nb].h1 = h1;
-                buf[nb].h2 = h2;
-                ++nb;
             }
         }
     }
@@ -486,7 +563,8 @@ static int find_event_range(const lfo_geometry* g, const lfo_params* p, int32_t 
                             lfo_output* out)
 {
     int cap = p->n_hits_window;
-    trip_t* buf = (trip_t*)malloc(sizeof(trip_t) * 2 * (size_t)cap * (size_t)cap + sizeof(trip_t));
+    const int n_sides = p->no_ut ? 2 : 1;
+    trip_t* buf = (trip_t*)malloc(sizeof(trip_t) * 2 * (size_t)n_sides * (size_t)cap * (size_t)cap + sizeof(trip_t));
     if (!buf) return -2;
     trip_t trips[LFO_MAX_TRIP];
     cand_t cd;
@@ -494,23 +572,30 @@ static int find_event_range(const lfo_geometry* g, const lfo_params* p, int32_t 
         const int32_t* ev_off = hit_offsets + (size_t)e * LFO_NB;
         for (int32_t t = trk_offsets[e]; t < trk_offsets[e + 1]; ++t) {
             state_t s = {sx[t], sy[t], stx[t], sty[t], sqop[t]};
-            win_t W;
-            track_windows(g, p, ev_off, x, &s, &W);
-            if (out->win_begin) for (int l = 0; l < LFO_NL; ++l) {
-                out->win_begin[(size_t)t * LFO_NL + l] = W.begin[l];
-                out->win_count[(size_t)t * LFO_NL + l] = W.count[l];
+            win_t Ws[2];
+            if (p->no_ut) {
+                track_windows_no_ut(g, p, ev_off, x, &s, 0, &Ws[0]);
+                track_windows_no_ut(g, p, ev_off, x, &s, 1, &Ws[1]);
+            } else {
+                track_windows(g, p, ev_off, x, &s, &Ws[0]);
+            }
+            if (out->win_begin) for (int sd = 0; sd < n_sides; ++sd) for (int l = 0; l < LFO_NL; ++l) {
+                size_t i = ((size_t)t * n_sides + sd) * LFO_NL + l;
+                out->win_begin[i] = Ws[sd].begin[l];
+                out->win_count[i] = Ws[sd].count[l];
                 if (out->win_xmin) {
-                    out->win_xmin[(size_t)t * LFO_NL + l] = W.xmin[l];
-                    out->win_xmax[(size_t)t * LFO_NL + l] = W.xmax[l];
-                    out->win_centre[(size_t)t * LFO_NL + l] = W.centre[l];
+                    out->win_xmin[i] = Ws[sd].xmin[l];
+                    out->win_xmax[i] = Ws[sd].xmax[l];
+                    out->win_centre[i] = Ws[sd].centre[l];
                 }
             }
-            int nt = track_triplets(g, p, x, z, &s, &W, buf, trips);
+            int nt = track_triplets(g, p, x, z, &s, Ws, n_sides, buf, trips);
             if (out->n_trip) {
                 out->n_trip[t] = nt;
                 for (int r = 0; r < nt; ++r) {
                     int32_t* q = out->trip + ((size_t)t * LFO_MAX_TRIP + r) * 4;
-                    q[0] = trips[r].cfg; q[1] = trips[r].h0; q[2] = trips[r].h1; q[3] = trips[r].h2;
+                    q[0] = trips[r].cfg + 2 * trips[r].side;
+                    q[1] = trips[r].h0; q[2] = trips[r].h1; q[3] = trips[r].h2;
                     out->trip_chi2[(size_t)t * LFO_MAX_TRIP + r] = trips[r].chi2;
                 }
             }
@@ -519,7 +604,8 @@ static int find_event_range(const lfo_geometry* g, const lfo_params* p, int32_t 
             cand_t bc;
             memset(&bc, 0, sizeof bc);
             for (int r = 0; r < nt; ++r) {
-                extend_fit(g, p, x, z, dxdy, w, &s, &W, &trips[r], &cd);
+                /* the triplet's own window set: its charge assumption */
+                extend_fit(g, p, x, z, dxdy, w, &s, &Ws[trips[r].side], &trips[r], &cd);
                 if (out->cand_status) {
                     out->cand_status[(size_t)t * LFO_MAX_TRIP + r] = cd.status;
                     out->cand_q[(size_t)t * LFO_MAX_TRIP + r] = cd.Q;
@@ -561,6 +647,8 @@ static int check_params(const lfo_params* p)
     if (p->n_hits_window < 1 || p->n_hits_window > 64) return -3;
     if (p->n_triplets < 0 || p->n_triplets > LFO_MAX_TRIP) return -3;
     if (p->min_hits < 9 || p->min_hits > 12) return -3;
+    if (p->no_ut != 0 && p->no_ut != 1) return -3;
+    if (p->no_ut && !(p->p_min > 0.0f && p->pt_min > 0.0f && p->x_overlap >= 0.0f)) return -3;
     return 0;
 }
 

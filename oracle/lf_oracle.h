@@ -47,14 +47,20 @@ typedef struct {
     float magtol_min, magtol_max, magtol_c, magtol_tx; /* doublet tolerance at the magnet */
     float T_triplet, T_x, T_uv_scale, T_uv_min, T_ty, T_y, T_Q;
     float C_n[4];               /* C(9), C(10), C(11), C(12) */
+    /* Sec. "No-UT tuning": VELO-only input, q/p unknown */
+    int32_t no_ut;              /* 0: VELO-UT input (q/p used), 1: no-UT variant */
+    float p_min, pt_min;        /* assumed momentum: the tighter of p_min and pt_min / sin(theta) */
+    float x_overlap;            /* overlap of the two one-sided windows (mm) */
+    float tol_c[8];             /* c0..c7 of Eq. tol_noUT (Table poly_tol) */
 } lfo_params;
 
 /* Outputs of lfo_find_tracks.  Per input track t (global index):
  *   found[t], nhits[t], hit_idx[t*12 + layer] (packed hit index or -1),
  *   state[t*6 + k] = (x, y, tx, ty, c, q/p) at z_ref, quality[t].
- * Optional stage dumps (NULL to skip):
- *   win_begin/win_count [t*12+l], win_xmin/xmax/centre [t*12+l],
- *   n_trip[t], trip[(t*32 + r)*4 + {cfg,h0,h1,h2}], trip_chi2[t*32 + r],
+ * Optional stage dumps (NULL to skip); S = 1 window set per track, 2 in the
+ * no-UT variant (side 0 the window below the straight line, 1 above):
+ *   win_begin/win_count [(t*S + side)*12 + l], win_xmin/xmax/centre alike,
+ *   n_trip[t], trip[(t*32 + r)*4 + {cfg + 2*side, h0, h1, h2}], trip_chi2[t*32 + r],
  *   cand_status[t*32 + r] (0 accepted, else the first failed requirement),
  *   cand_q[t*32 + r], state64[t*6 + k] (binary64 refit of the selected hits). */
 typedef struct {

@@ -111,6 +111,15 @@ lf_status check_params(lf_ctx* c, const lf_geometry* g, const lf_params* p) {
     if (!(g->z_magnet < g->z[0])) return fail(c, LF_ERR_ARG, "z_magnet must lie before the first layer");
     if (!(p->magtol_max >= p->magtol_min)) return fail(c, LF_ERR_ARG, "magtol_max < magtol_min");
     if (g->kappa == 0.0f) return fail(c, LF_ERR_ARG, "kappa must be non-zero");
+    if (p->no_ut != 0 && p->no_ut != 1) return fail(c, LF_ERR_ARG, "no_ut must be 0 or 1");
+    if (p->no_ut) return fail(c, LF_ERR_ARG, "the no-UT variant is not built into the kernels yet");
+    if (p->no_ut) {
+        if (!(p->p_min > 0.0f) || !(p->pt_min > 0.0f) || !finite(p->p_min) || !finite(p->pt_min))
+            return fail(c, LF_ERR_ARG, "p_min and pt_min must be positive");
+        if (!(p->x_overlap >= 0.0f) || !finite(p->x_overlap)) return fail(c, LF_ERR_ARG, "x_overlap must be >= 0");
+        for (int i = 0; i < 8; ++i)
+            if (!finite(p->tol_c[i])) return fail(c, LF_ERR_ARG, "tol_c[%d] not finite", i);
+    }
     return LF_OK;
 }
 

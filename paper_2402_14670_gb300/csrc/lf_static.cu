@@ -68,6 +68,7 @@ bool params_ok(const lf_geometry* g, const lf_params* p) {
         if (!x && g->dxdy[l] == 0.0f) return false;
     }
     if (!(g->z_magnet < g->z[0]) || !(p->magtol_max >= p->magtol_min) || g->kappa == 0.0f) return false;
+    if (p->no_ut != 0) return false;  // the tile kernel follows VELO-UT input only
     return true;
 }
 

@@ -49,7 +49,8 @@ class lf_params(C.Structure):
                 ("magtol_min", C.c_float), ("magtol_max", C.c_float), ("magtol_c", C.c_float),
                 ("magtol_tx", C.c_float), ("T_triplet", C.c_float), ("T_x", C.c_float),
                 ("T_uv_scale", C.c_float), ("T_uv_min", C.c_float), ("T_ty", C.c_float), ("T_y", C.c_float),
-                ("T_Q", C.c_float), ("C_n", C.c_float * 4)]
+                ("T_Q", C.c_float), ("C_n", C.c_float * 4), ("no_ut", C.c_int32), ("p_min", C.c_float),
+                ("pt_min", C.c_float), ("x_overlap", C.c_float), ("tol_c", C.c_float * 8)]
 
 
 class lf_raw_hits(C.Structure):
@@ -149,7 +150,21 @@ def default_params(paper_K: bool = False) -> dict:
                 min_hits=9, K_first=1.00177513 if paper_K else 1.0, K_last=1.00142634 if paper_K else 1.0,
                 p_bend=5.0, magtol_min=8.0, magtol_max=40.0, magtol_c=96.0, magtol_tx=10.0, T_triplet=8.0,
                 T_x=2.0, T_uv_scale=50.0, T_uv_min=2.0, T_ty=0.02, T_y=800.0, T_Q=0.5,
-                C_n=[5.0, 1.0, 0.8, 0.5])
+                C_n=[5.0, 1.0, 0.8, 0.5], no_ut=0, p_min=5.0, pt_min=1.0, x_overlap=5.0,
+                tol_c=[4824.3, 426.3, 7071.1, 12080.4, 14077.8, 13909.3, 9315.3, 3209.5])
+
+
+def no_ut_params() -> dict:
+    """The no-UT variant (Sec. "No-UT tuning"): VELO tracks without a
+    momentum, windows from Eq. tol_noUT (Table poly_tol) at the tighter of
+    p = 5 GeV and pT = 1 GeV, two one-sided windows overlapping by 5 mm, u/v
+    tolerance 1200 mm, a fixed 10 mm magnet tolerance, and the "Forward
+    no-UT" column of Table tolerances (T_uv = max(T_x, 15 (|t_x| + |t_y|)))."""
+    p = default_params()
+    p.update(no_ut=1, uv_tol=1200.0, n_hits_window=64, n_triplets=20, magtol_min=10.0, magtol_max=10.0,
+             magtol_c=0.0, magtol_tx=0.0, T_triplet=2.0, T_x=0.5, T_uv_scale=15.0, T_uv_min=0.5, T_ty=0.003,
+             T_y=800.0, T_Q=0.5)
+    return p
 
 
 def _geometry(g: dict) -> lf_geometry:
@@ -165,8 +180,8 @@ def _geometry(g: dict) -> lf_geometry:
 def _params(p: dict) -> lf_params:
     s = lf_params()
     for name, _ in lf_params._fields_:
-        if name == "C_n":
-            s.C_n[:] = [float(v) for v in p["C_n"]]
+        if name in ("C_n", "tol_c"):
+            getattr(s, name)[:] = [float(v) for v in p[name]]
         else:
             setattr(s, name, p[name])
     return s

@@ -28,12 +28,24 @@ What pins what:
                   hits inside windows, true hits inside pre-cap windows
   binary32 fit    the binary32 fit agrees with the binary64 refit
   compact         exclusive scan of per-event counts
+  no-UT (Sec. No-UT tuning, Eq. tol_noUT, Eq. noUT_size_window, Table poly_tol):
+    window edges  hand-worked x_tol of the polynomial at the assumed momentum,
+                  the two one-sided windows with their 5 mm overlap and the
+                  1200 mm u/v tolerance (tests/golden/no_ut_window_examples.txt)
+    closed form   noise-free particles well above the assumed momentum are
+                  recovered with exactly their hits from the window side of
+                  their charge; q/p from the kick to 1e-5 in binary64
+    overlap       a straight track seeds identical triplets on both sides,
+                  ranked side 0 first
+    magnet tol    the fixed 10 mm doublet tolerance at the magnet
+    q/p unused    the input q/p does not change any result
 """
 from __future__ import annotations
 
 import os
 
 import numpy as np
+import torch
 
 import oracle
 from helpers import geo_dict, make_batch, raw_ids_in_windows, track_hits
@@ -448,7 +460,168 @@ def pin_compact(orc):
     assert np.array_equal(res["out_trk"], np.nonzero(found)[0])
 
 
+# ------------------------------------------------------------------- no-UT
+
+def _no_ut(**kw):
+    p = oracle.no_ut_params()
+    p.update(kw)
+    return p
+
+
+def _golden_no_ut_windows():
+    rows = []
+    with open(os.path.join(GOLDEN, "no_ut_window_examples.txt")) as f:
+        for ln in f:
+            ln = ln.strip()
+            if ln and not ln.startswith("#"):
+                rows.append(tuple(float(v) for v in ln.split()))
+    return rows
+
+
+def _side_ids(res, t, side):
+    """layer -> sorted raw ids inside window set `side` of track t."""
+    perm = res["packed"]["perm"]
+    out = {}
+    for l in range(12):
+        b = int(res["win_begin"][t, side * 12 + l])
+        c = int(res["win_count"][t, side * 12 + l])
+        out[l] = sorted(int(perm[i]) for i in range(b, b + c))
+    return out
+
+
+def pin_no_ut_window_edges(orc):
+    g = synth.Geometry()
+    xs, ys = 37.0, -21.0
+    for (tx, ty, _p, x_tol) in _golden_no_ut_windows():
+        zone = 1 if ty >= 0 else 0
+        hits, inside = [], {0: {}, 1: {}}
+        for l in range(12):
+            x_line = xs + tx * (g.z[l] - g.z_state)
+            if l % 4 in (0, 3):
+                c, tol = x_line, x_tol
+            else:
+                y = ys + ty * (g.z[l] - g.z_state)
+                c, tol = x_line - y * g.dxdy[l], 1200.0
+            lo0, hi0 = c - tol, c + 5.0      # side 0
+            lo1, hi1 = c - 5.0, c + tol      # side 1
+            e = 0.1  # far above the rounding of x_tol (ulp ~ 1e-4 mm), below each term checked
+            probes = [lo0 - e, lo0 + e, hi0 - e, hi0 + e, lo1 - e, lo1 + e, hi1 - e, hi1 + e]
+            inside[0][l], inside[1][l] = [], []
+            for xv in probes:
+                for sd, (lo, hi) in enumerate(((lo0, hi0), (lo1, hi1))):
+                    if lo <= xv <= hi:
+                        inside[sd][l].append(len(hits))
+                hits.append((l, zone, float(xv)))
+        # the input q/p is not used by the variant: give it a nonsense value
+        st = (xs, ys, tx, ty, 0.7)
+        b = make_batch([dict(hits=hits, states=[st])], g)
+        res = orc.run_batch(b, params=_no_ut())
+        for sd in (0, 1):
+            got = _side_ids(res, 0, sd)
+            for l in range(12):
+                assert got[l] == sorted(inside[sd][l]), ("no-UT window", tx, ty, sd, l, got[l], inside[sd][l])
+
+
+def pin_no_ut_closed_form(orc, polarity=1):
+    geo, b = closed_form_batch(polarity, seed=23)
+    res = orc.run_batch(b, geometry=geo_dict(geo), params=_no_ut(), use_x64=True)
+    perm = res["packed"]["perm"]
+    hit_mcp = b.hit_mcp.numpy()[perm]
+    layer = res["packed"]["layer"]
+    trk_mcp = b.trk_mcp.numpy()
+    mc = {k: v.numpy() for k, v in b.mcp.items()}
+    n_checked = 0
+    for t in range(b.n_tracks):
+        m = trk_mcp[t]
+        own = np.nonzero(hit_mcp == m)[0]
+        lay = set(layer[own].tolist())
+        reco = (len(own) >= 9 and all(any(l in lay for l in (4 * s + 1, 4 * s + 2)) for s in range(3))
+                and ({0, 4, 8} <= lay or {3, 7, 11} <= lay))
+        # the windows hold the particle when its momentum is well above the
+        # assumed one (the tighter of 5 GeV and pT = 1 GeV at its polar angle)
+        tx, ty = mc["tx"][m], mc["ty"][m]
+        sin_t = np.sqrt(tx * tx + ty * ty) / np.sqrt(1.0 + tx * tx + ty * ty)
+        if not reco or abs(1.0 / mc["qop"][m]) < 1.25 * max(5.0, 1.0 / sin_t):
+            continue
+        n_checked += 1
+        assert res["found"][t], "no-UT: reconstructible track %d not found" % t
+        got = res["hit_idx"][t]
+        assert np.array_equal(np.sort(got[got >= 0]), np.sort(own)), "no-UT hit set %d" % t
+        # the winning candidate was seeded on the side its charge bends to
+        acc = [r for r in range(res["n_trip"][t]) if res["cand_status"][t, r] == 0]
+        best = min(acc, key=lambda r: (res["cand_q"][t, r], r))
+        side = int(res["trip"][t, best, 0]) // 2
+        assert side == (1 if polarity * mc["qop"][m] > 0 else 0), ("no-UT side", t, side)
+        truth = synth.truth_params(mc["tx"][m], mc["ty"][m], mc["qop"][m], geo)
+        assert _rel_close(res["state64"][t][5], truth[5], 1e-5, 1e-9), ("no-UT q/p", t)
+        assert _rel_close(res["state"][t][5], truth[5], 1e-5, 1e-6), ("no-UT q/p f32", t)
+    assert n_checked >= 15, n_checked
+
+
+def pin_no_ut_closed_form_md(orc):
+    pin_no_ut_closed_form(orc, polarity=-1)
+
+
+def pin_no_ut_overlap(orc):
+    """Hits inside the 5 mm overlap serve both charge assumptions.  A track
+    with x = 100 mm in every x layer and a straight input line through it
+    gives chi2 = 0 exactly in both configurations and on both sides, so the
+    ranking (chi2, side, configuration) alone orders the four triplets.  A
+    p = 5 TeV particle (bend under a millimetre) is found."""
+    hits = [(l, 1, 100.0) for l in (0, 3, 4, 7, 8, 11)]
+    st = (100.0, 270.0, 0.0, 0.07, 0.0)
+    res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]), params=_no_ut())
+    n = res["n_trip"][0]
+    assert n == 4, n
+    assert list(res["trip"][0, :n, 0]) == [0, 1, 2, 3], res["trip"][0, :n, 0]   # cfg + 2*side
+    assert np.all(res["trip_chi2"][0, :n] == 0.0)
+    assert np.array_equal(res["trip"][0, 0, 1:], res["trip"][0, 2, 1:])
+    r1 = orc.run_batch(make_batch([dict(hits=hits, states=[st])]), params=_no_ut(n_triplets=1))
+    assert r1["n_trip"][0] == 1 and r1["trip"][0, 0, 0] == 0
+    tx, ty, qop = 0.04, 0.07, 1.0 / 5000.0
+    b = make_batch([dict(hits=track_hits(tx, ty, qop), states=[synth.state_of(tx, ty, qop)])])
+    res = orc.run_batch(b, params=_no_ut())
+    assert res["found"][0] and res["nhits"][0] == 12
+    assert set((res["trip"][0, :res["n_trip"][0], 0] // 2).tolist()) == {0, 1}
+
+
+def pin_no_ut_magnet_tolerance(orc):
+    # straight input line with x = 100 mm at the magnet centre, T-station slope
+    # 0.1 (a 200 mm bend at T3, inside the side-1 windows)
+    T0 = 0.1
+    g = synth.Geometry()
+    txs = 0.05
+    st = (100.0 + txs * (g.z_state - g.z_magnet), 270.0, txs, 0.1, 0.0)
+    line = lambda z: 100.0 + T0 * (z - g.z_magnet)
+    dz = g.z[8] - g.z[0]
+    r = (g.z[0] - g.z_magnet) / dz          # x offset at the magnet per unit x2 offset
+    s_star = 10.0 / r                       # a fixed 10 mm, whatever p and slope
+    for s, inside in ((s_star - 0.05, True), (s_star + 0.05, False)):
+        x1 = line(g.z[4]) + s * (g.z[4] - g.z[0]) / dz
+        hits = [(0, 1, line(g.z[0])), (8, 1, line(g.z[8])), (4, 1, line(g.z[4])),
+                (8, 1, line(g.z[8]) + s), (4, 1, x1)]
+        res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]), params=_no_ut())
+        perm = res["packed"]["perm"]
+        h2s = {int(perm[res["trip"][0, k, 3]]) for k in range(res["n_trip"][0])}
+        assert 1 in h2s, "no-UT: true doublet lost"
+        assert (3 in h2s) == inside, ("no-UT magnet tolerance", s, h2s)
+
+
+def pin_no_ut_qop_unused(orc):
+    b = synth.generate(1, n_events=3)
+    r0 = orc.run_batch(b, params=_no_ut())
+    gen = np.random.default_rng(5)
+    b.sqop = b.sqop.clone()
+    b.sqop[:] = torch.as_tensor(gen.uniform(-1.0, 1.0, b.n_tracks).astype(np.float32))
+    r1 = orc.run_batch(b, params=_no_ut())
+    for k in ("found", "hit_idx", "state", "quality", "win_begin", "win_count", "n_trip", "trip"):
+        assert np.array_equal(r0[k], r1[k]), k
+    assert r0["found"].sum() > 10
+
+
 ALL_PINS = [pin_pack_lexsort, pin_closed_form, pin_closed_form_md, pin_window_edges, pin_window_cap,
             pin_closest_tie, pin_triplet_chi2_K, pin_top_n, pin_bending_filter,
             pin_magnet_tolerance, pin_known_residual_Q, pin_T_Q, pin_ty_cut, pin_invariants,
-            pin_true_hits_in_window, pin_fit32_vs_fit64, pin_compact]
+            pin_true_hits_in_window, pin_fit32_vs_fit64, pin_compact,
+            pin_no_ut_window_edges, pin_no_ut_closed_form, pin_no_ut_closed_form_md, pin_no_ut_overlap,
+            pin_no_ut_magnet_tolerance, pin_no_ut_qop_unused]

@@ -68,6 +68,33 @@ MUTANTS = [
      "for (int32_t t = trk_offsets[e]; t < trk_offsets[e + 1]; ++t)\n            if (found[t])",
      "for (int32_t t = trk_offsets[e]; t + 1 < trk_offsets[e + 1]; ++t)\n            if (found[t])",
      ["pin_compact"]),
+    # no-UT variant
+    ("no-UT windows swap sides", "float xmin = side ? centre - p->x_overlap : centre - tol;",
+     "float xmin = side ? centre - tol : centre - p->x_overlap;", ["pin_no_ut_window_edges"]),
+    ("no-UT overlap on the wrong side of the line", "float xmax = side ? centre + tol : centre + p->x_overlap;",
+     "float xmax = side ? centre + tol : centre - p->x_overlap;", ["pin_no_ut_window_edges"]),
+    ("no-UT assumed momentum the looser threshold", "return fminf(ip_p, ip_pt);", "return fmaxf(ip_p, ip_pt);",
+     ["pin_no_ut_window_edges"]),
+    ("no-UT pT threshold with tan(theta)", "float sin_theta = sqrtf(t2) / sqrtf(1.0f + t2);",
+     "float sin_theta = sqrtf(t2);", ["pin_no_ut_window_edges"]),
+    ("no-UT c3 term linear in ty", "float b = (ty * ty) * (c[3] + tx * (c[4] + c[5] * tx));",
+     "float b = ty * (c[3] + tx * (c[4] + c[5] * tx));", ["pin_no_ut_window_edges"]),
+    ("no-UT c4 and c5 swapped", "(c[3] + tx * (c[4] + c[5] * tx))", "(c[3] + tx * (c[5] + c[4] * tx))",
+     ["pin_no_ut_window_edges"]),
+    ("no-UT c6 term without t_x", "float d = ip * (c[6] * tx + c[7] * ip);",
+     "float d = ip * (c[6] + c[7] * ip);", ["pin_no_ut_window_edges"]),
+    ("no-UT u/v windows with the x tolerance", "            tol = p->uv_tol;\n", "            tol = x_tol;\n",
+     ["pin_no_ut_window_edges"]),
+    ("no-UT extrapolation with the kick", "centre = s->xs + s->txs * (g->z[l] - g->z_state);",
+     "centre = x_extrap(g, s, l);", ["pin_no_ut_window_edges"]),
+    ("no-UT extension in the other side's windows", "&Ws[trips[r].side]", "&Ws[1 - trips[r].side]",
+     ["pin_no_ut_closed_form", "pin_no_ut_closed_form_md"]),
+    ("no-UT side ranked after the configuration",
+     "if (p->side != q->side) return p->side < q->side ? -1 : 1;\n    if (p->cfg != q->cfg) return p->cfg < q->cfg ? -1 : 1;",
+     "if (p->cfg != q->cfg) return p->cfg < q->cfg ? -1 : 1;\n    if (p->side != q->side) return p->side < q->side ? -1 : 1;",
+     ["pin_no_ut_overlap"]),
+    ("no-UT only one side seeded", "for (int side = 0; side < n_sides; ++side) {",
+     "for (int side = n_sides - 1; side < n_sides; ++side) {", ["pin_no_ut_closed_form", "pin_no_ut_overlap"]),
 ]
 
 

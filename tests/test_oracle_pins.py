@@ -32,3 +32,20 @@ def test_defaults_are_the_papers_constants():
     pk = oracle.default_params(paper_K=True)
     assert pk["K_first"] == gold["K_x1"]["K_first"] and pk["K_last"] == gold["K_x1"]["K_last"]
     assert oracle.default_geometry()["z_ref"] == gold["z_ref_mm"]["value"]
+
+
+def test_no_ut_defaults_are_the_papers_constants():
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as f:
+        gold = json.load(f)
+    p = oracle.no_ut_params()
+    assert p["no_ut"] == 1
+    for k, v in gold["forward_no_ut_tolerances"].items():
+        if not k.startswith("_"):
+            assert p[k] == v, k
+    assert p["tol_c"] == gold["no_ut_poly_tol"]["c"]
+    w = gold["no_ut_window"]
+    for k in ("p_min", "pt_min", "x_overlap", "uv_tol"):
+        assert p[k] == w[k], k
+    assert p["magtol_min"] == p["magtol_max"] == w["magtol"]
+    # T_uv = max(T_x, 15 (|t_x| + |t_y|)): the floor is the no-UT T_x
+    assert p["T_uv_min"] == p["T_x"]
