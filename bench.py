@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-no-ut", action="store_true", help="skip the no-UT variant measurement")
     ap.add_argument("--cpu-events", type=int, default=3000, help="oracle sample size (events)")
     ap.add_argument("--tuning", type=str, default=None, help="json of warps_per_block/blocks_per_sm/grain")
     return ap.parse_args()
@@ -406,6 +407,36 @@ def main():
         tr.find(packed, batch, n_ev, "batched", tuning, out=out)
         torch.cuda.synchronize()
 
+    # ---------------- the no-UT variant (Sec. "No-UT tuning") on the same events:
+    # pack + persistent find with two window sets per track, q/p unused
+    no_ut = None
+    if not args.no_no_ut:
+        tr_nu = lf.Tracker(None, lf.no_ut_params())
+        out_nu = tr_nu.find(packed, batch, n_ev, "batched")
+        torch.cuda.synchronize()
+        assert tr_nu.status() == 0
+        ev_nu = []
+        for i in range(args.warmup + args.steps):
+            e3 = mk()
+            e3[0].record(stream)
+            tr_nu.pack(batch, out=packed)
+            e3[1].record(stream)
+            tr_nu.find(packed, batch, n_ev, "batched", out=out_nu)
+            e3[2].record(stream)
+            if i >= args.warmup:
+                ev_nu.append(e3)
+        torch.cuda.synchronize()
+        nu_step = max_over_ranks(ws, statistics.mean(e[0].elapsed_time(e[2]) for e in ev_nu))
+        nu_find = statistics.mean(e[1].elapsed_time(e[2]) for e in ev_nu)
+        nu_found = int(out_nu["found"].sum())
+        nu_algo = algorithmic_bytes(n_ev, batch.n_hits, batch.n_tracks, nu_found)
+        no_ut = {"value": ws * n_ev / (nu_step / 1e3), "unit": UNIT, "ms_per_step": nu_step, "find_ms": nu_find,
+                 "found_tracks": nu_found, "find_hbm_frac": nu_algo / (nu_find / 1e3) / 1e9 / peaks()[0],
+                 "form": "no-UT parameters (two one-sided window sets per track, 64-hit cap, 20 triplets), "
+                         "batched persistent stage pipeline"}
+        tr_nu.close()
+        del out_nu
+
     # ---------------- end to end through lf_process_host on pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -488,9 +519,10 @@ def main():
         except Exception as e:  # the oracle is test infrastructure; report why it did not run
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "error": str(e)}
 
-    # pack: bucket + sort; find (default queue mode): track->event map, four
-    # persistent stage kernels, three compaction kernels
-    launches_per_step = 2 + 1 + 4 + 3
+    # pack: bucket, gather, small-bucket sort, large-bucket sort; find (default
+    # queue mode): track->event map, three persistent stage kernels (windows,
+    # triplets, extension with the selection), three compaction kernels
+    launches_per_step = 4 + (1 + 3) + 3
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -503,7 +535,8 @@ def main():
                        "tuning": tuning or "defaults",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "single"},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-            "roofline": roof, "roofline_pack": roof_pack, "plain": plain, "served": served, "cpu_baseline": cpu,
+            "roofline": roof, "roofline_pack": roof_pack, "plain": plain, "served": served, "no_ut": no_ut,
+            "cpu_baseline": cpu,
             "stage_ms": {"pack": pack_avg, "find": find_avg}, "found_tracks": n_found,
         }
         print(json.dumps(line), flush=True)

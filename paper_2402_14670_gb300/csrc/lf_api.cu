@@ -112,7 +112,6 @@ lf_status check_params(lf_ctx* c, const lf_geometry* g, const lf_params* p) {
     if (!(p->magtol_max >= p->magtol_min)) return fail(c, LF_ERR_ARG, "magtol_max < magtol_min");
     if (g->kappa == 0.0f) return fail(c, LF_ERR_ARG, "kappa must be non-zero");
     if (p->no_ut != 0 && p->no_ut != 1) return fail(c, LF_ERR_ARG, "no_ut must be 0 or 1");
-    if (p->no_ut) return fail(c, LF_ERR_ARG, "the no-UT variant is not built into the kernels yet");
     if (p->no_ut) {
         if (!(p->p_min > 0.0f) || !(p->pt_min > 0.0f) || !finite(p->p_min) || !finite(p->pt_min))
             return fail(c, LF_ERR_ARG, "p_min and pt_min must be positive");
@@ -159,6 +158,11 @@ KParams make_kparams(const lf_geometry* g, const lf_params* p) {
     k.T_y = p->T_y;
     k.T_Q = p->T_Q;
     for (int i = 0; i < 4; ++i) k.C_n[i] = p->C_n[i];
+    k.no_ut = p->no_ut;
+    k.p_min = p->p_min;
+    k.pt_min = p->pt_min;
+    k.x_overlap = p->x_overlap;
+    for (int i = 0; i < 8; ++i) k.tol_c[i] = p->tol_c[i];
     volatile float pol = (float)g->polarity;  // binary32 products, as the method forms them
     k.pol_f = pol;
     k.pk = pol * g->kappa;
@@ -217,9 +221,10 @@ KOut to_kout(const lf_output* o) {
 lf_status plain_stages(lf_ctx* c, const lf_batch* b, cudaStream_t s) {
     const size_t nt = (size_t)b->n_tracks, NT = (size_t)(c->p.n_triplets > 0 ? c->p.n_triplets : 1);
     lf_status st;
+    const size_t ns = c->p.no_ut ? 2 : 1;  // window sets per track
     if ((st = ensure(c, c->trk_event, nt * 4)) != LF_OK) return st;
-    if ((st = ensure(c, c->wbeg, nt * NL * 4)) != LF_OK) return st;
-    if ((st = ensure(c, c->wcnt, nt * NL)) != LF_OK) return st;
+    if ((st = ensure(c, c->wbeg, nt * ns * NL * 4)) != LF_OK) return st;
+    if ((st = ensure(c, c->wcnt, nt * ns * NL)) != LF_OK) return st;
     if ((st = ensure(c, c->keys, nt * NT * 8)) != LF_OK) return st;
     if ((st = ensure(c, c->ntrip, nt)) != LF_OK) return st;
     KBatch kb = to_kbatch(b);
@@ -343,6 +348,8 @@ lf_status resolve_shape(lf_ctx* c, const lf_tuning* tuning, Shape& sh) {
     sh.wpb = tuning && tuning->warps_per_block > 0 ? tuning->warps_per_block : 8;
     sh.grain = (tuning && tuning->grain > 0 ? (tuning->grain & 15) : 0) + (sh.queue == 1 ? 16 : 0);
     if (sh.wpb > 16) return fail(c, LF_ERR_ARG, "warps_per_block %d above 16", sh.wpb);
+    if (c->p.no_ut && sh.queue != 0)
+        return fail(c, LF_ERR_ARG, "the no-UT variant runs on the staged pipeline (queue 0) only");
     if (sh.queue == 0) {
         if (!c->stage_bps[0]) LF_CUDA(c, stage_blocks_per_sm(c->kp, c->stage_bps));
         sh.bps = tuning && tuning->blocks_per_sm > 0 ? tuning->blocks_per_sm : 0;
@@ -362,9 +369,10 @@ lf_status prepare_batched(lf_ctx* c, const lf_batch* b, const Shape& sh) {
     if ((st = ensure(c, c->ev_count, (size_t)b->n_events * 4)) != LF_OK) return st;
     if (sh.queue == 0) {
         const size_t nt = (size_t)b->n_tracks, NT = (size_t)(c->p.n_triplets > 0 ? c->p.n_triplets : 1);
+        const size_t ns = c->p.no_ut ? 2 : 1;
         if ((st = ensure(c, c->trk_event, nt * 4)) != LF_OK) return st;
-        if ((st = ensure(c, c->wbeg, nt * NL * 4)) != LF_OK) return st;
-        if ((st = ensure(c, c->wcnt, nt * NL)) != LF_OK) return st;
+        if ((st = ensure(c, c->wbeg, nt * ns * NL * 4)) != LF_OK) return st;
+        if ((st = ensure(c, c->wcnt, nt * ns * NL)) != LF_OK) return st;
         if ((st = ensure(c, c->keys, nt * NT * 8)) != LF_OK) return st;
         if ((st = ensure(c, c->ntrip, nt)) != LF_OK) return st;
     }
@@ -468,7 +476,8 @@ lf_status lf_debug_stages(lf_ctx* c, const lf_batch* b, int32_t* win_begin, int3
     if ((st = plain_stages(c, b, s)) != LF_OK) return st;
     const size_t nt = (size_t)b->n_tracks;
     if (nt == 0) return LF_OK;
-    LF_CUDA(c, cudaMemcpyAsync(win_begin, c->wbeg.p, nt * NL * 4, cudaMemcpyDeviceToDevice, s));
+    const size_t ns = c->p.no_ut ? 2 : 1;
+    LF_CUDA(c, cudaMemcpyAsync(win_begin, c->wbeg.p, nt * ns * NL * 4, cudaMemcpyDeviceToDevice, s));
     LF_CUDA(c, launch_debug_triplets(c->kp, to_kbatch(b), (int*)c->wbeg.p, (uint8_t*)c->wcnt.p,
                                      (uint64_t*)c->keys.p, (uint8_t*)c->ntrip.p, win_count, n_trip, trip, trip_chi2,
                                      s));

@@ -26,6 +26,9 @@ struct KParams {
     float K_first, K_last, p_bend, magtol_min, magtol_max, magtol_c, magtol_tx;
     float T_triplet, T_x, T_uv_scale, T_uv_min, T_ty, T_y, T_Q;
     float C_n[4];
+    int no_ut;    // Sec. "No-UT tuning": two window sets per track, q/p unused
+    float p_min, pt_min, x_overlap;
+    float tol_c[8];
     float pol_f;  // (float)polarity
     float pk;     // pol_f * kappa
     float pg;     // pol_f * gamma
@@ -54,7 +57,8 @@ struct CandRec {
     int8_t status;   // 0 accepted
     int8_t n;
     int8_t hl[NL];   // window-local hit index per layer, -1 none
-    int8_t pad[6];
+    int8_t side;     // window set of the triplet (no-UT variant; 0 otherwise)
+    int8_t pad[5];
     float st[6];
 };
 static_assert(sizeof(CandRec) == 48, "CandRec layout");

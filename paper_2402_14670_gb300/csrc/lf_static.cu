@@ -87,6 +87,7 @@ lfk::KParams kparams(const lf_geometry* g, const lf_params* p) {
     k.T_triplet = p->T_triplet; k.T_x = p->T_x; k.T_uv_scale = p->T_uv_scale; k.T_uv_min = p->T_uv_min;
     k.T_ty = p->T_ty; k.T_y = p->T_y; k.T_Q = p->T_Q;
     for (int i = 0; i < 4; ++i) k.C_n[i] = p->C_n[i];
+    k.no_ut = 0;
     volatile float pol = (float)g->polarity;
     k.pol_f = pol;
     k.pk = pol * g->kappa;

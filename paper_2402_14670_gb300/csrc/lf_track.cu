@@ -28,6 +28,13 @@
 //   selection  lowest Q among accepted candidates by a warp-wide minimum of
 //              (Q bits, rank); the winner's hits and state go out coalesced.
 //
+// No-UT variant (Sec. "No-UT tuning", NOUT = true): an input track has two
+// window sets, one per charge assumption, built around its straight-line
+// extrapolation with the Eq. tol_noUT tolerance; the triplet stage stages and
+// scans the two sets in turn into one kept-triplet list (the side is a key
+// bit), and the extension stages each set in turn for the triplets seeded in
+// it.
+//
 // Arithmetic: binary32, no contraction (built with -fmad=false), IEEE
 // division; every expression is written in the evaluation order of the
 // method's definition so that results do not depend on the launch shape.
@@ -144,9 +151,46 @@ __device__ __forceinline__ float x_extrap(const KParams& k, const TState& s, int
     return (x_mag + t1) + t2 * t3;
 }
 
-// Limits and centre of the window of layer l.
-__device__ __forceinline__ void window_limits(const KParams& k, const TState& s, int l, float& xmin, float& xmax,
-                                              float& centre) {
+// Assumed inverse momentum of a track without a momentum estimate: the
+// tighter of p_min and pt_min / sin(theta) (Sec. "No-UT tuning").
+__device__ __forceinline__ float no_ut_inv_p(const KParams& k, const TState& s) {
+    float t2 = s.txs * s.txs + s.tys * s.tys;
+    float sin_theta = sqrtf(t2) / sqrtf(1.0f + t2);
+    float ip_pt = sin_theta / k.pt_min;
+    float ip_p = 1.0f / k.p_min;
+    return fminf(ip_p, ip_pt);
+}
+
+// Eq. tol_noUT (coefficients of Table poly_tol), ip = 1/p
+__device__ __forceinline__ float no_ut_xtol(const KParams& k, float ip, float tx, float ty) {
+    float a = k.tol_c[0] + tx * (k.tol_c[1] + k.tol_c[2] * tx);
+    float b = (ty * ty) * (k.tol_c[3] + tx * (k.tol_c[4] + k.tol_c[5] * tx));
+    float d = ip * (k.tol_c[6] * tx + k.tol_c[7] * ip);
+    return ip * ((a + b) + d);
+}
+
+// Limits and centre of the window of layer l.  NOUT: window set `side` of
+// Eq. noUT_size_window (side 0 reaches x_tol below the straight line and
+// x_overlap above it, side 1 the mirror image; u/v layers alike with uv_tol).
+template <bool NOUT>
+__device__ __forceinline__ void window_limits(const KParams& k, const TState& s, int l, int side, float& xmin,
+                                              float& xmax, float& centre) {
+    if (NOUT) {
+        float tol;
+        if (is_x(l)) {
+            centre = s.xs + s.txs * (k.z[l] - k.z_state);
+            tol = no_ut_xtol(k, no_ut_inv_p(k, s), s.txs, s.tys);
+        } else {
+            int n = neighbour_x(l);
+            float xn = s.xs + s.txs * (k.z[n] - k.z_state);
+            float yl = s.ys + s.tys * (k.z[l] - k.z_state);
+            centre = (xn + s.txs * (k.z[l] - k.z[n])) - yl * k.dxdy[l];
+            tol = k.uv_tol;
+        }
+        xmin = side ? centre - k.x_overlap : centre - tol;
+        xmax = side ? centre + tol : centre + k.x_overlap;
+        return;
+    }
     const float pmom = 1.0f / fabsf(s.qop);
     if (is_x(l)) {
         float x_tol = k.xtol_c + k.xtol_p / pmom;
@@ -171,12 +215,13 @@ __device__ __forceinline__ void window_limits(const KParams& k, const TState& s,
 // Windows of all twelve layers, [begin, begin+count) in packed hit indices,
 // returned on lanes 0..11: lanes 0..11 search the lower bounds and lanes
 // 12..23 the upper bounds in parallel, then lanes 0..11 apply the cap.
+template <bool NOUT>
 __device__ __forceinline__ void warp_windows(const KParams& k, const KBatch& b, const TState& s, int e, int lane,
-                                             int& begin, int& count) {
+                                             int side, int& begin, int& count) {
     const int zone = (s.tys >= 0.0f) ? 1 : 0;
     const int l = lane < NL ? lane : (lane < 2 * NL ? lane - NL : 0);
     float xmin, xmax, centre;
-    window_limits(k, s, l, xmin, xmax, centre);
+    window_limits<NOUT>(k, s, l, side, xmin, xmax, centre);
     const int* off = b.hit_offsets + (size_t)e * NB + zone * NL + l;
     const int bb = __ldg(off), be = __ldg(off + 1);
     int v = 0;
@@ -336,20 +381,24 @@ __device__ __forceinline__ int select_buffer(const Scratch& sc, int nb, int NT, 
 
 // ---------------------------------------------------------- stage: triplets
 
-// Returns this lane's entry of the sorted list of kept triplet keys
-// (lane r holds rank r; NOKEY past the end) and the list length.
-// key = chi2 bits << 32 | cfg << 18 | j0 << 12 | j2 << 6 | j1 (window-local
-// indices), which orders by (chi2, cfg, h0, h2).
-template <int NIT>
-__device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState& s, const Slot& m, const Scratch& sc,
-                                                 int lane, int& n_trip) {
+// One window set's triplets, merged into the warp's key buffer (nb keys,
+// threshold thr, this lane's kept key `mine`; see select_buffer).
+// key = chi2 bits << 32 | side << 19 | cfg << 18 | j0 << 12 | j2 << 6 | j1
+// (window-local indices), which orders by (chi2, side, cfg, h0, h2).
+template <int NIT, bool NOUT>
+__device__ __forceinline__ void triplet_pass(const KParams& k, const TState& s, const Slot& m, const Scratch& sc,
+                                             int lane, int side, int& nb, uint64_t& thr, uint64_t& mine) {
     const int cap = k.cap;
     const int NT = k.n_trip;
-    n_trip = 0;
-    if (NT <= 0) return NOKEY;
-    const float pmom = 1.0f / fabsf(s.qop);
+    float pmom, bend;  // momentum, and the sign of the expected slope change
+    if (NOUT) {
+        pmom = 1.0f / no_ut_inv_p(k, s);
+        bend = side ? 1.0f : -1.0f;  // side 1 holds the tracks bending to larger x
+    } else {
+        pmom = 1.0f / fabsf(s.qop);
+        bend = (s.qop > 0.0f) ? k.pol_f : -k.pol_f;
+    }
     const float x_mag_in = s.xs + s.txs * (k.z_magnet - k.z_state);
-    const float bend = (s.qop > 0.0f) ? k.pol_f : -k.pol_f;
     const float tol_base = k.magtol_min + k.magtol_c / pmom;
     const bool f1 = pmom < k.p_bend;
     const int c0 = m.h->wcnt[0], c1 = m.h->wcnt[3];
@@ -410,9 +459,6 @@ __device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState&
         P += __shfl_sync(FULL, inc, 31);
     }
 
-    int nb = 0;            // keys in the buffer
-    uint64_t thr = NOKEY;  // keys at or above thr cannot be kept
-    uint64_t mine = NOKEY;
 #pragma unroll 1
     for (int seg = 0; seg < P; seg += PAIR_CAP) {
         // materialise the pairs of this segment
@@ -455,8 +501,9 @@ __device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState&
                         float dx = m.wx[L1 * cap + j1] - x1_exp;
                         float chi2 = dx * dx;
                         if (chi2 < k.T_triplet) {
-                            key = ((uint64_t)__float_as_uint(chi2) << 32) | ((uint64_t)cfg << 18) |
-                                  ((uint64_t)j0 << 12) | ((uint64_t)j2 << 6) | (uint64_t)j1;
+                            key = ((uint64_t)__float_as_uint(chi2) << 32) | ((uint64_t)side << 19) |
+                                  ((uint64_t)cfg << 18) | ((uint64_t)j0 << 12) | ((uint64_t)j2 << 6) |
+                                  (uint64_t)j1;
                             valid = key < thr;
                         }
                     }
@@ -476,7 +523,21 @@ __device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState&
         }
         __syncwarp();
     }
-    nb = select_buffer(sc, nb, NT, thr, lane, mine);
+}
+
+// Triplet stage of one window set: returns this lane's entry of the sorted
+// list of kept triplet keys (lane r holds rank r; NOKEY past the end) and
+// the list length.
+template <int NIT>
+__device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState& s, const Slot& m, const Scratch& sc,
+                                                 int lane, int& n_trip) {
+    n_trip = 0;
+    if (k.n_trip <= 0) return NOKEY;
+    int nb = 0;            // keys in the buffer
+    uint64_t thr = NOKEY;  // keys at or above thr cannot be kept
+    uint64_t mine = NOKEY;
+    triplet_pass<NIT, false>(k, s, m, sc, lane, 0, nb, thr, mine);
+    nb = select_buffer(sc, nb, k.n_trip, thr, lane, mine);
     n_trip = nb;
     return mine;
 }
@@ -743,60 +804,83 @@ __device__ __forceinline__ int queue_take(int* cursor, int n, int lane) {
     return __shfl_sync(FULL, v, 0);
 }
 
+// Window sets in scratch: set ws = t (VELO-UT) or 2t + side (no-UT), its
+// twelve windows at [ws * 12, ws * 12 + 12).
+template <bool NOUT>
 __device__ __forceinline__ void windows_track(const KParams& k, const KBatch& b, const int* __restrict__ trk_event,
                                               int* wbeg, uint8_t* wcnt, int t, int lane) {
     TState s = load_state(b, t);
-    int beg, cnt;
-    warp_windows(k, b, s, __ldg(trk_event + t), lane, beg, cnt);
-    if (lane < NL) {
-        wbeg[(size_t)t * NL + lane] = beg;
-        wcnt[(size_t)t * NL + lane] = (uint8_t)cnt;
+    const int e = __ldg(trk_event + t);
+    constexpr int NS = NOUT ? 2 : 1;
+#pragma unroll
+    for (int side = 0; side < NS; ++side) {
+        int beg, cnt;
+        warp_windows<NOUT>(k, b, s, e, lane, side, beg, cnt);
+        if (lane < NL) {
+            wbeg[((size_t)t * NS + side) * NL + lane] = beg;
+            wcnt[((size_t)t * NS + side) * NL + lane] = (uint8_t)cnt;
+        }
     }
 }
 
 // stage 1: windows (warp per track)
-template <bool P>
+template <bool P, bool NOUT>
 __global__ void k_windows(KParams k, KBatch b, const int* __restrict__ trk_event, int* wbeg, uint8_t* wcnt,
                           int* cursor) {
     const int lane = threadIdx.x & 31;
     if (!P) {
         const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        if (t < b.n_tracks) windows_track(k, b, trk_event, wbeg, wcnt, t, lane);
+        if (t < b.n_tracks) windows_track<NOUT>(k, b, trk_event, wbeg, wcnt, t, lane);
         return;
     }
     for (;;) {
         const int t = queue_take(cursor, 1, lane);
         if (t >= b.n_tracks) break;
-        windows_track(k, b, trk_event, wbeg, wcnt, t, lane);
+        windows_track<NOUT>(k, b, trk_event, wbeg, wcnt, t, lane);
     }
 }
 
-__device__ __forceinline__ void load_windows(const int* wbeg, const uint8_t* wcnt, int t, const Slot& m, int lane) {
+// window set ws into the slot's descriptors
+__device__ __forceinline__ void load_windows(const int* wbeg, const uint8_t* wcnt, int ws, const Slot& m, int lane) {
     if (lane < NL) {
-        m.h->wbeg[lane] = wbeg[(size_t)t * NL + lane];
-        m.h->wcnt[lane] = wcnt[(size_t)t * NL + lane];
+        m.h->wbeg[lane] = wbeg[(size_t)ws * NL + lane];
+        m.h->wcnt[lane] = wcnt[(size_t)ws * NL + lane];
     }
     __syncwarp();
 }
 
 constexpr int PLAIN_WARPS = 8;
 
-template <int NIT>
+template <int NIT, bool NOUT>
 __device__ __forceinline__ void triplets_track(const KParams& k, const KBatch& b, const int* __restrict__ wbeg,
                                                const uint8_t* __restrict__ wcnt, uint64_t* keys, uint8_t* ntrip,
                                                const Slot& m, const Scratch& sc, int t, int lane) {
-    load_windows(wbeg, wcnt, t, m, lane);
-    stage_windows<true>(k, b, m, lane);
     TState s = load_state(b, t);
-    int nt;
-    uint64_t top = triplet_scan<NIT>(k, s, m, sc, lane, nt);
+    int nt = 0;
+    uint64_t top = NOKEY;
+    if (!NOUT) {
+        load_windows(wbeg, wcnt, t, m, lane);
+        stage_windows<true>(k, b, m, lane);
+        top = triplet_scan<NIT>(k, s, m, sc, lane, nt);
+    } else if (k.n_trip > 0) {
+        // both charge assumptions into one list: stage and scan each set
+        int nb = 0;
+        uint64_t thr = NOKEY;
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+            load_windows(wbeg, wcnt, 2 * t + side, m, lane);
+            stage_windows<true>(k, b, m, lane);
+            triplet_pass<NIT, true>(k, s, m, sc, lane, side, nb, thr, top);
+        }
+        nt = select_buffer(sc, nb, k.n_trip, thr, lane, top);
+    }
     if (lane < nt) keys[(size_t)t * k.n_trip + lane] = top;
     if (lane == 0) ntrip[t] = (uint8_t)nt;
     __syncwarp();
 }
 
 // stage 2: triplet seeding (warp per track)
-template <int NIT, bool P>
+template <int NIT, bool P, bool NOUT>
 __global__ void k_triplets(KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ wcnt,
                            uint64_t* keys, uint8_t* ntrip, int* cursor) {
     extern __shared__ __align__(16) char smem[];
@@ -805,14 +889,77 @@ __global__ void k_triplets(KParams k, KBatch b, const int* __restrict__ wbeg, co
     const Scratch sc = scratch_at(smem + PLAIN_WARPS * slot_bytes(k.cap), warp);
     if (!P) {
         const int t = blockIdx.x * PLAIN_WARPS + warp;
-        if (t < b.n_tracks) triplets_track<NIT>(k, b, wbeg, wcnt, keys, ntrip, m, sc, t, lane);
+        if (t < b.n_tracks) triplets_track<NIT, NOUT>(k, b, wbeg, wcnt, keys, ntrip, m, sc, t, lane);
         return;
     }
     for (;;) {
         const int t = queue_take(cursor, 1, lane);
         if (t >= b.n_tracks) break;
-        triplets_track<NIT>(k, b, wbeg, wcnt, keys, ntrip, m, sc, t, lane);
+        triplets_track<NIT, NOUT>(k, b, wbeg, wcnt, keys, ntrip, m, sc, t, lane);
     }
+}
+
+__device__ __forceinline__ void write_cand(CandRec* cands, const KParams& k, int t, int r, const Cand& cd, int side) {
+    CandRec rec;
+    rec.Q = cd.Q;
+    rec.status = (int8_t)cd.status;
+    rec.n = (int8_t)cd.n;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) rec.hl[l] = (int8_t)(cd.status == 0 ? cd.hl[l] : -1);
+    rec.side = (int8_t)side;
+#pragma unroll
+    for (int p = 0; p < 5; ++p) rec.pad[p] = 0;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) rec.st[p] = cd.status == 0 ? cd.st[p] : 0.0f;
+    cands[(size_t)t * k.n_trip + r] = rec;
+}
+
+__device__ __forceinline__ void clear_cand(Cand& cd) {
+    cd.status = 9;
+    cd.Q = 0.0f;
+    cd.n = 0;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) cd.st[p] = 0.0f;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) cd.hl[l] = -1;
+}
+
+// No-UT extension of track t (one track per warp, lane r extends triplet
+// r): each window set is staged in turn and extends the triplets seeded in
+// it.
+template <bool SEL>
+__device__ __forceinline__ void extend_track_no_ut(const KParams& k, const KBatch& b, const int* __restrict__ wbeg,
+                                                   const uint8_t* __restrict__ wcnt,
+                                                   const uint64_t* __restrict__ keys,
+                                                   const uint8_t* __restrict__ ntrip, CandRec* cands,
+                                                   const KOut& o, const Slot& m, int t, int lane) {
+    const bool live = t < b.n_tracks;
+    const bool act = live && lane < ntrip[t];
+    const uint64_t key = act ? keys[(size_t)t * k.n_trip + lane] : NOKEY;
+    const int side_r = (int)((key >> 19) & 1);
+    Cand cd;
+    clear_cand(cd);
+    int hg[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) hg[l] = -1;
+    TState s = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (live) s = load_state(b, t);
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        const bool mine = act && side_r == side;
+        if (!__any_sync(FULL, mine)) continue;
+        load_windows(wbeg, wcnt, 2 * t + side, m, lane);
+        stage_windows(k, b, m, lane);
+        if (mine) {
+            extend_fit(k, b, s, m, key, cd);
+#pragma unroll
+            for (int l = 0; l < NL; ++l) hg[l] = (cd.status == 0 && cd.hl[l] >= 0) ? m.h->wbeg[l] + cd.hl[l] : -1;
+        }
+        __syncwarp();
+    }
+    if (SEL) group_select_write<32>(o, t, live, lane, act && cd.status == 0, cd.Q, cd.n, hg, cd.st);
+    else if (act) write_cand(cands, k, t, lane, cd, side_r);
+    __syncwarp();
 }
 
 // SEL = false: write every candidate for the selection kernel; SEL = true:
@@ -855,17 +1002,7 @@ __device__ __forceinline__ void extend_tracks(const KParams& k, const KBatch& b,
         for (int l = 0; l < NL; ++l) hg[l] = (act && cd.status == 0 && cd.hl[l] >= 0) ? mq.h->wbeg[l] + cd.hl[l] : -1;
         group_select_write<G>(o, t, live, r, act && cd.status == 0, cd.Q, cd.n, hg, cd.st);
     } else if (act) {
-        CandRec rec;
-        rec.Q = cd.Q;
-        rec.status = (int8_t)cd.status;
-        rec.n = (int8_t)cd.n;
-#pragma unroll
-        for (int l = 0; l < NL; ++l) rec.hl[l] = (int8_t)(cd.status == 0 ? cd.hl[l] : -1);
-#pragma unroll
-        for (int p = 0; p < 6; ++p) rec.pad[p] = 0;
-#pragma unroll
-        for (int p = 0; p < 6; ++p) rec.st[p] = cd.status == 0 ? cd.st[p] : 0.0f;
-        cands[(size_t)t * k.n_trip + r] = rec;
+        write_cand(cands, k, t, r, cd, 0);
     }
     __syncwarp();
 }
@@ -873,10 +1010,12 @@ __device__ __forceinline__ void extend_tracks(const KParams& k, const KBatch& b,
 // stage 3: extension and fit of every kept triplet; TPW tracks per warp
 // (two when n_triplets <= 16: lanes 0..15 and 16..31).  The persistent
 // variant also selects and writes the output (no candidate round trip).
-template <int TPW, bool P>
+// NOUT: one track per warp (TPW = 1), window sets staged in turn.
+template <int TPW, bool P, bool NOUT>
 __global__ void __launch_bounds__(PLAIN_WARPS * 32, 4) k_extend(
     KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ wcnt,
     const uint64_t* __restrict__ keys, const uint8_t* __restrict__ ntrip, CandRec* cands, KOut o, int* cursor) {
+    static_assert(!NOUT || TPW == 1, "the no-UT extension runs one track per warp");
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Slot sl[TPW];
@@ -884,13 +1023,17 @@ __global__ void __launch_bounds__(PLAIN_WARPS * 32, 4) k_extend(
     for (int q = 0; q < TPW; ++q) sl[q] = slot_at(smem, warp * TPW + q, k.cap);
     if (!P) {
         const int t0 = (blockIdx.x * PLAIN_WARPS + warp) * TPW;
-        if (t0 < b.n_tracks) extend_tracks<TPW, false>(k, b, wbeg, wcnt, keys, ntrip, cands, o, sl, t0, lane);
+        if (t0 < b.n_tracks) {
+            if (NOUT) extend_track_no_ut<false>(k, b, wbeg, wcnt, keys, ntrip, cands, o, sl[0], t0, lane);
+            else extend_tracks<TPW, false>(k, b, wbeg, wcnt, keys, ntrip, cands, o, sl, t0, lane);
+        }
         return;
     }
     for (;;) {
         const int t0 = queue_take(cursor, TPW, lane);
         if (t0 >= b.n_tracks) break;
-        extend_tracks<TPW, true>(k, b, wbeg, wcnt, keys, ntrip, cands, o, sl, t0, lane);
+        if (NOUT) extend_track_no_ut<true>(k, b, wbeg, wcnt, keys, ntrip, cands, o, sl[0], t0, lane);
+        else extend_tracks<TPW, true>(k, b, wbeg, wcnt, keys, ntrip, cands, o, sl, t0, lane);
     }
 }
 
@@ -912,8 +1055,9 @@ __device__ __forceinline__ void select_track(const KParams& k, const int* __rest
         have = r.status == 0;
         Q = r.Q;
         n = r.n;
+        const size_t ws = (size_t)t * (k.no_ut ? 2 : 1) + r.side;
 #pragma unroll
-        for (int l = 0; l < NL; ++l) hg[l] = r.hl[l] >= 0 ? wbeg[(size_t)t * NL + l] + r.hl[l] : -1;
+        for (int l = 0; l < NL; ++l) hg[l] = r.hl[l] >= 0 ? wbeg[ws * NL + l] + r.hl[l] : -1;
 #pragma unroll
         for (int q = 0; q < 6; ++q) st[q] = r.st[q];
     }
@@ -983,7 +1127,7 @@ __global__ void __launch_bounds__(512, 1) k_tile(KParams k, KBatch b, KOut o, in
                 while (t >= __ldg(b.trk_offsets + e + 1)) ++e;
                 st[q] = load_state(b, t);
                 int beg, cnt;
-                warp_windows(k, b, st[q], e, lane, beg, cnt);
+                warp_windows<false>(k, b, st[q], e, lane, 0, beg, cnt);
                 if (lane < NL) {
                     sl[q].h->wbeg[lane] = beg;
                     sl[q].h->wcnt[lane] = cnt;
@@ -1050,19 +1194,21 @@ __global__ void k_debug_triplets(KParams k, KBatch b, const int* __restrict__ wb
                                  int* win_count_out, int* n_trip_out, int* trip_out, float* chi2_out) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= b.n_tracks) return;
-    for (int l = 0; l < NL; ++l) win_count_out[(size_t)t * NL + l] = wcnt[(size_t)t * NL + l];
+    const int ns = k.no_ut ? 2 : 1;
+    for (int l = 0; l < ns * NL; ++l) win_count_out[(size_t)t * ns * NL + l] = wcnt[(size_t)t * ns * NL + l];
     int nt = ntrip[t];
     n_trip_out[t] = nt;
     for (int r = 0; r < nt; ++r) {
         uint64_t key = keys[(size_t)t * k.n_trip + r];
-        int cfg = (int)((key >> 18) & 1);
+        int side = (int)((key >> 19) & 1), cfg = (int)((key >> 18) & 1);
         int j0 = (int)((key >> 12) & 63), j2 = (int)((key >> 6) & 63), j1 = (int)(key & 63);
         int L0 = cfg ? 3 : 0, L1 = cfg ? 7 : 4, L2 = cfg ? 11 : 8;
+        const int* wb = wbeg + ((size_t)t * ns + side) * NL;
         int* q = trip_out + ((size_t)t * k.n_trip + r) * 4;
-        q[0] = cfg;
-        q[1] = wbeg[(size_t)t * NL + L0] + j0;
-        q[2] = wbeg[(size_t)t * NL + L1] + j1;
-        q[3] = wbeg[(size_t)t * NL + L2] + j2;
+        q[0] = cfg + 2 * side;
+        q[1] = wb[L0] + j0;
+        q[2] = wb[L1] + j1;
+        q[3] = wb[L2] + j2;
         chi2_out[(size_t)t * k.n_trip + r] = __uint_as_float((unsigned)(key >> 32));
     }
 }
@@ -1160,28 +1306,36 @@ cudaError_t launch_track_event(const KBatch& b, int* trk_event, cudaStream_t s) 
 cudaError_t launch_windows(const KParams& k, const KBatch& b, const int* trk_event, int* wbeg, uint8_t* wcnt,
                            cudaStream_t s, int* cursor, int blocks) {
     if (b.n_tracks <= 0) return cudaSuccess;
-    if (cursor) k_windows<true><<<blocks, 256, 0, s>>>(k, b, trk_event, wbeg, wcnt, cursor);
-    else k_windows<false><<<cdiv((long)b.n_tracks * 32, 256), 256, 0, s>>>(k, b, trk_event, wbeg, wcnt, nullptr);
+    const int plain_grid = cdiv((long)b.n_tracks * 32, 256);
+    if (k.no_ut) {
+        if (cursor) k_windows<true, true><<<blocks, 256, 0, s>>>(k, b, trk_event, wbeg, wcnt, cursor);
+        else k_windows<false, true><<<plain_grid, 256, 0, s>>>(k, b, trk_event, wbeg, wcnt, nullptr);
+    } else {
+        if (cursor) k_windows<true, false><<<blocks, 256, 0, s>>>(k, b, trk_event, wbeg, wcnt, cursor);
+        else k_windows<false, false><<<plain_grid, 256, 0, s>>>(k, b, trk_event, wbeg, wcnt, nullptr);
+    }
     return cudaGetLastError();
 }
 
-template <int NIT, bool P>
+template <int NIT, bool P, bool NOUT>
 static cudaError_t launch_triplets_t(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* wcnt,
                                      uint64_t* keys, uint8_t* ntrip, cudaStream_t s, int* cursor, int blocks) {
     size_t sm = block_smem_bytes(k.cap, PLAIN_WARPS, 1);
-    cudaError_t err = set_smem((const void*)k_triplets<NIT, P>, sm);
+    cudaError_t err = set_smem((const void*)k_triplets<NIT, P, NOUT>, sm);
     if (err != cudaSuccess) return err;
     const int grid = P ? blocks : cdiv(b.n_tracks, PLAIN_WARPS);
-    k_triplets<NIT, P><<<grid, PLAIN_WARPS * 32, sm, s>>>(k, b, wbeg, wcnt, keys, ntrip, cursor);
+    k_triplets<NIT, P, NOUT><<<grid, PLAIN_WARPS * 32, sm, s>>>(k, b, wbeg, wcnt, keys, ntrip, cursor);
     return cudaGetLastError();
 }
 
+// items per lane NIT: 32 * NIT >= 2 * cap; the no-UT variant always takes 4
 template <bool P>
 static cudaError_t launch_triplets_p(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* wcnt,
                                      uint64_t* keys, uint8_t* ntrip, cudaStream_t s, int* cursor, int blocks) {
-    if (k.cap <= 16) return launch_triplets_t<1, P>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
-    if (k.cap <= 32) return launch_triplets_t<2, P>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
-    return launch_triplets_t<4, P>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
+    if (k.no_ut) return launch_triplets_t<4, P, true>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
+    if (k.cap <= 16) return launch_triplets_t<1, P, false>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
+    if (k.cap <= 32) return launch_triplets_t<2, P, false>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
+    return launch_triplets_t<4, P, false>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
 }
 
 cudaError_t launch_triplets(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
@@ -1193,15 +1347,15 @@ cudaError_t launch_triplets(const KParams& k, const KBatch& b, const int* trk_ev
     return launch_triplets_p<false>(k, b, wbeg, wcnt, keys, ntrip, s, nullptr, 0);
 }
 
-template <int TPW, bool P>
+template <int TPW, bool P, bool NOUT>
 static cudaError_t launch_extend_t(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* wcnt,
                                    const uint64_t* keys, const uint8_t* ntrip, CandRec* cands, const KOut& o,
                                    cudaStream_t s, int* cursor, int blocks) {
     size_t sm = (size_t)PLAIN_WARPS * TPW * slot_bytes(k.cap);
-    cudaError_t err = set_smem((const void*)k_extend<TPW, P>, sm);
+    cudaError_t err = set_smem((const void*)k_extend<TPW, P, NOUT>, sm);
     if (err != cudaSuccess) return err;
     const int grid = P ? blocks : cdiv(b.n_tracks, PLAIN_WARPS * TPW);
-    k_extend<TPW, P><<<grid, PLAIN_WARPS * 32, sm, s>>>(k, b, wbeg, wcnt, keys, ntrip, cands, o, cursor);
+    k_extend<TPW, P, NOUT><<<grid, PLAIN_WARPS * 32, sm, s>>>(k, b, wbeg, wcnt, keys, ntrip, cands, o, cursor);
     return cudaGetLastError();
 }
 
@@ -1210,12 +1364,17 @@ cudaError_t launch_extend(const KParams& k, const KBatch& b, const int* trk_even
                           const KOut& o, cudaStream_t s, int* cursor, int blocks) {
     (void)trk_event;
     if (b.n_tracks <= 0) return cudaSuccess;
-    if (k.n_trip <= 16) {
-        if (cursor) return launch_extend_t<2, true>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, cursor, blocks);
-        return launch_extend_t<2, false>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, nullptr, 0);
+    if (k.no_ut) {
+        if (cursor) return launch_extend_t<1, true, true>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, cursor, blocks);
+        return launch_extend_t<1, false, true>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, nullptr, 0);
     }
-    if (cursor) return launch_extend_t<1, true>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, cursor, blocks);
-    return launch_extend_t<1, false>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, nullptr, 0);
+    if (k.n_trip <= 16) {
+        if (cursor)
+            return launch_extend_t<2, true, false>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, cursor, blocks);
+        return launch_extend_t<2, false, false>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, nullptr, 0);
+    }
+    if (cursor) return launch_extend_t<1, true, false>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, cursor, blocks);
+    return launch_extend_t<1, false, false>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, nullptr, 0);
 }
 
 cudaError_t launch_select(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* ntrip,
@@ -1230,14 +1389,19 @@ cudaError_t launch_select(const KParams& k, const KBatch& b, const int* wbeg, co
 cudaError_t stage_blocks_per_sm(const KParams& k, int* out4) {
     cudaError_t err;
     size_t smt = block_smem_bytes(k.cap, PLAIN_WARPS, 1);
-    const int tpw = k.n_trip <= 16 ? 2 : 1;
+    const int tpw = (k.n_trip <= 16 && !k.no_ut) ? 2 : 1;
     size_t sme = (size_t)PLAIN_WARPS * tpw * slot_bytes(k.cap);
-    const void* ft = k.cap <= 16 ? (const void*)k_triplets<1, true>
-                                 : (k.cap <= 32 ? (const void*)k_triplets<2, true> : (const void*)k_triplets<4, true>);
-    const void* fe = tpw == 2 ? (const void*)k_extend<2, true> : (const void*)k_extend<1, true>;
+    const void* ft = k.no_ut ? (const void*)k_triplets<4, true, true>
+                   : k.cap <= 16 ? (const void*)k_triplets<1, true, false>
+                   : k.cap <= 32 ? (const void*)k_triplets<2, true, false>
+                                 : (const void*)k_triplets<4, true, false>;
+    const void* fe = k.no_ut  ? (const void*)k_extend<1, true, true>
+                   : tpw == 2 ? (const void*)k_extend<2, true, false>
+                              : (const void*)k_extend<1, true, false>;
+    const void* fw = k.no_ut ? (const void*)k_windows<true, true> : (const void*)k_windows<true, false>;
     if ((err = set_smem(ft, smt)) != cudaSuccess) return err;
     if ((err = set_smem(fe, sme)) != cudaSuccess) return err;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out4[0], k_windows<true>, 256, 0)) != cudaSuccess)
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out4[0], fw, 256, 0)) != cudaSuccess)
         return err;
     if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out4[1], ft, PLAIN_WARPS * 32, smt)) != cudaSuccess)
         return err;
@@ -1266,7 +1430,9 @@ static const void* tile_fn(const KParams& k, int tpw, bool sync) {
     return tile_fn_nit<4>(tpw, sync);
 }
 
+// the tile kernel follows VELO-UT input only (no_ut is refused by the API)
 cudaError_t fused_max_blocks_per_sm(const KParams& k, int warps_per_block, int grain, int* out) {
+    if (k.no_ut) return cudaErrorInvalidValue;
     const int tpw = tile_tpw(k, grain & 15);
     const bool sync = (grain >> 4) & 1;
     size_t sm = block_smem_bytes(k.cap, warps_per_block, tpw);
@@ -1278,6 +1444,7 @@ cudaError_t fused_max_blocks_per_sm(const KParams& k, int warps_per_block, int g
 
 cudaError_t launch_fused(const KParams& k, const KBatch& b, const KOut& o, int* cursor, int grain,
                          int warps_per_block, int n_blocks, cudaStream_t s) {
+    if (k.no_ut) return cudaErrorInvalidValue;
     const int tpw = tile_tpw(k, grain & 15);
     const bool sync = (grain >> 4) & 1;
     size_t sm = block_smem_bytes(k.cap, warps_per_block, tpw);

@@ -355,8 +355,9 @@ class Tracker:
         n_t = int(states.sx.numel())
         nt = max(int(self.params["n_triplets"]), 1)
         dev = packed["x"].device
-        d = dict(win_begin=torch.empty((n_t, NL), dtype=torch.int32, device=dev),
-                 win_count=torch.empty((n_t, NL), dtype=torch.int32, device=dev),
+        ns = 2 if self.params.get("no_ut", 0) else 1   # window sets per track, side-major
+        d = dict(win_begin=torch.empty((n_t, ns * NL), dtype=torch.int32, device=dev),
+                 win_count=torch.empty((n_t, ns * NL), dtype=torch.int32, device=dev),
                  n_trip=torch.empty(n_t, dtype=torch.int32, device=dev),
                  trip=torch.full((n_t, nt, 4), -1, dtype=torch.int32, device=dev),
                  trip_chi2=torch.zeros((n_t, nt), dtype=torch.float32, device=dev))
