@@ -51,7 +51,7 @@ extern "C" {
 #define LF_N_BUCKETS 24          /* (zone, layer) buckets per event: zone*12 + layer */
 #define LF_MAX_WINDOW 64         /* largest n_hits_window */
 #define LF_MAX_TRIPLETS 32       /* largest n_triplets */
-#define LF_MAX_BUCKET 8192       /* largest number of hits in one (event, zone, layer) bucket */
+#define LF_MAX_BUCKET 16384      /* largest number of hits in one (event, zone, layer) bucket */
 
 typedef enum {
     LF_OK = 0,
@@ -190,7 +190,10 @@ int32_t lf_device_sm_count(void);
 /* Bucket and sort raw hits: per event, buckets ordered zone*12+layer, x
  * ascending inside a bucket, ties by raw index; -0.0 becomes +0.0.  Output
  * arrays hold raw->n_hits entries and hit_offsets 24*n_events+1.  A plane
- * code >= 24 or a bucket above LF_MAX_BUCKET hits sets a status flag. */
+ * code >= 24 sets status flag 0x2 (the hit is counted in bucket 23); a
+ * bucket above LF_MAX_BUCKET hits sets flag 0x1 and is not sorted (its perm
+ * entries are -1, its other outputs meaningless).  Scratch: none beyond the
+ * context's work-queue cursor. */
 lf_status lf_pack_hits(lf_ctx* ctx, const lf_raw_hits* raw, const lf_packed* packed, void* stream);
 
 /* Plain form: one launch per stage (windows, triplets, extension+fit,

@@ -40,7 +40,7 @@ struct lf_ctx {
     int* cursor = nullptr;   // device work-queue cursors (8 ints)
     unsigned long long generation = 0;  // bumped whenever scratch is reallocated
     int stage_bps[4] = {0, 0, 0, 0};
-    DevBuf trk_event, wbeg, wcnt, keys, ntrip, cands, ev_count, tmp, big_list;
+    DevBuf trk_event, wbeg, wcnt, keys, ntrip, cands, ev_count;
     struct GraphEntry {
         cudaGraphExec_t exec = nullptr;
         cudaStream_t stream = nullptr;
@@ -281,7 +281,7 @@ void lf_destroy(lf_ctx* c) {
     for (auto& kv : c->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     DevBuf* bufs[] = {&c->trk_event, &c->wbeg, &c->wcnt, &c->keys, &c->ntrip,
-                      &c->cands, &c->ev_count, &c->tmp, &c->big_list};
+                      &c->cands, &c->ev_count};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     cudaFree(c->status);
@@ -307,12 +307,11 @@ lf_status lf_pack_hits(lf_ctx* c, const lf_raw_hits* raw, const lf_packed* pk, v
                             !pk->dxdy || !pk->w || !pk->layer || !pk->perm))
         return fail(c, LF_ERR_ARG, "a hit array is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    lf_status st;
-    if ((st = ensure(c, c->tmp, (size_t)raw->n_hits * 20)) != LF_OK) return st;  // bucket-ordered staging
-    if ((st = ensure(c, c->big_list, 2 * ((size_t)raw->n_events * NB + 1) * 4)) != LF_OK) return st;
+    // the pack's two work-queue cursors are the context's last two (the find
+    // stages use the first ones; calls of one context are stream-ordered)
     LF_CUDA(c, launch_pack(raw->raw_offsets, raw->x, raw->z, raw->dxdy, raw->w, raw->plane, raw->n_events,
-                           raw->n_hits, pk->hit_offsets, pk->x, pk->z, pk->dxdy, pk->w, pk->layer, pk->perm,
-                           (int*)c->tmp.p, (int*)c->big_list.p, c->status, c->n_sm, s));
+                           raw->n_hits, pk->hit_offsets, pk->x, pk->z, pk->dxdy, pk->w, pk->layer, pk->perm, c->cursor + 6,
+                           c->status, c->n_sm, s));
     return LF_OK;
 }
 

@@ -11,9 +11,7 @@ constexpr int NL = 12;
 constexpr int NB = 24;
 constexpr int MAX_CAP = 64;     // largest n_hits_window
 constexpr int MAX_NT = 32;      // largest n_triplets
-constexpr int WARP_SORT_MAX = 768;   // buckets up to this size are sorted by one warp
-constexpr int BLOCK_SORT_MAX = 8192; // larger buckets by one block (LF_MAX_BUCKET)
-constexpr int BLOCK_SORT_THREADS = 512;
+constexpr int BLOCK_SORT_MAX = 16384; // largest bucket the pack sorts (LF_MAX_BUCKET)
 
 // Geometry, parameters and the few products both the method and the oracle
 // form once per call (polarity*kappa, polarity*gamma, 1000*dRatio).
@@ -90,10 +88,11 @@ __host__ __device__ inline size_t block_smem_bytes(int cap, int nw, int tpw) {
 }
 
 // ---- launchers (defined in the .cu files) ----
+// persistent per-event pack; cursor: two device ints (the work queues)
 cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, const float* dxdy,
-                        const float* w, const uint8_t* plane, int n_events, int n_hits,
-                        int* hit_offsets, float* ox, float* oz, float* odxdy, float* ow, uint8_t* olayer,
-                        int* perm, int* tmp, int* big_list, int* status, int n_sm, cudaStream_t s);
+                        const float* w, const uint8_t* plane, int n_events, int n_hits, int* hit_offsets,
+                        float* ox, float* oz, float* odxdy, float* ow, uint8_t* olayer, int* perm, int* cursor,
+                        int* status, int n_sm, cudaStream_t s);
 
 cudaError_t launch_track_event(const KBatch& b, int* trk_event, cudaStream_t s);
 // stage kernels: cursor == nullptr launches the plain one-pass grid,

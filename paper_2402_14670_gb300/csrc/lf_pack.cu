@@ -1,25 +1,36 @@
 // Hit packing for sm_103a: per event, bucket the raw hits by (zone, layer),
-// then sort every bucket by x (ties by raw index) and write the SoA.
+// sort every bucket by x (ties by raw index) and write the SoA.
 //
-//   k_pack_bucket   one block per event (grid-stride): each warp counts the
-//                   plane codes of its slice of the event (ranked with
-//                   __match_any_sync), a per-bucket prefix over buckets and
-//                   warps gives the bucket offsets and each warp's cursors,
-//                   and each warp scatters its slice in order: a STABLE
-//                   scatter of raw indices into bucket order, so inside a
-//                   bucket raw indices stay ascending.
-//   k_pack_gather   walks the packed positions in order and copies x (with
-//                   -0 -> +0), z, dxdy, w into bucket order (coalesced
-//                   writes; the raw reads stay inside the events in flight).
-//   k_pack_sort_*   buckets of at most 1024 hits by one warp each, larger
-//                   ones (at most 8192) by one block each; a bin sort in
-//                   shared memory on the contiguous bucket-ordered copy.
-//                   Bins split [min, max] of the bucket into as many equal
-//                   parts as hits (the bin is a monotone function of x); each
-//                   bin is then ordered by (x, position) with an insertion
-//                   sort; positions follow raw order, so the result is the
-//                   exact (x, raw index) order whatever the data.
-//   The sorted bucket is written out coalesced: x, z, dxdy, w, layer, perm.
+// Two kernels.  k_pack_event (persistent): a block takes one event at a
+// time from a device work queue and sorts it in shared memory:
+//   count     the plane codes of the event are counted per warp (peers by
+//             __match_any_sync, warp-private counters); an exclusive scan of
+//             the totals gives the bucket offsets, written to hit_offsets.
+//   chunk     consecutive buckets are grouped into chunks of at most CHUNK
+//             hits (one chunk for all but the largest events); per chunk:
+//   scatter   the event's hits of the chunk's buckets are placed, bucket
+//             by bucket, into shared memory as (x with -0 -> +0, raw index
+//             inside the event): every warp owns a fixed share of the hits
+//             and, from the counts, its own cursor per bucket (no shared
+//             atomics); a warp per bucket then reduces the bucket's x range;
+//   bin sort  every bucket is split into as many equal x bins as it has hits
+//             (a monotone function of x), and the bins of all buckets of the
+//             chunk are counted, scanned and filled by the whole block at
+//             once; each bin is then ordered by (x, raw index) with an
+//             insertion sort, so the result is the exact (x, raw index) order
+//             whatever the data and whatever the order of the scatter;
+//   write     the chunk's output range is contiguous: x, layer and perm are
+//             written coalesced from shared memory.
+// While an event is processed, the block has already taken its next event
+// from the queue and prefetched that event's plane codes and x into L2.
+// k_pack_payload then walks the packed positions in order (coalesced
+// writes) and gathers z, dxdy and w through perm: scattered 4-byte reads
+// want many loads in flight, i.e. a kernel at full occupancy rather than
+// one large block per SM.
+// A bucket above CHUNK hits cannot be sorted: it is flagged (status bit
+// 0x1), its perm entries are set to -1 and its other outputs are not
+// meaningful; a plane code >= 24 is flagged (0x2) and counted in the last
+// bucket.
 #include <cstdint>
 
 #include "lf_internal.h"
@@ -29,10 +40,32 @@ namespace lfk {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int BUCKET_THREADS = 256;
-constexpr int BUCKET_WARPS = BUCKET_THREADS / 32;
-constexpr int WARP_MAX = 1024;      // bucket size sorted by one warp
-constexpr int SORT_THREADS = 256;   // 8 warps: 8 warp areas of WARP_MAX == one block area of BLOCK_SORT_MAX
+constexpr int PACK_THREADS = 1024;
+constexpr int PACK_WARPS = PACK_THREADS / 32;
+constexpr int CHUNK = BLOCK_SORT_MAX;  // hits sorted together in shared memory
+constexpr int UNROLL = 4;              // hits per thread with loads in flight together
+
+// shared memory per element: x, raw index, bin counter (16-bit halves of
+// 32-bit words), slot inside the bin, element at each sorted position
+constexpr size_t AREA_BYTES = (size_t)CHUNK * (4 + 4 + 2 + 2 + 2);
+
+struct Area {
+    float* xs;          // x of element k
+    uint32_t* id;       // raw index of element k, relative to the event
+    uint32_t* bins2;    // bin counters / starts, two 16-bit values per word
+    uint16_t* slot;     // slot of element k inside its bin
+    uint16_t* order;    // element at sorted position j
+};
+
+__device__ __forceinline__ Area area_at(char* p) {
+    Area a;
+    a.xs = reinterpret_cast<float*>(p);
+    a.id = reinterpret_cast<uint32_t*>(p + (size_t)CHUNK * 4);
+    a.bins2 = reinterpret_cast<uint32_t*>(p + (size_t)CHUNK * 8);
+    a.slot = reinterpret_cast<uint16_t*>(p + (size_t)CHUNK * 10);
+    a.order = reinterpret_cast<uint16_t*>(p + (size_t)CHUNK * 12);
+    return a;
+}
 
 __device__ __forceinline__ int wscan_incl(int v, int lane) {
 #pragma unroll
@@ -43,302 +76,372 @@ __device__ __forceinline__ int wscan_incl(int v, int lane) {
     return v;
 }
 
-// Staging of one batch in bucket order: raw index, x (with -0 -> +0), z,
-// dxdy, w.
-struct Staged {
-    int* idx;
-    float *x, *z, *d, *w;
-};
-
-__global__ void __launch_bounds__(BUCKET_THREADS) k_pack_bucket(
-    const int* __restrict__ raw_offsets, const uint8_t* __restrict__ plane, int n_events, int* hit_offsets,
-    int* tmp, int* big_list, int* status) {
-    __shared__ int wc[BUCKET_WARPS][NB];   // per-warp counts, then per-warp cursors
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int e = blockIdx.x; e < n_events; e += gridDim.x) {
-        const int rb = raw_offsets[e], re = raw_offsets[e + 1];
-        const int slice = ((re - rb + BUCKET_WARPS - 1) / BUCKET_WARPS + 31) & ~31;
-        const int s0 = min(rb + warp * slice, re), s1 = min(s0 + slice, re);
-        if (lane < NB) wc[warp][lane] = 0;
-        __syncwarp();
-        for (int base = s0; base < s1; base += 32) {
-            int i = base + lane;
-            int p = -1;
-            if (i < s1) {
-                p = plane[i];
-                if (p >= NB) {
-                    atomicOr(status, 0x2);
-                    p = NB - 1;
-                }
-            }
-            unsigned peers = __match_any_sync(FULL, p);
-            if (p >= 0 && lane == __ffs(peers) - 1) wc[warp][p] += __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        if (tid < 32) {
-            // bucket totals, their exclusive scan, then each warp's cursor
-            int tot = 0;
-            if (lane < NB)
-                for (int w = 0; w < BUCKET_WARPS; ++w) tot += wc[w][lane];
-            int inc = wscan_incl(tot, lane);
-            int start = rb + inc - tot;
-            if (lane < NB) {
-                hit_offsets[(size_t)e * NB + lane] = start;
-                if (tot > BLOCK_SORT_MAX) atomicOr(status, 0x1);
-                else if (tot > WARP_MAX) big_list[1 + atomicAdd(big_list, 1)] = e * NB + lane;
-                int acc = start;
-                for (int w = 0; w < BUCKET_WARPS; ++w) {
-                    int c = wc[w][lane];
-                    wc[w][lane] = acc;
-                    acc += c;
-                }
-            }
-        }
-        __syncthreads();
-        for (int base = s0; base < s1; base += 32) {
-            int i = base + lane;
-            int p = -1;
-            if (i < s1) {
-                p = plane[i];
-                if (p >= NB) p = NB - 1;
-            }
-            unsigned peers = __match_any_sync(FULL, p);
-            int rank = __popc(peers & ((1u << lane) - 1u));
-            int cur = p >= 0 ? wc[warp][p] : 0;
-            __syncwarp();
-            if (p >= 0) {
-                tmp[cur + rank] = i;
-                if (rank == 0) wc[warp][p] = cur + __popc(peers);
-            }
-            __syncwarp();
-        }
-        __syncthreads();
-    }
-    if (blockIdx.x == 0 && tid == 0) hit_offsets[(size_t)n_events * NB] = raw_offsets[n_events];
+// x as an unsigned integer with the same order (-0 already turned into +0)
+__device__ __forceinline__ unsigned ordered(float x) {
+    unsigned u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unordered(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
-// Bucket-ordered copy of the hit data: packed positions are walked in order
-// (coalesced writes); the raw reads stay inside the few events in flight, so
-// they are served by L2.
-__global__ void k_pack_gather(const float* __restrict__ x, const float* __restrict__ z,
-                              const float* __restrict__ dxdy, const float* __restrict__ w, int n_hits, Staged sg) {
-    const int stride = gridDim.x * blockDim.x;
-#pragma unroll 4
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_hits; j += stride) {
-        const int r = sg.idx[j];
-        sg.x[j] = __ldg(x + r) + 0.0f;
-        sg.z[j] = __ldg(z + r);
-        sg.d[j] = __ldg(dxdy + r);
-        sg.w[j] = __ldg(w + r);
-    }
-}
-
-__device__ __forceinline__ int bin_of(float x, float xmin, float scale, int nb) {
-    float f = (x - xmin) * scale;   // monotone in x; NaN only when x == xmin and scale is infinite
+__device__ __forceinline__ int bin_of(float x, float lo, float scale, int nb) {
+    float f = (x - lo) * scale;   // monotone in x
     if (!(f > 0.0f)) return 0;
     if (!(f < (float)nb)) return nb - 1;
     return (int)f;
 }
 
-template <bool BLOCK>
-__device__ __forceinline__ void gsync() {
-    if (BLOCK) __syncthreads(); else __syncwarp();
+// 16-bit counter i of the packed bin array
+__device__ __forceinline__ unsigned bin_add(uint32_t* bins2, int i) {
+    unsigned old = atomicAdd(&bins2[i >> 1], (i & 1) ? 0x10000u : 1u);
+    return (i & 1) ? (old >> 16) : (old & 0xffffu);
+}
+__device__ __forceinline__ unsigned bin_get(const uint32_t* bins2, int i) {
+    unsigned v = bins2[i >> 1];
+    return (i & 1) ? (v >> 16) : (v & 0xffffu);
 }
 
-// Work area of one bucket sort (m entries each): keys x, bin counters, and
-// the positions (0..m-1, raw order inside the bucket) in sorted order.
-struct SortArea {
-    float* xa;
-    int* bins;
-    uint16_t* pos;    // slot of each element inside its bin
-    uint16_t* pos2;   // positions in sorted order
+struct EvShared {
+    uint16_t wcur[PACK_WARPS][NB];   // per-warp scatter cursor inside each bucket
+    int cnt[NB];                // bucket sizes
+    int off[NB + 1];            // bucket offsets inside the event
+    int coff[NB + 1];           // bucket offsets inside the chunk
+    float blo[NB], bscale[NB];  // bin mapping of each bucket
+    int warp_tot[PACK_WARPS];
+    int event, next;
 };
 
-// Cooperative bin sort of one bucket by a warp (BLOCK = false) or a block.
-template <bool BLOCK>
-__device__ void sort_bucket(const Staged& sg, int b0, int m, int layer, float* ox, float* oz, float* od, float* ow,
-                            uint8_t* ol, int* perm, SortArea a, int rank, int size, float* red_f, int* red_i) {
-    const int lane = rank & 31, wid = rank >> 5, nw = size >> 5;
-    float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
-#pragma unroll 8
-    for (int i = rank; i < m; i += size) {
-        float xv = sg.x[b0 + i];
-        a.xa[i] = xv;
-        lo = fminf(lo, xv);
-        hi = fmaxf(hi, xv);
-    }
+// L2 prefetch of bytes [p, p + bytes): one instruction per 128-byte line,
+// each line holding at least one byte of the range
+__device__ __forceinline__ void prefetch_range(const void* p, size_t bytes, int tid) {
+    if (bytes == 0) return;
+    const uintptr_t b0 = reinterpret_cast<uintptr_t>(p) & ~uintptr_t(127);
+    const uintptr_t b1 = reinterpret_cast<uintptr_t>(p) + bytes - 1;
+    const int lines = (int)((b1 - b0) / 128) + 1;
+    for (int q = tid; q < lines; q += PACK_THREADS)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(b0 + (uintptr_t)q * 128));
+}
+
+// bucket of chunk element k: the last bucket q in [qa, ql] with coff[q] <= k
+// (an empty bucket shares its offset with the next one, so the last wins)
+__device__ __forceinline__ int bucket_of(const EvShared& sh, int qa, int ql, int k) {
+    int lo = qa, hi = ql;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = fminf(lo, __shfl_xor_sync(FULL, lo, o));
-        hi = fmaxf(hi, __shfl_xor_sync(FULL, hi, o));
+    for (int it = 0; it < 5; ++it) {   // 2^5 >= 24 buckets
+        const int mid = (lo + hi + 1) >> 1;
+        if (lo < hi) {
+            if (sh.coff[mid] <= k) lo = mid; else hi = mid - 1;
+        }
     }
-    if (BLOCK) {
-        if (lane == 0) {
-            red_f[wid] = lo;
-            red_f[32 + wid] = hi;
+    return lo;
+}
+
+__global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
+    const int* __restrict__ raw_offsets, const float* __restrict__ x, const uint8_t* __restrict__ plane,
+    int n_events, int* hit_offsets, float* ox, uint8_t* ol, int* perm, int* cursor, int* status) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ EvShared sh;
+    const Area a = area_at(smem);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (blockIdx.x == 0 && tid == 0) hit_offsets[(size_t)n_events * NB] = raw_offsets[n_events];
+    if (tid == 0) sh.next = atomicAdd(cursor, 1);
+    for (;;) {
+        __syncthreads();   // the previous event is fully consumed
+        if (tid == 0) {
+            sh.event = sh.next;
+            sh.next = sh.event < n_events ? atomicAdd(cursor, 1) : n_events;
         }
         __syncthreads();
-        lo = red_f[0];
-        hi = red_f[32];
-        for (int q = 1; q < nw; ++q) {
-            lo = fminf(lo, red_f[q]);
-            hi = fmaxf(hi, red_f[32 + q]);
-        }
-    }
-    const int nb = m;
-    const float scale = hi > lo ? (float)nb / (hi - lo) : 0.0f;
-    for (int i = rank; i < nb; i += size) a.bins[i] = 0;
-    gsync<BLOCK>();
-    // counting pass; the returned count is the element's slot inside its bin
-    for (int i = rank; i < m; i += size) a.pos[i] = (uint16_t)atomicAdd(&a.bins[bin_of(a.xa[i], lo, scale, nb)], 1);
-    gsync<BLOCK>();
-    {
-        // exclusive scan of the bin counts: a contiguous chunk per thread
-        const int per = (nb + size - 1) / size;
-        const int s0 = min(rank * per, nb), s1 = min(s0 + per, nb);
-        int sum = 0;
-        for (int i = s0; i < s1; ++i) sum += a.bins[i];
-        int inc = wscan_incl(sum, lane);
-        int excl = inc - sum;
-        if (BLOCK) {
-            if (lane == 31) red_i[wid] = inc;
-            __syncthreads();
-            int base = 0;
-            for (int q = 0; q < wid; ++q) base += red_i[q];
-            excl += base;
-        }
-        for (int i = s0; i < s1; ++i) {
-            int c = a.bins[i];
-            a.bins[i] = excl;
-            excl += c;
-        }
-    }
-    gsync<BLOCK>();
-    // placement: bins[b] is the start of bin b; slot from the counting pass
-    // (positions go to a second array: the first still holds the slots)
-    for (int i = rank; i < m; i += size) {
-        int d = a.bins[bin_of(a.xa[i], lo, scale, nb)] + a.pos[i];
-        a.pos2[d] = (uint16_t)i;
-    }
-    gsync<BLOCK>();
-    // order each bin by (x, position); bin b ends where bin b+1 starts
-    for (int bn = rank; bn < nb; bn += size) {
-        int s = a.bins[bn], e = bn + 1 < nb ? a.bins[bn + 1] : m;
-        for (int i = s + 1; i < e; ++i) {
-            int pv = a.pos2[i];
-            float xv = a.xa[pv];
-            int j = i - 1;
-            while (j >= s) {
-                int pj = a.pos2[j];
-                float xj = a.xa[pj];
-                if (!(xv < xj || (xv == xj && pv < pj))) break;
-                a.pos2[j + 1] = (uint16_t)pj;
-                --j;
+        const int e = sh.event;
+        if (e >= n_events) break;
+        const int rb = raw_offsets[e], n = raw_offsets[e + 1] - rb;
+        // the next event's raw arrays go to L2 while this one is processed
+        // (addresses inside the next event's range only)
+        if (sh.next < n_events) {
+            const int nb0 = raw_offsets[sh.next], nn = raw_offsets[sh.next + 1] - nb0;
+            if (nn > 0) {
+                prefetch_range(plane + nb0, (size_t)nn, tid);
+                prefetch_range(x + nb0, (size_t)nn * 4, tid);
             }
-            a.pos2[j + 1] = (uint16_t)pv;
+        }
+
+        // count into warp-private counters (in the element area, unused until
+        // the scatter); the leader of each group of equal codes adds its size
+        int* wcnt = reinterpret_cast<int*>(smem) + warp * NB;
+        if (lane < NB) wcnt[lane] = 0;
+        __syncwarp();
+        bool bad = false;
+        for (int base = warp * 32; base < n; base += PACK_THREADS * UNROLL) {
+            int pu[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int i = base + u * PACK_THREADS + lane;
+                pu[u] = i < n ? (int)plane[rb + i] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                int p = pu[u];
+                if (p >= NB) {
+                    bad = true;
+                    p = NB - 1;
+                }
+                const unsigned peers = __match_any_sync(FULL, p);
+                if (p >= 0 && lane == __ffs(peers) - 1) wcnt[p] += __popc(peers);
+                __syncwarp();
+            }
+        }
+        if (bad) atomicOr(status, 0x2);
+        wcnt = reinterpret_cast<int*>(smem);
+        __syncthreads();
+        if (tid < 32) {
+            // bucket totals; each warp's cursor starts after the earlier warps' hits
+            int c = 0;
+            if (lane < NB)
+                for (int q = 0; q < PACK_WARPS; ++q) {
+                    sh.wcur[q][lane] = (uint16_t)c;
+                    c += wcnt[q * NB + lane];
+                }
+            const int inc = wscan_incl(c, lane);
+            if (lane < NB) {
+                sh.cnt[lane] = c;
+                sh.off[lane] = inc - c;
+                hit_offsets[(size_t)e * NB + lane] = rb + inc - c;
+                if (c > CHUNK) atomicOr(status, 0x1);
+            }
+            if (lane == NB - 1) sh.off[NB] = inc;
+        }
+        __syncthreads();
+
+        // chunks of consecutive buckets (every thread takes the same decisions)
+        int qa = 0;
+        while (qa < NB) {
+            int qb = qa, tot = 0;
+            while (qb < NB && tot + sh.cnt[qb] <= CHUNK) tot += sh.cnt[qb++];
+            if (qb == qa) {   // a bucket above CHUNK hits: flagged above, not sorted
+                const size_t o0 = (size_t)rb + sh.off[qa];
+                for (int j = tid; j < sh.cnt[qa]; j += PACK_THREADS) perm[o0 + j] = -1;
+                ++qa;
+                continue;
+            }
+            if (tot == 0) {
+                qa = qb;
+                continue;
+            }
+            const int ql = qb - 1;
+            // scatter the chunk's hits, bucket by bucket; a warp visits the
+            // same hits as in the count and advances its own cursors
+            if (tid < NB) sh.coff[tid] = (tid >= qa && tid < qb) ? sh.off[tid] - sh.off[qa] : 0;
+            __syncthreads();
+            for (int base = 0; base < n; base += PACK_THREADS * UNROLL) {
+                int pu[UNROLL];
+                float xu[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const int i = base + u * PACK_THREADS + tid;
+                    pu[u] = -1;
+                    xu[u] = 0.0f;
+                    if (i < n) {
+                        pu[u] = plane[rb + i];
+                        xu[u] = x[rb + i];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                const int i = base + u * PACK_THREADS + tid;
+                int p = pu[u];
+                if (p >= NB) p = NB - 1;
+                if (p < qa || p >= qb) p = -1;
+                const unsigned peers = __match_any_sync(FULL, p);
+                const int cur = p >= 0 ? (int)sh.wcur[warp][p] : 0;
+                __syncwarp();
+                if (p >= 0) {
+                    const int rank = __popc(peers & ((1u << lane) - 1u));
+                    if (rank == 0) sh.wcur[warp][p] = (uint16_t)(cur + __popc(peers));
+                    const int k = sh.coff[p] + cur + rank;
+                    a.xs[k] = xu[u] + 0.0f;
+                    a.id[k] = (uint32_t)i;
+                }
+                __syncwarp();
+                }
+            }
+            for (int q = tid; q < (tot + 1) / 2; q += PACK_THREADS) a.bins2[q] = 0u;
+            __syncthreads();
+            // x range of bucket q, reduced by warp q - qa (buckets of a chunk <= 24 < 32 warps)
+            {
+                const int q = qa + warp;
+                if (q < qb) {
+                    const int m = sh.cnt[q], k0 = sh.coff[q];
+                    unsigned mn = 0xffffffffu, mx = 0u;
+                    for (int k = lane; k < m; k += 32) {
+                        const unsigned ov = ordered(a.xs[k0 + k]);
+                        mn = min(mn, ov);
+                        mx = max(mx, ov);
+                    }
+                    mn = __reduce_min_sync(FULL, mn);
+                    mx = __reduce_max_sync(FULL, mx);
+                    if (lane == 0) {
+                        float lo = 0.0f, scale = 0.0f;
+                        if (m > 0) {
+                            lo = unordered(mn);
+                            const float hi = unordered(mx);
+                            scale = hi > lo ? (float)m / (hi - lo) : 0.0f;
+                        }
+                        sh.blo[q] = lo;
+                        sh.bscale[q] = scale;
+                    }
+                }
+            }
+            __syncthreads();
+
+            // count: bin of element k = bucket offset + bin inside the bucket
+            for (int k = tid; k < tot; k += PACK_THREADS) {
+                const int q = bucket_of(sh, qa, ql, k);
+                const int bn = sh.coff[q] + bin_of(a.xs[k], sh.blo[q], sh.bscale[q], sh.cnt[q]);
+                a.slot[k] = (uint16_t)bin_add(a.bins2, bn);
+            }
+            __syncthreads();
+            // exclusive scan of the tot counters; every thread's run starts
+            // on an even counter, so each 32-bit word has a single writer
+            {
+                const int per = 2 * ((tot + 2 * PACK_THREADS - 1) / (2 * PACK_THREADS));
+                const int s0 = min(tid * per, tot), s1 = min(s0 + per, tot);
+                int sum = 0;
+                for (int i = s0; i < s1; ++i) sum += (int)bin_get(a.bins2, i);
+                const int inc = wscan_incl(sum, lane);
+                if (lane == 31) sh.warp_tot[warp] = inc;
+                __syncthreads();
+                int excl = inc - sum;
+                for (int q = 0; q < warp; ++q) excl += sh.warp_tot[q];
+                for (int i = s0; i < s1; i += 2) {
+                    const unsigned v = a.bins2[i >> 1];
+                    const unsigned c0 = v & 0xffffu, c1 = v >> 16;
+                    const unsigned st0 = (unsigned)excl, st1 = st0 + c0;
+                    a.bins2[i >> 1] = st0 | (st1 << 16);
+                    excl += (int)(c0 + c1);
+                }
+            }
+            __syncthreads();
+            // placement
+            for (int k = tid; k < tot; k += PACK_THREADS) {
+                const int q = bucket_of(sh, qa, ql, k);
+                const int bn = sh.coff[q] + bin_of(a.xs[k], sh.blo[q], sh.bscale[q], sh.cnt[q]);
+                a.order[bin_get(a.bins2, bn) + a.slot[k]] = (uint16_t)k;
+            }
+            __syncthreads();
+            // order each bin by (x, raw index); bin b ends where b + 1 starts
+            for (int bn = tid; bn < tot; bn += PACK_THREADS) {
+                const int s = (int)bin_get(a.bins2, bn), en = bn + 1 < tot ? (int)bin_get(a.bins2, bn + 1) : tot;
+                for (int i = s + 1; i < en; ++i) {
+                    const int pv = a.order[i];
+                    const float xv = a.xs[pv];
+                    const uint32_t iv = a.id[pv];
+                    int j = i - 1;
+                    while (j >= s) {
+                        const int pj = a.order[j];
+                        const float xj = a.xs[pj];
+                        if (!(xv < xj || (xv == xj && iv < a.id[pj]))) break;
+                        a.order[j + 1] = (uint16_t)pj;
+                        --j;
+                    }
+                    a.order[j + 1] = (uint16_t)pv;
+                }
+            }
+            __syncthreads();
+            // the chunk's output range is contiguous
+            {
+                const size_t o0 = (size_t)rb + sh.off[qa];
+#pragma unroll 4
+                for (int j = tid; j < tot; j += PACK_THREADS) {
+                    const int q = bucket_of(sh, qa, ql, j);
+                    const int k = a.order[j];
+                    const size_t o = o0 + j;
+                    ox[o] = a.xs[k];
+                    ol[o] = (uint8_t)(q % NL);
+                    perm[o] = rb + (int)a.id[k];
+                }
+            }
+            __syncthreads();
+            qa = qb;
         }
     }
-    gsync<BLOCK>();
-#pragma unroll 4
-    for (int i = rank; i < m; i += size) {
-        int pv = a.pos2[i];
-        size_t o = (size_t)b0 + i, q = (size_t)b0 + pv;
-        ox[o] = a.xa[pv];
-        oz[o] = sg.z[q];
-        od[o] = sg.d[q];
-        ow[o] = sg.w[q];
-        ol[o] = (uint8_t)layer;
-        perm[o] = sg.idx[q];
-    }
-    gsync<BLOCK>();
 }
 
-__host__ __device__ constexpr size_t area_bytes(int n) { return (size_t)n * 12; }
+// z, dxdy and w in packed order: position o takes raw hit perm[o].  Blocks
+// take tiles of consecutive positions from a work queue, so the tiles in
+// flight stay a narrow window of events whose raw lines L2 reuses (a grid
+// stride lets warps drift apart over the batch and loses that reuse).
+constexpr int PAYLOAD_THREADS = 256;
+constexpr int PAYLOAD_PER_THREAD = 8;
+constexpr int PAYLOAD_TILE = PAYLOAD_THREADS * PAYLOAD_PER_THREAD;
 
-__device__ __forceinline__ SortArea area_at(char* p, int n) {
-    SortArea a;
-    a.xa = reinterpret_cast<float*>(p);
-    a.bins = reinterpret_cast<int*>(p + (size_t)n * 4);
-    a.pos = reinterpret_cast<uint16_t*>(p + (size_t)n * 8);
-    a.pos2 = reinterpret_cast<uint16_t*>(p + (size_t)n * 10);
-    return a;
-}
-
-constexpr int SMALL_WARPS = 4;   // warps per block of the small-bucket kernel
-
-// Buckets of at most WARP_MAX hits: one warp each (grid-stride over buckets).
-__global__ void __launch_bounds__(SMALL_WARPS * 32) k_pack_sort_small(
-    const int* __restrict__ hit_offsets, Staged sg, int n_buckets, float* ox, float* oz, float* od, float* ow,
-    uint8_t* ol, int* perm) {
-    extern __shared__ __align__(16) char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const SortArea wa = area_at(smem + (size_t)warp * area_bytes(WARP_MAX), WARP_MAX);
-    for (int q = blockIdx.x * SMALL_WARPS + warp; q < n_buckets; q += gridDim.x * SMALL_WARPS) {
-        int b0 = hit_offsets[q], m = hit_offsets[q + 1] - b0;
-        if (m >= 1 && m <= WARP_MAX)
-            sort_bucket<false>(sg, b0, m, (q % NB) % NL, ox, oz, od, ow, ol, perm, wa, lane, 32, nullptr, nullptr);
-    }
-}
-
-// Buckets above WARP_MAX hits (listed by k_pack_bucket): one block each.
-__global__ void __launch_bounds__(SORT_THREADS) k_pack_sort_large(
-    const int* __restrict__ hit_offsets, const int* __restrict__ list, Staged sg, float* ox, float* oz, float* od,
-    float* ow, uint8_t* ol, int* perm) {
-    extern __shared__ __align__(16) char smem[];
-    __shared__ float red_f[64];
-    __shared__ int red_i[32];
-    const SortArea ba = area_at(smem, BLOCK_SORT_MAX);
-    const int n = list[0];
-    for (int k = blockIdx.x; k < n; k += gridDim.x) {
-        int q = list[1 + k];
-        int b0 = hit_offsets[q], m = hit_offsets[q + 1] - b0;
-        sort_bucket<true>(sg, b0, m, (q % NB) % NL, ox, oz, od, ow, ol, perm, ba, threadIdx.x, SORT_THREADS, red_f,
-                          red_i);
+__global__ void __launch_bounds__(PAYLOAD_THREADS) k_pack_payload(
+    const float* __restrict__ z, const float* __restrict__ dxdy, const float* __restrict__ w,
+    const int* __restrict__ perm, int n_hits, float* __restrict__ oz, float* __restrict__ od,
+    float* __restrict__ ow, int* cursor) {
+    __shared__ int s_tile;
+    const int n_tiles = (n_hits + PAYLOAD_TILE - 1) / PAYLOAD_TILE;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(cursor, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        __syncthreads();
+        if (tile >= n_tiles) break;
+        const int o0 = tile * PAYLOAD_TILE + threadIdx.x;
+        int r[PAYLOAD_PER_THREAD];
+#pragma unroll
+        for (int u = 0; u < PAYLOAD_PER_THREAD; ++u) {
+            const int o = o0 + u * PAYLOAD_THREADS;
+            r[u] = o < n_hits ? perm[o] : -1;
+        }
+        float vz[PAYLOAD_PER_THREAD], vd[PAYLOAD_PER_THREAD], vw[PAYLOAD_PER_THREAD];
+#pragma unroll
+        for (int u = 0; u < PAYLOAD_PER_THREAD; ++u) {
+            // r < 0: past the end, or a bucket the pack could not sort
+            vz[u] = r[u] >= 0 ? __ldg(z + r[u]) : 0.0f;
+            vd[u] = r[u] >= 0 ? __ldg(dxdy + r[u]) : 0.0f;
+            vw[u] = r[u] >= 0 ? __ldg(w + r[u]) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < PAYLOAD_PER_THREAD; ++u) {
+            const int o = o0 + u * PAYLOAD_THREADS;
+            if (o < n_hits) {
+                oz[o] = vz[u];
+                od[o] = vd[u];
+                ow[o] = vw[u];
+            }
+        }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, const float* dxdy,
-                        const float* w, const uint8_t* plane, int n_events, int n_hits,
-                        int* hit_offsets, float* ox, float* oz, float* odxdy, float* ow, uint8_t* olayer,
-                        int* perm, int* tmp, int* big_list, int* status, int n_sm, cudaStream_t s) {
-    if (n_events <= 0) return cudaMemsetAsync(hit_offsets, 0, sizeof(int), s);
-    // tmp holds 5 arrays of n_hits 4-byte words: the bucket-ordered staging
-    Staged sg;
-    sg.idx = tmp;
-    sg.x = reinterpret_cast<float*>(tmp + (size_t)n_hits);
-    sg.z = sg.x + (size_t)n_hits;
-    sg.d = sg.z + (size_t)n_hits;
-    sg.w = sg.d + (size_t)n_hits;
-    cudaError_t err = cudaMemsetAsync(big_list, 0, sizeof(int), s);
+cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, const float* dxdy, const float* w,
+                        const uint8_t* plane, int n_events, int n_hits, int* hit_offsets, float* ox, float* oz,
+                        float* odxdy, float* ow, uint8_t* olayer, int* perm, int* cursor, int* status, int n_sm,
+                        cudaStream_t s) {
+    cudaError_t err =
+        cudaFuncSetAttribute(k_pack_event, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AREA_BYTES);
     if (err != cudaSuccess) return err;
-    int grid = n_events < n_sm * 8 ? n_events : n_sm * 8;
-    k_pack_bucket<<<grid, BUCKET_THREADS, 0, s>>>(raw_offsets, plane, n_events, hit_offsets, tmp, big_list, status);
+    int bps = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_pack_event, PACK_THREADS, AREA_BYTES);
+    if (err != cudaSuccess) return err;
+    if (bps < 1) bps = 1;
+    if ((err = cudaMemsetAsync(cursor, 0, 2 * sizeof(int), s)) != cudaSuccess) return err;
+    int grid = n_sm * bps;
+    if (grid > n_events) grid = n_events > 0 ? n_events : 1;
+    k_pack_event<<<grid, PACK_THREADS, AREA_BYTES, s>>>(raw_offsets, x, plane, n_events, hit_offsets, ox, olayer,
+                                                        perm, cursor, status);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (n_hits > 0) {
-        int gg = (int)(((long)n_hits + 255) / 256);
-        if (gg > n_sm * 32) gg = n_sm * 32;
-        k_pack_gather<<<gg, 256, 0, s>>>(x, z, dxdy, w, n_hits, sg);
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        int bpp = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpp, k_pack_payload, PAYLOAD_THREADS, 0);
+        if (err != cudaSuccess) return err;
+        const long tiles = ((long)n_hits + PAYLOAD_TILE - 1) / PAYLOAD_TILE;
+        int gp = n_sm * (bpp > 0 ? bpp : 1);
+        if (gp > tiles) gp = (int)tiles;
+        k_pack_payload<<<gp, PAYLOAD_THREADS, 0, s>>>(z, dxdy, w, perm, n_hits, oz, odxdy, ow, cursor + 1);
     }
-    const int n_buckets = n_events * NB;
-    const size_t sms = (size_t)SMALL_WARPS * area_bytes(WARP_MAX);
-    if ((err = cudaFuncSetAttribute(k_pack_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms)) !=
-        cudaSuccess)
-        return err;
-    int gsm = (n_buckets + SMALL_WARPS - 1) / SMALL_WARPS;
-    if (gsm > n_sm * 32) gsm = n_sm * 32;
-    k_pack_sort_small<<<gsm, SMALL_WARPS * 32, sms, s>>>(hit_offsets, sg, n_buckets, ox, oz, odxdy, ow, olayer,
-                                                         perm);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    const size_t sml = area_bytes(BLOCK_SORT_MAX);
-    if ((err = cudaFuncSetAttribute(k_pack_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sml)) !=
-        cudaSuccess)
-        return err;
-    k_pack_sort_large<<<n_sm * 2, SORT_THREADS, sml, s>>>(hit_offsets, big_list, sg, ox, oz, odxdy, ow, olayer,
-                                                          perm);
     return cudaGetLastError();
 }
 

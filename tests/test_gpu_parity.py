@@ -127,7 +127,7 @@ def test_empty_batch(lfm):
 
 def test_bucket_over_capacity_is_reported(lfm):
     # one bucket above the largest sortable size: the pack skips it and flags it
-    n = 8193
+    n = 16385   # LF_MAX_BUCKET + 1
     hits = [(0, 1, float(i % 5000)) for i in range(n)]
     b = make_batch([dict(hits=hits, states=[])], synth.Geometry()).to("cuda")
     tr = _tracker(lfm)
