@@ -231,10 +231,13 @@ typedef struct {
 
 /* End-to-end call on host buffers: the batch is cut at event boundaries into
  * chunks of at most chunk_hits hits; each chunk is copied to the device,
- * packed, followed (persistent form) and its results copied back, with two
- * chunks in flight on two internal streams so copies overlap compute.  The
- * device staging buffers belong to the context.  Synchronous: returns after
- * the results are in host memory.  chunk_hits <= 0 selects 1<<26. */
+ * packed, followed (persistent form) and its results copied back.  Three
+ * internal streams (copies in, compute, copies out) chained by events over
+ * three device staging slots form a pipeline: the copies in of chunk k+1,
+ * the compute of chunk k and the copies out of chunk k-1 overlap.  The
+ * staging slots and the compute scratch belong to the context and are sized
+ * before the first copy.  Synchronous: returns after the results are in host
+ * memory.  chunk_hits <= 0 selects 1<<26. */
 lf_status lf_process_host(lf_ctx* ctx, const lf_host_batch* batch, const lf_host_output* out,
                           const lf_tuning* tuning, int64_t chunk_hits);
 

@@ -46,11 +46,14 @@ struct lf_ctx {
         cudaStream_t stream = nullptr;
     };
     std::map<GraphKey, GraphEntry> graphs;
-    // end-to-end host pipeline: two sub-contexts (own scratch), two streams,
-    // two device staging arenas
-    lf_ctx* sub[2] = {nullptr, nullptr};
-    cudaStream_t pipe_stream[2] = {nullptr, nullptr};
-    DevBuf arena[2];
+    // end-to-end host pipeline: a compute sub-context (own scratch), three
+    // streams (copies in, compute, copies out), events chaining them, and
+    // three device staging arenas
+    static constexpr int NSLOT = 3;
+    lf_ctx* sub = nullptr;
+    cudaStream_t pipe_stream[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_in[NSLOT] = {}, ev_comp[NSLOT] = {}, ev_out[NSLOT] = {};
+    DevBuf arena[NSLOT];
 };
 
 namespace {
@@ -273,9 +276,13 @@ lf_status lf_create(const lf_geometry* geometry, const lf_params* params, lf_ctx
 void lf_destroy(lf_ctx* c) {
     if (!c) return;
     cudaDeviceSynchronize();
-    for (int i = 0; i < 2; ++i) {
-        if (c->sub[i]) lf_destroy(c->sub[i]);
+    if (c->sub) lf_destroy(c->sub);
+    for (int i = 0; i < 3; ++i)
         if (c->pipe_stream[i]) cudaStreamDestroy(c->pipe_stream[i]);
+    for (int i = 0; i < lf_ctx::NSLOT; ++i) {
+        if (c->ev_in[i]) cudaEventDestroy(c->ev_in[i]);
+        if (c->ev_comp[i]) cudaEventDestroy(c->ev_comp[i]);
+        if (c->ev_out[i]) cudaEventDestroy(c->ev_out[i]);
         if (c->arena[i].p) cudaFree(c->arena[i].p);
     }
     for (auto& kv : c->graphs)
@@ -507,14 +514,20 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
         return fail(c, LF_ERR_ARG, "offsets do not end at n_hits / n_tracks");
     if (hb->n_events == 0) return LF_OK;
     if (chunk_hits <= 0) chunk_hits = (int64_t)1 << 26;
+    constexpr int NS = lf_ctx::NSLOT;
     lf_status st;
-    Shape shs[2];
-    for (int i = 0; i < 2; ++i) {
-        if (!c->sub[i] && (st = lf_create(&c->g, &c->p, &c->sub[i])) != LF_OK)
-            return fail(c, st, "sub-context creation failed");
+    if (!c->sub && (st = lf_create(&c->g, &c->p, &c->sub)) != LF_OK) return fail(c, st, "sub-context creation failed");
+    lf_ctx* sc = c->sub;
+    for (int i = 0; i < 3; ++i)
         if (!c->pipe_stream[i]) LF_CUDA(c, cudaStreamCreateWithFlags(&c->pipe_stream[i], cudaStreamNonBlocking));
-        if ((st = resolve_shape(c->sub[i], tuning, shs[i])) != LF_OK) return fail(c, st, "%s", c->sub[i]->err);
+    for (int i = 0; i < NS; ++i) {
+        if (!c->ev_in[i]) LF_CUDA(c, cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming));
+        if (!c->ev_comp[i]) LF_CUDA(c, cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming));
+        if (!c->ev_out[i]) LF_CUDA(c, cudaEventCreateWithFlags(&c->ev_out[i], cudaEventDisableTiming));
     }
+    cudaStream_t s_in = c->pipe_stream[0], s_comp = c->pipe_stream[1], s_out = c->pipe_stream[2];
+    Shape sh;
+    if ((st = resolve_shape(sc, tuning, sh)) != LF_OK) return fail(c, st, "%s", sc->err);
     // chunk boundaries at event boundaries
     std::vector<int> cut{0};
     const int32_t* ro = hb->raw_offsets;
@@ -529,6 +542,13 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
         H = std::max(H, (size_t)(ro[cut[k + 1]] - ro[cut[k]]));
         E = std::max(E, (size_t)(cut[k + 1] - cut[k]));
         T = std::max(T, (size_t)(to[cut[k + 1]] - to[cut[k]]));
+    }
+    // the compute context's scratch at the largest chunk's size before any
+    // copy is queued (growing it later would synchronise the device)
+    {
+        lf_batch big{(int32_t)E, (int32_t)H, (int32_t)T, nullptr, nullptr, nullptr, nullptr, nullptr,
+                     nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        if ((st = prepare_batched(sc, &big, sh)) != LF_OK) return fail(c, st, "%s", sc->err);
     }
     // rebased offsets of every chunk, in one pinned block
     const size_t n_chunks = cut.size() - 1;
@@ -571,23 +591,27 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
     size_t o_oo = sz; sz += al(4 * (E + 1));
     size_t o_ot = sz; sz += al(4 * (T + 1));
     size_t o_no = sz; sz += al(4);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NS; ++i) {
         if ((st = ensure(c, c->arena[i], sz)) != LF_OK) {
             cudaFreeHost(pin);
             return st;
         }
     }
+    // three-stage pipeline over NS arena slots: chunk k's copies in (stream
+    // s_in) wait until the slot's previous chunk has left (its copies out),
+    // its compute (s_comp) waits for its copies in, its copies out (s_out)
+    // wait for its compute; so copies in of chunk k+1, compute of chunk k and
+    // copies out of chunk k-1 overlap
     lf_status rc = LF_OK;
     cudaError_t ce = cudaSuccess;
     for (size_t k = 0; k < n_chunks && rc == LF_OK && ce == cudaSuccess; ++k) {
-        const int slot = (int)(k & 1);
-        lf_ctx* sc = c->sub[slot];
-        cudaStream_t s = c->pipe_stream[slot];
+        const int slot = (int)(k % NS);
         char* A = (char*)c->arena[slot].p;
         const int e0 = cut[k], e1 = cut[k + 1];
         const int ne = e1 - e0, h0 = ro[e0], nh = ro[e1] - ro[e0], t0 = to[e0], nt = to[e1] - to[e0];
+        if (k >= (size_t)NS && (ce = cudaStreamWaitEvent(s_in, c->ev_out[slot], 0)) != cudaSuccess) break;
         auto cp = [&](size_t dst, const void* src, size_t bytes) {
-            if (ce == cudaSuccess && bytes) ce = cudaMemcpyAsync(A + dst, src, bytes, cudaMemcpyHostToDevice, s);
+            if (ce == cudaSuccess && bytes) ce = cudaMemcpyAsync(A + dst, src, bytes, cudaMemcpyHostToDevice, s_in);
         };
         cp(o_ro, pin + pin_off[k], 4 * (size_t)(ne + 1));
         cp(o_to, pin + pin_off[k] + ne + 1, 4 * (size_t)(ne + 1));
@@ -601,43 +625,43 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
         cp(o_st + 2 * 4 * T, hb->stx + t0, 4 * (size_t)nt);
         cp(o_st + 3 * 4 * T, hb->sty + t0, 4 * (size_t)nt);
         cp(o_st + 4 * 4 * T, hb->sqop + t0, 4 * (size_t)nt);
+        if (ce == cudaSuccess) ce = cudaEventRecord(c->ev_in[slot], s_in);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s_comp, c->ev_in[slot], 0);
         if (ce != cudaSuccess) break;
         lf_raw_hits raw{ne, nh, (const int32_t*)(A + o_ro), (const float*)(A + o_x), (const float*)(A + o_z),
                         (const float*)(A + o_d), (const float*)(A + o_w), (const uint8_t*)(A + o_pl)};
         lf_packed pk{(int32_t*)(A + o_ho), (float*)(A + o_px), (float*)(A + o_pz), (float*)(A + o_pd),
                      (float*)(A + o_pw), (uint8_t*)(A + o_pl2), (int32_t*)(A + o_pm)};
-        if ((rc = lf_pack_hits(sc, &raw, &pk, s)) != LF_OK) break;
+        if ((rc = lf_pack_hits(sc, &raw, &pk, s_comp)) != LF_OK) break;
         lf_batch bt{ne, nh, nt, pk.hit_offsets, pk.x, pk.z, pk.dxdy, pk.w, (const int32_t*)(A + o_to),
                     (const float*)(A + o_st), (const float*)(A + o_st + 4 * T), (const float*)(A + o_st + 8 * T),
                     (const float*)(A + o_st + 12 * T), (const float*)(A + o_st + 16 * T)};
         lf_output out{(uint8_t*)(A + o_fd), (uint8_t*)(A + o_nh), (int32_t*)(A + o_hi), (float*)(A + o_sv),
                       (float*)(A + o_q), (int32_t*)(A + o_oo), (int32_t*)(A + o_ot), (int32_t*)(A + o_no)};
-        if ((rc = batched_direct(sc, &bt, &out, shs[slot], s)) != LF_OK) break;
-        ce = launch_hits_to_raw(out.found, out.hit_idx, pk.perm, nt, h0, s);
+        if ((rc = batched_direct(sc, &bt, &out, sh, s_comp)) != LF_OK) break;
+        ce = launch_hits_to_raw(out.found, out.hit_idx, pk.perm, nt, h0, s_comp);
+        if (ce == cudaSuccess) ce = cudaEventRecord(c->ev_comp[slot], s_comp);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s_out, c->ev_comp[slot], 0);
         auto back = [&](void* dst, size_t src, size_t bytes) {
-            if (ce == cudaSuccess && bytes && dst) ce = cudaMemcpyAsync(dst, A + src, bytes, cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess && bytes && dst) ce = cudaMemcpyAsync(dst, A + src, bytes, cudaMemcpyDeviceToHost, s_out);
         };
         back(ho->found + t0, o_fd, (size_t)nt);
         back(ho->nhits + t0, o_nh, (size_t)nt);
         back(ho->hit_idx + (size_t)t0 * NL, o_hi, 4 * NL * (size_t)nt);
         back(ho->state + (size_t)t0 * 6, o_sv, 4 * 6 * (size_t)nt);
         back(ho->quality + t0, o_q, 4 * (size_t)nt);
+        if (ce == cudaSuccess) ce = cudaEventRecord(c->ev_out[slot], s_out);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {
         cudaError_t e2 = cudaStreamSynchronize(c->pipe_stream[i]);
         if (ce == cudaSuccess) ce = e2;
     }
     cudaFreeHost(pin);
-    if (rc != LF_OK) return fail(c, rc, "chunk failed: %s", lf_last_error(c->sub[0])[0] ? lf_last_error(c->sub[0]) : lf_last_error(c->sub[1]));
+    if (rc != LF_OK) return fail(c, rc, "chunk failed: %s", lf_last_error(sc));
     if (ce != cudaSuccess) return fail(c, LF_ERR_CUDA, "host pipeline: %s", cudaGetErrorString(ce));
-    int flags = 0;
-    for (int i = 0; i < 2; ++i) {
-        int32_t f = 0;
-        lf_status s2 = lf_sync_status(c->sub[i], c->pipe_stream[i], &f);
-        flags |= f;
-        if (s2 != LF_OK && rc == LF_OK) rc = s2;
-    }
-    if (rc != LF_OK) return fail(c, rc, "device status flags 0x%x", flags);
+    int32_t flags = 0;
+    lf_status s2 = lf_sync_status(sc, s_comp, &flags);
+    if (s2 != LF_OK) return fail(c, s2, "device status flags 0x%x", flags);
     return LF_OK;
 }
 

@@ -1,38 +1,42 @@
 // Hit packing for sm_103a: per event, bucket the raw hits by (zone, layer),
 // sort every bucket by x (ties by raw index) and write the SoA.
 //
-// Two kernels.  k_pack_event (persistent): a block takes one event at a
-// time from a device work queue and sorts it in shared memory:
-//   count     the plane codes of the event are counted per warp (peers by
-//             __match_any_sync, warp-private counters); an exclusive scan of
-//             the totals gives the bucket offsets, written to hit_offsets.
-//   chunk     consecutive buckets are grouped into chunks of at most CHUNK
-//             hits (one chunk for all but the largest events); per chunk:
-//   scatter   the event's hits of the chunk's buckets are placed, bucket
-//             by bucket, into shared memory as (x with -0 -> +0, raw index
-//             inside the event): every warp owns a fixed share of the hits
-//             and, from the counts, its own cursor per bucket (no shared
-//             atomics); a warp per bucket then reduces the bucket's x range;
-//   bin sort  every bucket is split into as many equal x bins as it has hits
-//             (a monotone function of x), and the bins of all buckets of the
-//             chunk are counted, scanned and filled by the whole block at
-//             once; each bin is then ordered by (x, raw index) with an
-//             insertion sort, so the result is the exact (x, raw index) order
-//             whatever the data and whatever the order of the scatter;
-//   write     the chunk's output range is contiguous: x, layer and perm are
-//             written coalesced from shared memory.
+// One persistent kernel, k_pack_event: a block of 1024 threads takes one
+// event at a time from a device work queue and sorts it as a distribution
+// sort whose bins are ordered like the result:
+//   range    the event's x range (one pass over x);
+//   bins     every bucket gets nbb equal x bins over that range (nbb a power
+//            of two between 16 and 512, about one hit per bin); the global
+//            bin of a hit is bucket * nbb + bin, a monotone function of
+//            (bucket, x), so bin order is already the bucket order and the x
+//            order up to the inside of a bin;
+//   count    one pass over (plane, x) counts the hits per bin (shared
+//            atomics); an exclusive scan gives every bin's start, and the
+//            bucket offsets are the starts of each bucket's first bin;
+//   place    one pass over the raw hits puts each at its bin's next free
+//            position;
+//   order    each bin is ordered by (x, raw index) with an insertion sort, so
+//            the result is the exact (bucket, x, raw index) order whatever
+//            the data (a skewed x distribution costs time, never exactness);
+//   write    x, layer and perm leave coalesced.
+// An event of at most CHUNK hits is placed straight into shared memory; its
+// z, dxdy and w are then read coalesced from the raw arrays (prefetched into
+// L2 when the event was taken) and transposed through shared memory with an
+// inverse map (raw index -> position), one array at a time.  A larger event
+// is sorted in chunks of consecutive bins of at most CHUNK hits: per chunk a
+// pass over the raw hits places the chunk's hits in shared memory, and after
+// the ordering a second pass reads the payload coalesced and stores each of
+// the chunk's hits' z, dxdy and w at its position.  (Staging a larger event
+// once through its output range instead costs five scattered 4-byte stores
+// per hit, which measured slower than the repeated coalesced passes.)
 // While an event is processed, the block has already taken its next event
 // from the queue and prefetched that event's plane codes and x into L2.
-// k_pack_payload then walks the packed positions in order (coalesced
-// writes) and gathers z, dxdy and w through perm: scattered 4-byte reads
-// want many loads in flight, i.e. a kernel at full occupancy rather than
-// one large block per SM.
-// A bucket above CHUNK hits cannot be sorted: it is flagged (status bit
-// 0x1), its perm entries are set to -1 and its other outputs are not
-// meaningful; a plane code >= 24 is flagged (0x2) and counted in the last
-// bucket.
+// A bucket above LF_MAX_BUCKET hits is not sorted: it is flagged (status bit
+// 0x1), its perm entries are set to -1 and its other outputs to 0; a plane
+// code >= 24 is flagged (0x2) and counted in the last bucket.
 #include <cstdint>
 
+#include "lf.h"
 #include "lf_internal.h"
 
 namespace lfk {
@@ -42,39 +46,29 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int PACK_THREADS = 1024;
 constexpr int PACK_WARPS = PACK_THREADS / 32;
-constexpr int CHUNK = BLOCK_SORT_MAX;  // hits sorted together in shared memory
-constexpr int UNROLL = 4;              // hits per thread with loads in flight together
+constexpr int NBB_MIN = 16;                 // x bins per bucket, fewest
+constexpr int NBB_MAX = 512;                // x bins per bucket, most
+constexpr int NBIN_MAX = NB * NBB_MAX;      // bins of an event, most
+constexpr int CHUNK = 20480;                // hits sorted together in shared memory
+constexpr int UNROLL = 4;                   // hits per thread with loads in flight together
+constexpr int ID_BITS = 27;                 // raw index inside the event; the bucket sits above
+constexpr uint32_t ID_MASK = (1u << ID_BITS) - 1u;
+static_assert(CHUNK >= BLOCK_SORT_MAX, "a sortable bucket must fit one chunk");
+static_assert(CHUNK <= 2 * (NBIN_MAX + 4), "the inverse map of one chunk fits the bins' area");
 
-// shared memory per element: x, raw index, bin counter (16-bit halves of
-// 32-bit words), slot inside the bin, element at each sorted position
-constexpr size_t AREA_BYTES = (size_t)CHUNK * (4 + 4 + 2 + 2 + 2);
+// shared memory: bin counters / starts (NBIN_MAX + 1, padded), then x and
+// (bucket << ID_BITS | raw index) of a chunk's hits in bin order
+constexpr size_t BINS_BYTES = 4 * (size_t)(NBIN_MAX + 4);
+constexpr size_t AREA_BYTES = BINS_BYTES + (size_t)CHUNK * 8;
 
-struct Area {
-    float* xs;          // x of element k
-    uint32_t* id;       // raw index of element k, relative to the event
-    uint32_t* bins2;    // bin counters / starts, two 16-bit values per word
-    uint16_t* slot;     // slot of element k inside its bin
-    uint16_t* order;    // element at sorted position j
+struct EvShared {
+    unsigned red_mn[PACK_WARPS], red_mx[PACK_WARPS];
+    int warp_tot[PACK_WARPS];
+    int boff[NB + 1];        // bucket offsets inside the event
+    int event, next;
+    unsigned flagged;        // buckets above LF_MAX_BUCKET
+    int b1;                  // end bin of the current chunk
 };
-
-__device__ __forceinline__ Area area_at(char* p) {
-    Area a;
-    a.xs = reinterpret_cast<float*>(p);
-    a.id = reinterpret_cast<uint32_t*>(p + (size_t)CHUNK * 4);
-    a.bins2 = reinterpret_cast<uint32_t*>(p + (size_t)CHUNK * 8);
-    a.slot = reinterpret_cast<uint16_t*>(p + (size_t)CHUNK * 10);
-    a.order = reinterpret_cast<uint16_t*>(p + (size_t)CHUNK * 12);
-    return a;
-}
-
-__device__ __forceinline__ int wscan_incl(int v, int lane) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int u = __shfl_up_sync(FULL, v, o);
-        if (lane >= o) v += u;
-    }
-    return v;
-}
 
 // x as an unsigned integer with the same order (-0 already turned into +0)
 __device__ __forceinline__ unsigned ordered(float x) {
@@ -85,32 +79,22 @@ __device__ __forceinline__ float unordered(unsigned u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
-__device__ __forceinline__ int bin_of(float x, float lo, float scale, int nb) {
-    float f = (x - lo) * scale;   // monotone in x
+// x bin inside a bucket: monotone non-decreasing in x
+__device__ __forceinline__ int bin_of(float x, float lo, float scale, int nbb) {
+    float f = (x - lo) * scale;
     if (!(f > 0.0f)) return 0;
-    if (!(f < (float)nb)) return nb - 1;
+    if (!(f < (float)nbb)) return nbb - 1;
     return (int)f;
 }
 
-// 16-bit counter i of the packed bin array
-__device__ __forceinline__ unsigned bin_add(uint32_t* bins2, int i) {
-    unsigned old = atomicAdd(&bins2[i >> 1], (i & 1) ? 0x10000u : 1u);
-    return (i & 1) ? (old >> 16) : (old & 0xffffu);
+__device__ __forceinline__ int wscan_incl(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
 }
-__device__ __forceinline__ unsigned bin_get(const uint32_t* bins2, int i) {
-    unsigned v = bins2[i >> 1];
-    return (i & 1) ? (v >> 16) : (v & 0xffffu);
-}
-
-struct EvShared {
-    uint16_t wcur[PACK_WARPS][NB];   // per-warp scatter cursor inside each bucket
-    int cnt[NB];                // bucket sizes
-    int off[NB + 1];            // bucket offsets inside the event
-    int coff[NB + 1];           // bucket offsets inside the chunk
-    float blo[NB], bscale[NB];  // bin mapping of each bucket
-    int warp_tot[PACK_WARPS];
-    int event, next;
-};
 
 // L2 prefetch of bytes [p, p + bytes): one instruction per 128-byte line,
 // each line holding at least one byte of the range
@@ -123,26 +107,44 @@ __device__ __forceinline__ void prefetch_range(const void* p, size_t bytes, int 
         asm volatile("prefetch.global.L2 [%0];" ::"l"(b0 + (uintptr_t)q * 128));
 }
 
-// bucket of chunk element k: the last bucket q in [qa, ql] with coff[q] <= k
-// (an empty bucket shares its offset with the next one, so the last wins)
-__device__ __forceinline__ int bucket_of(const EvShared& sh, int qa, int ql, int k) {
-    int lo = qa, hi = ql;
-#pragma unroll
-    for (int it = 0; it < 5; ++it) {   // 2^5 >= 24 buckets
-        const int mid = (lo + hi + 1) >> 1;
-        if (lo < hi) {
-            if (sh.coff[mid] <= k) lo = mid; else hi = mid - 1;
-        }
+// plane code of a raw hit as a bucket (codes >= 24 go to the last bucket)
+__device__ __forceinline__ int bucket_code(int p, bool& bad) {
+    if (p >= NB) {
+        bad = true;
+        return NB - 1;
     }
-    return lo;
+    return p;
 }
 
+// insertion sort of the bin [s, e) by (x, key) (keys of one bin share their
+// bucket bits, so key order is raw-index order)
+__device__ __forceinline__ void sort_bin2(float* xs, uint32_t* ks, int s, int e) {
+    for (int i = s + 1; i < e; ++i) {
+        const float xv = xs[i];
+        const uint32_t kv = ks[i];
+        int j = i - 1;
+        while (j >= s) {
+            const float xj = xs[j];
+            const uint32_t kj = ks[j];
+            if (!(xv < xj || (xv == xj && kv < kj))) break;
+            xs[j + 1] = xj;
+            ks[j + 1] = kj;
+            --j;
+        }
+        xs[j + 1] = xv;
+        ks[j + 1] = kv;
+    }
+}
 __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
-    const int* __restrict__ raw_offsets, const float* __restrict__ x, const uint8_t* __restrict__ plane,
-    int n_events, int* hit_offsets, float* ox, uint8_t* ol, int* perm, int* cursor, int* status) {
+    const int* __restrict__ raw_offsets, const float* __restrict__ x, const float* __restrict__ z,
+    const float* __restrict__ dxdy, const float* __restrict__ w, const uint8_t* __restrict__ plane, int n_events,
+    int* hit_offsets, float* ox, float* oz, float* od, float* ow, uint8_t* ol, int* perm, int* cursor,
+    int* status) {
     extern __shared__ __align__(16) char smem[];
     __shared__ EvShared sh;
-    const Area a = area_at(smem);
+    int* bins = reinterpret_cast<int*>(smem);
+    float* xs = reinterpret_cast<float*>(smem + BINS_BYTES);
+    uint32_t* ks = reinterpret_cast<uint32_t*>(smem + BINS_BYTES + (size_t)CHUNK * 4);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (blockIdx.x == 0 && tid == 0) hit_offsets[(size_t)n_events * NB] = raw_offsets[n_events];
     if (tid == 0) sh.next = atomicAdd(cursor, 1);
@@ -151,13 +153,19 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
         if (tid == 0) {
             sh.event = sh.next;
             sh.next = sh.event < n_events ? atomicAdd(cursor, 1) : n_events;
+            sh.flagged = 0u;
         }
         __syncthreads();
         const int e = sh.event;
         if (e >= n_events) break;
         const int rb = raw_offsets[e], n = raw_offsets[e + 1] - rb;
-        // the next event's raw arrays go to L2 while this one is processed
-        // (addresses inside the next event's range only)
+        // this event's payload and the next event's keys go to L2 while the
+        // event is sorted (addresses inside the events' ranges only)
+        if (n > 0) {
+            prefetch_range(z + rb, (size_t)n * 4, tid);
+            prefetch_range(dxdy + rb, (size_t)n * 4, tid);
+            prefetch_range(w + rb, (size_t)n * 4, tid);
+        }
         if (sh.next < n_events) {
             const int nb0 = raw_offsets[sh.next], nn = raw_offsets[sh.next + 1] - nb0;
             if (nn > 0) {
@@ -165,80 +173,126 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
                 prefetch_range(x + nb0, (size_t)nn * 4, tid);
             }
         }
+        if (n == 0) {
+            if (tid < NB) hit_offsets[(size_t)e * NB + tid] = rb;
+            continue;
+        }
+        if ((unsigned)n > ID_MASK) {
+            // beyond the index field: nothing is sorted, every bucket flagged
+            if (tid < NB) hit_offsets[(size_t)e * NB + tid] = rb;
+            if (tid == 0) atomicOr(status, LF_FLAG_BUCKET_OVERFLOW);
+            for (int i = tid; i < n; i += PACK_THREADS) perm[(size_t)rb + i] = -1;
+            continue;
+        }
 
-        // count into warp-private counters (in the element area, unused until
-        // the scatter); the leader of each group of equal codes adds its size
-        int* wcnt = reinterpret_cast<int*>(smem) + warp * NB;
-        if (lane < NB) wcnt[lane] = 0;
-        __syncwarp();
+        // x range of the event
+        unsigned mn = 0xffffffffu, mx = 0u;
+        for (int base = 0; base < n; base += PACK_THREADS * UNROLL) {
+            float xu[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int i = base + u * PACK_THREADS + tid;
+                xu[u] = i < n ? x[rb + i] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                if (base + u * PACK_THREADS + tid < n) {
+                    const unsigned ov = ordered(xu[u] + 0.0f);
+                    mn = min(mn, ov);
+                    mx = max(mx, ov);
+                }
+            }
+        }
+        mn = __reduce_min_sync(FULL, mn);
+        mx = __reduce_max_sync(FULL, mx);
+        if (lane == 0) {
+            sh.red_mn[warp] = mn;
+            sh.red_mx[warp] = mx;
+        }
+        // bins per bucket: a power of two near n / 24
+        int nbb = NBB_MIN;
+        while (nbb < NBB_MAX && nbb * NB < n) nbb <<= 1;
+        const int nbin = nbb * NB;
+        for (int b = tid; b <= nbin; b += PACK_THREADS) bins[b] = 0;
+        __syncthreads();
+        mn = sh.red_mn[lane];
+        mx = sh.red_mx[lane];
+        mn = __reduce_min_sync(FULL, mn);
+        mx = __reduce_max_sync(FULL, mx);
+        float lo = 0.0f, scale = 0.0f;
+        if (n > 0) {
+            lo = unordered(mn);
+            const float hi = unordered(mx);
+            scale = hi > lo ? (float)nbb / (hi - lo) : 0.0f;
+        }
+
+        // count per bin
         bool bad = false;
-        for (int base = warp * 32; base < n; base += PACK_THREADS * UNROLL) {
+        for (int base = 0; base < n; base += PACK_THREADS * UNROLL) {
             int pu[UNROLL];
+            float xu[UNROLL];
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
-                const int i = base + u * PACK_THREADS + lane;
-                pu[u] = i < n ? (int)plane[rb + i] : -1;
+                const int i = base + u * PACK_THREADS + tid;
+                pu[u] = -1;
+                xu[u] = 0.0f;
+                if (i < n) {
+                    pu[u] = plane[rb + i];
+                    xu[u] = x[rb + i];
+                }
             }
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
-                int p = pu[u];
-                if (p >= NB) {
-                    bad = true;
-                    p = NB - 1;
-                }
-                const unsigned peers = __match_any_sync(FULL, p);
-                if (p >= 0 && lane == __ffs(peers) - 1) wcnt[p] += __popc(peers);
-                __syncwarp();
+                if (pu[u] < 0) continue;
+                const int q = bucket_code(pu[u], bad);
+                atomicAdd(&bins[q * nbb + bin_of(xu[u] + 0.0f, lo, scale, nbb)], 1);
             }
         }
-        if (bad) atomicOr(status, 0x2);
-        wcnt = reinterpret_cast<int*>(smem);
+        if (bad) atomicOr(status, LF_FLAG_PLANE_RANGE);
         __syncthreads();
-        if (tid < 32) {
-            // bucket totals; each warp's cursor starts after the earlier warps' hits
-            int c = 0;
-            if (lane < NB)
-                for (int q = 0; q < PACK_WARPS; ++q) {
-                    sh.wcur[q][lane] = (uint16_t)c;
-                    c += wcnt[q * NB + lane];
-                }
-            const int inc = wscan_incl(c, lane);
-            if (lane < NB) {
-                sh.cnt[lane] = c;
-                sh.off[lane] = inc - c;
-                hit_offsets[(size_t)e * NB + lane] = rb + inc - c;
-                if (c > CHUNK) atomicOr(status, 0x1);
+
+        // exclusive scan of the nbin counters: thread tid owns a run of per
+        {
+            const int per = (nbin + PACK_THREADS - 1) / PACK_THREADS;
+            const int s0 = min(tid * per, nbin), s1 = min(s0 + per, nbin);
+            int sum = 0;
+            for (int b = s0; b < s1; ++b) sum += bins[b];
+            const int inc = wscan_incl(sum, lane);
+            if (lane == 31) sh.warp_tot[warp] = inc;
+            __syncthreads();
+            int wt = sh.warp_tot[lane];
+            const int winc = wscan_incl(wt, lane);
+            int excl = inc - sum + __shfl_sync(FULL, winc - wt, warp);
+            for (int b = s0; b < s1; ++b) {
+                const int c = bins[b];
+                bins[b] = excl;
+                excl += c;
             }
-            if (lane == NB - 1) sh.off[NB] = inc;
+            if (tid == 0) bins[nbin] = n;
+        }
+        __syncthreads();
+        if (tid <= NB) {
+            const int s = bins[tid * nbb];
+            sh.boff[tid] = s;
+            if (tid < NB) {
+                hit_offsets[(size_t)e * NB + tid] = rb + s;
+                if (bins[(tid + 1) * nbb] - s > BLOCK_SORT_MAX) {
+                    atomicOr(&sh.flagged, 1u << tid);
+                    atomicOr(status, LF_FLAG_BUCKET_OVERFLOW);
+                }
+            }
         }
         __syncthreads();
 
-        // chunks of consecutive buckets (every thread takes the same decisions)
-        int qa = 0;
-        while (qa < NB) {
-            int qb = qa, tot = 0;
-            while (qb < NB && tot + sh.cnt[qb] <= CHUNK) tot += sh.cnt[qb++];
-            if (qb == qa) {   // a bucket above CHUNK hits: flagged above, not sorted
-                const size_t o0 = (size_t)rb + sh.off[qa];
-                for (int j = tid; j < sh.cnt[qa]; j += PACK_THREADS) perm[o0 + j] = -1;
-                ++qa;
-                continue;
-            }
-            if (tot == 0) {
-                qa = qb;
-                continue;
-            }
-            const int ql = qb - 1;
-            // scatter the chunk's hits, bucket by bucket; a warp visits the
-            // same hits as in the count and advances its own cursors
-            if (tid < NB) sh.coff[tid] = (tid >= qa && tid < qb) ? sh.off[tid] - sh.off[qa] : 0;
-            __syncthreads();
-            for (int base = 0; base < n; base += PACK_THREADS * UNROLL) {
+        const unsigned flagged = sh.flagged;
+        if (n <= CHUNK && flagged == 0u) {
+            // ---- the whole event in one chunk: placed straight into shared memory
+            for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
                 int pu[UNROLL];
                 float xu[UNROLL];
 #pragma unroll
                 for (int u = 0; u < UNROLL; ++u) {
-                    const int i = base + u * PACK_THREADS + tid;
+                    const int i = ib + u * PACK_THREADS + tid;
                     pu[u] = -1;
                     xu[u] = 0.0f;
                     if (i < n) {
@@ -248,168 +302,179 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
                 }
 #pragma unroll
                 for (int u = 0; u < UNROLL; ++u) {
-                const int i = base + u * PACK_THREADS + tid;
-                int p = pu[u];
-                if (p >= NB) p = NB - 1;
-                if (p < qa || p >= qb) p = -1;
-                const unsigned peers = __match_any_sync(FULL, p);
-                const int cur = p >= 0 ? (int)sh.wcur[warp][p] : 0;
-                __syncwarp();
-                if (p >= 0) {
-                    const int rank = __popc(peers & ((1u << lane) - 1u));
-                    if (rank == 0) sh.wcur[warp][p] = (uint16_t)(cur + __popc(peers));
-                    const int k = sh.coff[p] + cur + rank;
-                    a.xs[k] = xu[u] + 0.0f;
-                    a.id[k] = (uint32_t)i;
-                }
-                __syncwarp();
+                    if (pu[u] < 0) continue;
+                    const int i = ib + u * PACK_THREADS + tid;
+                    bool bb = false;
+                    const int q = bucket_code(pu[u], bb);
+                    const float xv = xu[u] + 0.0f;
+                    const int pos = atomicAdd(&bins[q * nbb + bin_of(xv, lo, scale, nbb)], 1);
+                    xs[pos] = xv;
+                    ks[pos] = ((uint32_t)q << ID_BITS) | (uint32_t)i;
                 }
             }
-            for (int q = tid; q < (tot + 1) / 2; q += PACK_THREADS) a.bins2[q] = 0u;
             __syncthreads();
-            // x range of bucket q, reduced by warp q - qa (buckets of a chunk <= 24 < 32 warps)
-            {
-                const int q = qa + warp;
-                if (q < qb) {
-                    const int m = sh.cnt[q], k0 = sh.coff[q];
-                    unsigned mn = 0xffffffffu, mx = 0u;
-                    for (int k = lane; k < m; k += 32) {
-                        const unsigned ov = ordered(a.xs[k0 + k]);
-                        mn = min(mn, ov);
-                        mx = max(mx, ov);
+            // bins[b] now holds the end of bin b; order each bin by (x, raw
+            // index) (the bucket bits are equal inside a bin)
+            for (int b = tid; b < nbin; b += PACK_THREADS)
+                sort_bin2(xs, ks, b == 0 ? 0 : bins[b - 1], bins[b]);
+            __syncthreads();
+            // x, layer and perm straight from shared memory, and the inverse map
+            // (raw index -> position) over the bins' area, free now
+            const size_t o0 = (size_t)rb;
+            uint16_t* inv = reinterpret_cast<uint16_t*>(bins);
+            for (int j = tid; j < n; j += PACK_THREADS) {
+                const uint32_t k = ks[j];
+                ox[o0 + j] = xs[j];
+                ol[o0 + j] = (uint8_t)((k >> ID_BITS) % NL);
+                perm[o0 + j] = rb + (int)(k & ID_MASK);
+                inv[k & ID_MASK] = (uint16_t)j;
+            }
+            __syncthreads();
+            // z, dxdy and w: coalesced reads of the raw arrays, transposed
+            // through shared memory (x's area), coalesced writes
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float* src = a == 0 ? z : (a == 1 ? dxdy : w);
+                float* dst = a == 0 ? oz : (a == 1 ? od : ow);
+                for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
+                    float v[UNROLL];
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u) {
+                        const int i = ib + u * PACK_THREADS + tid;
+                        v[u] = i < n ? src[rb + i] : 0.0f;
                     }
-                    mn = __reduce_min_sync(FULL, mn);
-                    mx = __reduce_max_sync(FULL, mx);
-                    if (lane == 0) {
-                        float lo = 0.0f, scale = 0.0f;
-                        if (m > 0) {
-                            lo = unordered(mn);
-                            const float hi = unordered(mx);
-                            scale = hi > lo ? (float)m / (hi - lo) : 0.0f;
-                        }
-                        sh.blo[q] = lo;
-                        sh.bscale[q] = scale;
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u) {
+                        const int i = ib + u * PACK_THREADS + tid;
+                        if (i < n) xs[inv[i]] = v[u];
                     }
                 }
-            }
-            __syncthreads();
-
-            // count: bin of element k = bucket offset + bin inside the bucket
-            for (int k = tid; k < tot; k += PACK_THREADS) {
-                const int q = bucket_of(sh, qa, ql, k);
-                const int bn = sh.coff[q] + bin_of(a.xs[k], sh.blo[q], sh.bscale[q], sh.cnt[q]);
-                a.slot[k] = (uint16_t)bin_add(a.bins2, bn);
-            }
-            __syncthreads();
-            // exclusive scan of the tot counters; every thread's run starts
-            // on an even counter, so each 32-bit word has a single writer
-            {
-                const int per = 2 * ((tot + 2 * PACK_THREADS - 1) / (2 * PACK_THREADS));
-                const int s0 = min(tid * per, tot), s1 = min(s0 + per, tot);
-                int sum = 0;
-                for (int i = s0; i < s1; ++i) sum += (int)bin_get(a.bins2, i);
-                const int inc = wscan_incl(sum, lane);
-                if (lane == 31) sh.warp_tot[warp] = inc;
                 __syncthreads();
-                int excl = inc - sum;
-                for (int q = 0; q < warp; ++q) excl += sh.warp_tot[q];
-                for (int i = s0; i < s1; i += 2) {
-                    const unsigned v = a.bins2[i >> 1];
-                    const unsigned c0 = v & 0xffffu, c1 = v >> 16;
-                    const unsigned st0 = (unsigned)excl, st1 = st0 + c0;
-                    a.bins2[i >> 1] = st0 | (st1 << 16);
-                    excl += (int)(c0 + c1);
+                for (int j = tid; j < n; j += PACK_THREADS) dst[o0 + j] = xs[j];
+                __syncthreads();
+            }
+            continue;
+        }
+
+        // ---- a larger event (or one with a flagged bucket): chunks of
+        // consecutive bins of at most CHUNK hits; per chunk one pass over the
+        // raw hits places the chunk's hits in shared memory, and after the
+        // ordering and the x, layer and perm writes, a second pass reads the
+        // payload coalesced and stores each hit's z, dxdy and w at its position
+        int b0 = 0;
+        while (b0 < nbin) {
+            const int q0 = b0 / nbb;
+            if ((flagged >> q0) & 1u) {   // b0 is the bucket's first bin
+                const int o0 = sh.boff[q0], o1 = sh.boff[q0 + 1];
+                for (int j = o0 + tid; j < o1; j += PACK_THREADS) {
+                    const size_t o = (size_t)rb + j;
+                    perm[o] = -1;
+                    ox[o] = 0.0f;
+                    oz[o] = 0.0f;
+                    od[o] = 0.0f;
+                    ow[o] = 0.0f;
+                    ol[o] = (uint8_t)(q0 % NL);
                 }
+                b0 = (q0 + 1) * nbb;
+                continue;
+            }
+            const int base = bins[b0];
+            if (tid == 0) {
+                // the chunk stops before the next flagged bucket
+                int limit = nbin;
+                const unsigned later = flagged & ~((2u << q0) - 1u);
+                if (later) limit = (__ffs(later) - 1) * nbb;
+                // largest b1 in (b0, limit] with bins[b1] - base <= CHUNK (bins
+                // past b0 still hold their starts, monotone in b; a single bin
+                // of an unflagged bucket always fits)
+                int l = b0 + 1, h = limit;
+                while (l < h) {
+                    const int m = (l + h + 1) >> 1;
+                    if (bins[m] - base <= CHUNK) l = m; else h = m - 1;
+                }
+                sh.b1 = l;
             }
             __syncthreads();
-            // placement
-            for (int k = tid; k < tot; k += PACK_THREADS) {
-                const int q = bucket_of(sh, qa, ql, k);
-                const int bn = sh.coff[q] + bin_of(a.xs[k], sh.blo[q], sh.bscale[q], sh.cnt[q]);
-                a.order[bin_get(a.bins2, bn) + a.slot[k]] = (uint16_t)k;
-            }
-            __syncthreads();
-            // order each bin by (x, raw index); bin b ends where b + 1 starts
-            for (int bn = tid; bn < tot; bn += PACK_THREADS) {
-                const int s = (int)bin_get(a.bins2, bn), en = bn + 1 < tot ? (int)bin_get(a.bins2, bn + 1) : tot;
-                for (int i = s + 1; i < en; ++i) {
-                    const int pv = a.order[i];
-                    const float xv = a.xs[pv];
-                    const uint32_t iv = a.id[pv];
-                    int j = i - 1;
-                    while (j >= s) {
-                        const int pj = a.order[j];
-                        const float xj = a.xs[pj];
-                        if (!(xv < xj || (xv == xj && iv < a.id[pj]))) break;
-                        a.order[j + 1] = (uint16_t)pj;
-                        --j;
+            const int b1 = sh.b1;
+            const int tot = bins[b1] - base;
+            __syncthreads();   // every thread has read bins[b0], bins[b1]
+            for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
+                int pu[UNROLL];
+                float xu[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const int i = ib + u * PACK_THREADS + tid;
+                    pu[u] = -1;
+                    xu[u] = 0.0f;
+                    if (i < n) {
+                        pu[u] = plane[rb + i];
+                        xu[u] = x[rb + i];
                     }
-                    a.order[j + 1] = (uint16_t)pv;
+                }
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    if (pu[u] < 0) continue;
+                    const int i = ib + u * PACK_THREADS + tid;
+                    bool bb = false;
+                    const int q = bucket_code(pu[u], bb);
+                    const float xv = xu[u] + 0.0f;
+                    const int b = q * nbb + bin_of(xv, lo, scale, nbb);
+                    if (b >= b0 && b < b1) {
+                        const int pos = atomicAdd(&bins[b], 1) - base;
+                        xs[pos] = xv;
+                        ks[pos] = ((uint32_t)q << ID_BITS) | (uint32_t)i;
+                    }
                 }
             }
             __syncthreads();
-            // the chunk's output range is contiguous
-            {
-                const size_t o0 = (size_t)rb + sh.off[qa];
-#pragma unroll 4
-                for (int j = tid; j < tot; j += PACK_THREADS) {
-                    const int q = bucket_of(sh, qa, ql, j);
-                    const int k = a.order[j];
-                    const size_t o = o0 + j;
-                    ox[o] = a.xs[k];
-                    ol[o] = (uint8_t)(q % NL);
-                    perm[o] = rb + (int)a.id[k];
+            // bins[b] now holds the end of bin b for b in [b0, b1)
+            for (int b = b0 + tid; b < b1; b += PACK_THREADS)
+                sort_bin2(xs, ks, (b == b0 ? base : bins[b - 1]) - base, bins[b] - base);
+            __syncthreads();
+            const size_t o0 = (size_t)rb + base;
+            for (int j = tid; j < tot; j += PACK_THREADS) {
+                const uint32_t k = ks[j];
+                ox[o0 + j] = xs[j];
+                ol[o0 + j] = (uint8_t)((k >> ID_BITS) % NL);
+                perm[o0 + j] = rb + (int)(k & ID_MASK);
+            }
+            for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
+                int pu[UNROLL];
+                float xu[UNROLL], zu[UNROLL], du[UNROLL], wu[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const int i = ib + u * PACK_THREADS + tid;
+                    pu[u] = -1;
+                    xu[u] = zu[u] = du[u] = wu[u] = 0.0f;
+                    if (i < n) {
+                        pu[u] = plane[rb + i];
+                        xu[u] = x[rb + i];
+                        zu[u] = z[rb + i];
+                        du[u] = dxdy[rb + i];
+                        wu[u] = w[rb + i];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    if (pu[u] < 0) continue;
+                    const int i = ib + u * PACK_THREADS + tid;
+                    bool bb = false;
+                    const int q = bucket_code(pu[u], bb);
+                    const int b = q * nbb + bin_of(xu[u] + 0.0f, lo, scale, nbb);
+                    if (b < b0 || b >= b1) continue;
+                    const uint32_t key = ((uint32_t)q << ID_BITS) | (uint32_t)i;
+                    const int en = bins[b] - base;
+                    int j = (b == b0 ? base : bins[b - 1]) - base;
+                    while (j < en && ks[j] != key) ++j;
+                    if (j < en) {
+                        oz[o0 + j] = zu[u];
+                        od[o0 + j] = du[u];
+                        ow[o0 + j] = wu[u];
+                    }
                 }
             }
             __syncthreads();
-            qa = qb;
-        }
-    }
-}
-
-// z, dxdy and w in packed order: position o takes raw hit perm[o].  Blocks
-// take tiles of consecutive positions from a work queue, so the tiles in
-// flight stay a narrow window of events whose raw lines L2 reuses (a grid
-// stride lets warps drift apart over the batch and loses that reuse).
-constexpr int PAYLOAD_THREADS = 256;
-constexpr int PAYLOAD_PER_THREAD = 8;
-constexpr int PAYLOAD_TILE = PAYLOAD_THREADS * PAYLOAD_PER_THREAD;
-
-__global__ void __launch_bounds__(PAYLOAD_THREADS) k_pack_payload(
-    const float* __restrict__ z, const float* __restrict__ dxdy, const float* __restrict__ w,
-    const int* __restrict__ perm, int n_hits, float* __restrict__ oz, float* __restrict__ od,
-    float* __restrict__ ow, int* cursor) {
-    __shared__ int s_tile;
-    const int n_tiles = (n_hits + PAYLOAD_TILE - 1) / PAYLOAD_TILE;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(cursor, 1);
-        __syncthreads();
-        const int tile = s_tile;
-        __syncthreads();
-        if (tile >= n_tiles) break;
-        const int o0 = tile * PAYLOAD_TILE + threadIdx.x;
-        int r[PAYLOAD_PER_THREAD];
-#pragma unroll
-        for (int u = 0; u < PAYLOAD_PER_THREAD; ++u) {
-            const int o = o0 + u * PAYLOAD_THREADS;
-            r[u] = o < n_hits ? perm[o] : -1;
-        }
-        float vz[PAYLOAD_PER_THREAD], vd[PAYLOAD_PER_THREAD], vw[PAYLOAD_PER_THREAD];
-#pragma unroll
-        for (int u = 0; u < PAYLOAD_PER_THREAD; ++u) {
-            // r < 0: past the end, or a bucket the pack could not sort
-            vz[u] = r[u] >= 0 ? __ldg(z + r[u]) : 0.0f;
-            vd[u] = r[u] >= 0 ? __ldg(dxdy + r[u]) : 0.0f;
-            vw[u] = r[u] >= 0 ? __ldg(w + r[u]) : 0.0f;
-        }
-#pragma unroll
-        for (int u = 0; u < PAYLOAD_PER_THREAD; ++u) {
-            const int o = o0 + u * PAYLOAD_THREADS;
-            if (o < n_hits) {
-                oz[o] = vz[u];
-                od[o] = vd[u];
-                ow[o] = vw[u];
-            }
+            b0 = b1;
         }
     }
 }
@@ -420,28 +485,15 @@ cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, 
                         const uint8_t* plane, int n_events, int n_hits, int* hit_offsets, float* ox, float* oz,
                         float* odxdy, float* ow, uint8_t* olayer, int* perm, int* cursor, int* status, int n_sm,
                         cudaStream_t s) {
+    (void)n_hits;
     cudaError_t err =
         cudaFuncSetAttribute(k_pack_event, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AREA_BYTES);
     if (err != cudaSuccess) return err;
-    int bps = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_pack_event, PACK_THREADS, AREA_BYTES);
-    if (err != cudaSuccess) return err;
-    if (bps < 1) bps = 1;
-    if ((err = cudaMemsetAsync(cursor, 0, 2 * sizeof(int), s)) != cudaSuccess) return err;
-    int grid = n_sm * bps;
+    if ((err = cudaMemsetAsync(cursor, 0, sizeof(int), s)) != cudaSuccess) return err;
+    int grid = n_sm;
     if (grid > n_events) grid = n_events > 0 ? n_events : 1;
-    k_pack_event<<<grid, PACK_THREADS, AREA_BYTES, s>>>(raw_offsets, x, plane, n_events, hit_offsets, ox, olayer,
-                                                        perm, cursor, status);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    if (n_hits > 0) {
-        int bpp = 0;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpp, k_pack_payload, PAYLOAD_THREADS, 0);
-        if (err != cudaSuccess) return err;
-        const long tiles = ((long)n_hits + PAYLOAD_TILE - 1) / PAYLOAD_TILE;
-        int gp = n_sm * (bpp > 0 ? bpp : 1);
-        if (gp > tiles) gp = (int)tiles;
-        k_pack_payload<<<gp, PAYLOAD_THREADS, 0, s>>>(z, dxdy, w, perm, n_hits, oz, odxdy, ow, cursor + 1);
-    }
+    k_pack_event<<<grid, PACK_THREADS, AREA_BYTES, s>>>(raw_offsets, x, z, dxdy, w, plane, n_events, hit_offsets,
+                                                        ox, oz, odxdy, ow, olayer, perm, cursor, status);
     return cudaGetLastError();
 }
 

@@ -1,14 +1,17 @@
 """Continuous-batching server for the forward-tracking path.
 
 Events arrive over time into a host-resident pool (pinned memory).  The
-server keeps S slots, each with its own CUDA stream, library context and
-device buffers allocated once (hit, state and output buffers stay resident;
-geometry and parameters live in the contexts).  Whenever a slot is free it
-takes every event that has arrived and is not yet scheduled (up to the slot's
-event and hit capacity), copies them to the device, packs and follows them
+server keeps S slots, each with its own library context and device buffers
+allocated once (hit, state and output buffers stay resident; geometry and
+parameters live in the contexts), and three CUDA streams shared by the slots:
+copies in, compute, copies out.  Whenever a slot is free it takes every event
+that has arrived and is not yet scheduled (up to the slot's event and hit
+capacity); its copies in are queued on the first stream, its pack and find
 (persistent form, launch shape from the autotuner for the batch's size
-bucket) and copies the per-track results back, all asynchronously on the
-slot's stream; batches on different slots overlap on the device.  A batch is
+bucket) on the compute stream after them, and the copies of its per-track
+results on the third stream after the compute, chained by events.  So the
+copies in of one batch, the compute of another and the copies out of a third
+overlap on the device.  A batch is
 admitted only while the device bytes of the batches in flight stay within the
 memory budget.  Latency is measured per event from its arrival time to the
 moment the server sees its batch complete with results in host memory.
@@ -32,10 +35,11 @@ from . import lf
 from .autotune import Autotuner
 
 NL = 12
-# device bytes per hit (raw 17 + packed 21 + pack staging 20) and per input
-# track (states 20, outputs 81, stage-pipeline scratch ~733)
-BYTES_PER_HIT = 58
-BYTES_PER_TRACK = 834
+# device bytes per hit (raw 17 + packed 21) and per input track (states 20,
+# outputs 81, persistent-pipeline scratch 161: event index, windows, kept
+# triplet keys and counts)
+BYTES_PER_HIT = 38
+BYTES_PER_TRACK = 262
 
 
 @dataclasses.dataclass
@@ -52,7 +56,6 @@ class ServeStats:
 
 class _Slot:
     def __init__(self, max_events: int, max_hits: int, max_tracks: int, geometry, params, dev):
-        self.stream = torch.cuda.Stream(device=dev)
         self.tr = lf.Tracker(geometry, params)
         e = lambda n, dt: torch.empty(n, dtype=dt, device=dev)
         self.raw = dict(x=e(max_hits, torch.float32), z=e(max_hits, torch.float32), dxdy=e(max_hits, torch.float32),
@@ -75,6 +78,8 @@ class _Slot:
         self.h_state = p((max_tracks, 6), torch.float32)
         self.h_q = p(max_tracks, torch.float32)
         self.h_perm = p(max_hits, torch.int32)
+        self.ev_in = torch.cuda.Event()
+        self.ev_comp = torch.cuda.Event()
         self.done = torch.cuda.Event()
         self.busy = False
         self.batch = None      # (e0, e1, h0, h1, t0, t1, nbytes)
@@ -109,6 +114,9 @@ class Server:
         self.max_tracks = max(max_tracks, 1)
         self.slots = [_Slot(max_events, self.max_hits, self.max_tracks, geometry, params, self.dev)
                       for _ in range(n_slots)]
+        self.s_in = torch.cuda.Stream(device=self.dev)
+        self.s_comp = torch.cuda.Stream(device=self.dev)
+        self.s_out = torch.cuda.Stream(device=self.dev)
         self.tuner = tuner or Autotuner()
         self.keep_results = keep_results
         self.results: Dict[int, dict] = {}
@@ -147,18 +155,23 @@ class Server:
         p = self.pool
         s.h_ro[:ne + 1].copy_(torch.from_numpy((self.ro[e0:e1 + 1] - h0).astype(np.int32)))
         s.h_to[:ne + 1].copy_(torch.from_numpy((self.to[e0:e1 + 1] - t0).astype(np.int32)))
-        with torch.cuda.stream(s.stream):
+        # a slot is launched only when its previous batch has completed, so
+        # its buffers are free
+        with torch.cuda.stream(self.s_in):
             for f in ("x", "z", "dxdy", "w", "plane"):
                 s.raw[f][:nh].copy_(getattr(p, f)[h0:h1], non_blocking=True)
             s.raw["raw_offsets"][:ne + 1].copy_(s.h_ro[:ne + 1], non_blocking=True)
             s.st["trk_offsets"][:ne + 1].copy_(s.h_to[:ne + 1], non_blocking=True)
             for f in ("sx", "sy", "stx", "sty", "sqop"):
                 s.st[f][:nt].copy_(getattr(p, f)[t0:t1], non_blocking=True)
+            s.ev_in.record(self.s_in)
+        self.s_comp.wait_event(s.ev_in)
+        with torch.cuda.stream(self.s_comp):
             raw = SimpleNamespace(n_events=ne, raw_offsets=s.raw["raw_offsets"][:ne + 1], x=s.raw["x"][:nh],
                                   z=s.raw["z"][:nh], dxdy=s.raw["dxdy"][:nh], w=s.raw["w"][:nh],
                                   plane=s.raw["plane"][:nh])
             pk = {k: (v[:24 * ne + 1] if k == "hit_offsets" else v[:nh]) for k, v in s.packed.items()}
-            s.tr.pack(raw, s.stream, out=pk)
+            s.tr.pack(raw, self.s_comp, out=pk)
             st = SimpleNamespace(trk_offsets=s.st["trk_offsets"][:ne + 1], sx=s.st["sx"][:nt], sy=s.st["sy"][:nt],
                                  stx=s.st["stx"][:nt], sty=s.st["sty"][:nt], sqop=s.st["sqop"][:nt])
             out = {k: v for k, v in s.out.items()}
@@ -167,7 +180,10 @@ class Server:
             out["out_offsets"] = s.out["out_offsets"][:ne + 1]
             out["out_trk"] = s.out["out_trk"][:max(nt, 1)]
             tuning = self.tuner.lookup(ne, nt)
-            s.tr.find(pk, st, ne, "batched", tuning, s.stream, out=out)
+            s.tr.find(pk, st, ne, "batched", tuning, self.s_comp, out=out)
+            s.ev_comp.record(self.s_comp)
+        self.s_out.wait_event(s.ev_comp)
+        with torch.cuda.stream(self.s_out):
             # the per-track results come back to the host for every batch
             s.h_found[:nt].copy_(out["found"], non_blocking=True)
             s.h_nhits[:nt].copy_(out["nhits"], non_blocking=True)
@@ -176,7 +192,7 @@ class Server:
             s.h_q[:nt].copy_(out["quality"], non_blocking=True)
             if self.keep_results:
                 s.h_perm[:nh].copy_(pk["perm"], non_blocking=True)
-            s.done.record(s.stream)
+            s.done.record(self.s_out)
         s.busy = True
         s.batch = batch
         self.inflight_bytes += nbytes

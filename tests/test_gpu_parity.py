@@ -138,6 +138,79 @@ def test_bucket_over_capacity_is_reported(lfm):
     assert tr.status() == 0  # cleared
 
 
+def _raw_event(rng, n, x, plane):
+    z = rng.uniform(7800.0, 9400.0, n).astype(np.float32)
+    d = rng.uniform(-0.1, 0.1, n).astype(np.float32)
+    w = rng.uniform(100.0, 200.0, n).astype(np.float32)
+    return np.asarray(x, np.float32), z, d, w, np.asarray(plane, np.uint8)
+
+
+def _batch_of(parts, n_states=0):
+    cat = lambda i: torch.from_numpy(np.concatenate([p[i] for p in parts]))
+    nh = [len(p[0]) for p in parts]
+    ro = torch.tensor(np.concatenate([[0], np.cumsum(nh)]).astype(np.int32))
+    to = torch.zeros(len(parts) + 1, dtype=torch.int32)
+    e = torch.zeros(0, dtype=torch.float32)
+    return synth.EventBatch(len(parts), ro, cat(0), cat(1), cat(2), cat(3), cat(4), to, e, e, e, e, e)
+
+
+def test_pack_paths_exact(lfm):
+    """Both pack paths against the oracle, bit for bit: events sorted in one
+    piece in shared memory (up to 20480 hits) and larger events staged
+    through their output range in chunks; ties in x (ordered by raw index),
+    -0.0 and +0.0, a skewed x distribution and random plane codes."""
+    rng = np.random.default_rng(11)
+    parts = []
+    for n in (1, 3000, 20480, 20481, 50000):
+        x = rng.uniform(-3000.0, 3000.0, n)
+        if n >= 3000:
+            x[: n // 3] = np.round(x[: n // 3] * 2.0) / 2.0     # many exact ties
+            x[n // 3: n // 3 + 50] = 0.0
+            x[n // 3 + 50: n // 3 + 100] = -0.0
+        parts.append(_raw_event(rng, n, x, rng.integers(0, 24, n)))
+    # skewed: 3000 hits inside one millimetre and one far outlier, one bucket
+    x = np.concatenate([rng.uniform(10.0, 11.0, 3000), [2900.0]])
+    parts.append(_raw_event(rng, 3001, x, np.full(3001, 5)))
+    b = _batch_of(parts).to("cuda")
+    tr = _tracker(lfm)
+    packed = tr.pack(b)
+    torch.cuda.synchronize()
+    assert tr.status() == 0
+    ref = oracle.pack(*(t.cpu().numpy() for t in (b.raw_offsets, b.x, b.z, b.dxdy, b.w, b.plane)))
+    compare_pack(packed, ref)
+
+
+def test_pack_flagged_bucket_beside_sorted_ones(lfm):
+    """A bucket above LF_MAX_BUCKET in an event whose other buckets are
+    sorted: those match the oracle, the flagged bucket's perm is -1."""
+    rng = np.random.default_rng(12)
+    n_big, n_rest = 16385, 9000
+    plane = np.concatenate([np.full(n_big, 7), rng.integers(8, 24, n_rest)])
+    x = rng.uniform(-3000.0, 3000.0, n_big + n_rest)
+    order = rng.permutation(n_big + n_rest)
+    parts = [_raw_event(rng, 500, rng.uniform(-100, 100, 500), rng.integers(0, 24, 500)),
+             _raw_event(rng, n_big + n_rest, x[order], plane[order])]
+    b = _batch_of(parts).to("cuda")
+    tr = _tracker(lfm)
+    packed = tr.pack(b)
+    torch.cuda.synchronize()
+    with pytest.raises(lfm.LFError) as ei:
+        tr.status()
+    assert ei.value.status == lfm.LF_ERR_CAPACITY
+    ref = oracle.pack(*(t.cpu().numpy() for t in (b.raw_offsets, b.x, b.z, b.dxdy, b.w, b.plane)))
+    ho = to_np(packed["hit_offsets"])
+    assert np.array_equal(ho, ref["hit_offsets"])
+    lo, hi = int(ho[24 + 7]), int(ho[24 + 8])          # event 1, bucket 7
+    perm = to_np(packed["perm"])
+    assert np.all(perm[lo:hi] == -1)
+    keep = np.ones(perm.size, bool)
+    keep[lo:hi] = False
+    assert np.array_equal(perm[keep], ref["perm"][keep])
+    for k in ("x", "z", "dxdy", "w"):
+        assert np.array_equal(to_np(packed[k])[keep].view(np.uint32), ref[k][keep].view(np.uint32))
+    assert np.array_equal(to_np(packed["layer"]), ref["layer"])
+
+
 def test_bad_parameters_rejected(lfm):
     p = lfm.default_params()
     p["n_hits_window"] = 65
