@@ -21,7 +21,6 @@ from __future__ import annotations
 import argparse
 import dataclasses
 import hashlib
-import mmap
 import json
 import os
 import statistics
@@ -148,37 +147,13 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(pw)}
 
 
-class PinnedArena:
-    """Page-locked host memory of an exact size (anonymous mmap registered
-    with CUDA), carved into torch tensors; avoids the power-of-two rounding
-    of torch's pinned allocator for multi-GB batches."""
-
-    def __init__(self, nbytes: int):
-        self.nbytes = max(int(nbytes), 4096)
-        self.mm = mmap.mmap(-1, self.nbytes)
-        self.base = torch.frombuffer(self.mm, dtype=torch.uint8)
-        rc = torch.cuda.cudart().cudaHostRegister(self.base.data_ptr(), self.nbytes, 0)
-        self.registered = int(rc) == 0
-        self.off = 0
-
-    def take(self, n: int, dtype) -> torch.Tensor:
-        esz = torch.empty(0, dtype=dtype).element_size()
-        self.off = (self.off + 255) & ~255
-        t = self.base[self.off:self.off + n * esz].view(dtype)
-        self.off += n * esz
-        return t
-
-    def close(self):
-        if self.registered:
-            torch.cuda.cudart().cudaHostUnregister(self.base.data_ptr())
-            self.registered = False
-
-
 def host_copy(batch, arena_bytes_extra: int = 0):
-    """Copy a device EventBatch into one pinned arena."""
+    """Copy a device EventBatch into one page-locked arena (cudaHostAlloc
+    through lf_host_alloc: copies from it overlap device work)."""
+    from paper_2402_14670_gb300 import lf
     fields = ("raw_offsets", "x", "z", "dxdy", "w", "plane", "trk_offsets", "sx", "sy", "stx", "sty", "sqop")
     total = sum(getattr(batch, f).numel() * getattr(batch, f).element_size() + 256 for f in fields)
-    arena = PinnedArena(total + arena_bytes_extra)
+    arena = lf.HostArena(total + arena_bytes_extra)
     kw = {}
     for f in fields:
         src = getattr(batch, f)
@@ -256,14 +231,24 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(units_hits: int):
-    """DRAM bytes of the fused kernel from a committed ncu capture, scaled to
-    this launch by hits, or None when the kernel changed since the capture."""
-    p = os.path.join(ROOT, "profiles", "k_fused_traffic.json")
+def find_profile():
+    """The committed ncu figures of the find kernels (DRAM bytes and warp
+    instructions of one launch on a 10 000-event slice), or None when the
+    kernels changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "find_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return d
+
+
+def traffic_per_launch(units_hits: int):
+    """DRAM bytes of the find kernels from the committed ncu capture, scaled
+    to this launch by hits, or None when the kernels changed since."""
+    d = find_profile()
+    if d is None:
         return None
     return float(d["dram_bytes_per_launch"]) * units_hits / float(d["hits"])
 
@@ -459,7 +444,7 @@ def main():
                "ms_per_step": 1e3 * e2e_s, "api": "lf_process_host (chunked; copies in, compute and copies out on three streams)"}
         n_hits, n_trk = host.n_hits, host.n_tracks
         cpu_src = host
-        e2e["pinned"] = arena.registered
+        e2e["host_memory"] = "cudaHostAlloc (lf_host_alloc)"
     else:
         n_hits, n_trk = batch.n_hits, batch.n_tracks
         cpu_src = None
@@ -498,6 +483,22 @@ def main():
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_kind": peak_kind, "traffic": traffic_per_launch(n_hits), "algorithmic_bytes": algo,
             "launch_ms": find_avg}
+    # the find kernels are bound by instruction issue, not by DRAM: their warp
+    # instructions (committed ncu count, scaled by input tracks) per second
+    # against the issue peak (4 warp instructions per SM per cycle at the
+    # median SM clock of the timed region)
+    roof_issue = None
+    fp = find_profile()
+    if fp is not None and torch.cuda.is_available():
+        n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+        inst = float(fp["warp_instructions_per_launch"]) * n_trk / float(fp["tracks"])
+        ach = inst / (find_avg / 1e3)
+        pk_issue = n_sm * 4 * mhz * 1e6
+        roof_issue = {"kernel": "k_windows + k_triplets + k_extend (persistent)", "bound": "issue",
+                      "achieved": ach, "peak": pk_issue, "unit": "warp-instructions/s", "frac": ach / pk_issue,
+                      "warp_instructions_per_launch": inst,
+                      "peak_kind": "%d SMs x 4 schedulers x %.0f MHz (median SM clock, timed region)" % (n_sm, mhz)}
     pk_algo = pack_bytes(n_ev, n_hits)
     roof_pack = {"kernel": "k_pack_event (persistent per-event bin sort with the payload gather)", "bound": "hbm",
                  "achieved": pk_algo / (pack_avg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
@@ -519,10 +520,10 @@ def main():
         except Exception as e:  # the oracle is test infrastructure; report why it did not run
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "error": str(e)}
 
-    # pack: bucket, gather, small-bucket sort, large-bucket sort; find (default
-    # queue mode): track->event map, three persistent stage kernels (windows,
-    # triplets, extension with the selection), three compaction kernels
-    launches_per_step = 4 + (1 + 3) + 3
+    # pack: one persistent kernel (k_pack_event); find (default queue mode):
+    # track->event map, three persistent stage kernels (windows, triplets,
+    # extension with the selection), three compaction kernels
+    launches_per_step = 1 + (1 + 3) + 3
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -535,7 +536,8 @@ def main():
                        "tuning": tuning or "defaults",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "single"},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-            "roofline": roof, "roofline_pack": roof_pack, "plain": plain, "served": served, "no_ut": no_ut,
+            "roofline": roof, "roofline_issue": roof_issue, "roofline_pack": roof_pack, "plain": plain,
+            "served": served, "no_ut": no_ut,
             "cpu_baseline": cpu,
             "stage_ms": {"pack": pack_avg, "find": find_avg}, "found_tracks": n_found,
         }

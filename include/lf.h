@@ -229,6 +229,17 @@ typedef struct {
     uint8_t* found; uint8_t* nhits; int32_t* hit_idx; float* state; float* quality;
 } lf_host_output;
 
+/* Page-locked host memory of exactly `bytes` bytes (cudaHostAlloc, portable
+ * across devices) for the host-side buffers of lf_process_host and of a
+ * serving loop: copies from it run asynchronously and overlap device work.
+ * (Memory pinned after the fact with cudaHostRegister can give copies that
+ * block the calling thread until they finish, which serialises the copies
+ * with the compute queued behind them.)  *out receives the pointer (NULL
+ * when bytes is 0); LF_ERR_OOM when the allocation fails.  Release with
+ * lf_host_free. */
+lf_status lf_host_alloc(size_t bytes, void** out);
+void lf_host_free(void* p);
+
 /* End-to-end call on host buffers: the batch is cut at event boundaries into
  * chunks of at most chunk_hits hits; each chunk is copied to the device,
  * packed, followed (persistent form) and its results copied back.  Three

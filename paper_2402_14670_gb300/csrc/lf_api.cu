@@ -504,6 +504,22 @@ lf_status lf_sync_status(lf_ctx* c, void* stream, int32_t* flags) {
     return LF_OK;
 }
 
+lf_status lf_host_alloc(size_t bytes, void** out) {
+    if (!out) return LF_ERR_ARG;
+    *out = nullptr;
+    if (bytes == 0) return LF_OK;
+    if (cudaHostAlloc(out, bytes, cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return LF_ERR_OOM;
+    }
+    return LF_OK;
+}
+
+void lf_host_free(void* p) {
+    if (p) cudaFreeHost(p);
+}
+
 lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_output* ho, const lf_tuning* tuning,
                           int64_t chunk_hits) {
     if (!c) return LF_ERR_ARG;

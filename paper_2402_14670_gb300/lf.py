@@ -113,10 +113,14 @@ _lib.lf_process_host.restype = C.c_int
 _lib.lf_find_tracks_static.argtypes = [C.POINTER(lf_geometry), C.POINTER(lf_params), C.POINTER(lf_batch),
                                        C.POINTER(lf_output), _P]
 _lib.lf_find_tracks_static.restype = C.c_int
+_lib.lf_host_alloc.argtypes = [C.c_size_t, C.POINTER(_P)]
+_lib.lf_host_alloc.restype = C.c_int
+_lib.lf_host_free.argtypes = [_P]
+_lib.lf_host_free.restype = None
 
 EXPORTED = ["lf_create", "lf_destroy", "lf_last_error", "lf_device_sm_count", "lf_pack_hits", "lf_find_tracks",
             "lf_find_tracks_batched", "lf_debug_stages", "lf_sync_status", "lf_process_host",
-            "lf_find_tracks_static"]
+            "lf_find_tracks_static", "lf_host_alloc", "lf_host_free"]
 
 
 class LFError(RuntimeError):
@@ -215,6 +219,46 @@ def lf_last_error(ctx) -> str:
 
 def lf_device_sm_count() -> int:
     return int(_lib.lf_device_sm_count())
+
+
+def lf_host_alloc(nbytes: int) -> int:
+    """Page-locked host memory of exactly nbytes (0 when nbytes is 0)."""
+    p = _P()
+    st = _lib.lf_host_alloc(C.c_size_t(int(nbytes)), C.byref(p))
+    if st != LF_OK:
+        raise LFError(st, "lf_host_alloc of %d bytes failed" % nbytes)
+    return int(p.value or 0)
+
+
+def lf_host_free(ptr: int) -> None:
+    _lib.lf_host_free(_P(ptr) if ptr else None)
+
+
+class HostArena:
+    """Page-locked host memory of an exact size from lf_host_alloc, carved
+    into torch tensors (torch's own pinned allocator rounds multi-GB requests
+    up to a power of two)."""
+
+    def __init__(self, nbytes: int):
+        self.nbytes = max(int(nbytes), 4096)
+        self.ptr = lf_host_alloc(self.nbytes)
+        self.base = torch.frombuffer((C.c_uint8 * self.nbytes).from_address(self.ptr), dtype=torch.uint8)
+        self.off = 0
+
+    def take(self, n: int, dtype) -> torch.Tensor:
+        esz = torch.empty(0, dtype=dtype).element_size()
+        self.off = (self.off + 255) & ~255
+        if self.off + n * esz > self.nbytes:
+            raise ValueError("host arena exhausted")
+        t = self.base[self.off:self.off + n * esz].view(dtype)
+        self.off += n * esz
+        return t
+
+    def close(self):
+        if self.ptr:
+            self.base = None
+            lf_host_free(self.ptr)
+            self.ptr = 0
 
 
 def lf_pack_hits(ctx, raw: lf_raw_hits, packed: lf_packed, stream) -> None:

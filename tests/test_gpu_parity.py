@@ -288,3 +288,22 @@ def test_end_to_end_host_pipeline(lfm, chunk_hits):
     assert np.array_equal(ho["state"].numpy()[found].view(np.uint32), to_np(out["state"])[found].view(np.uint32))
     res = oracle.run_batch(b, dumps=False)
     assert np.array_equal(res["found"].astype(bool), found)
+
+
+def test_host_arena_is_page_locked(lfm):
+    """lf_host_alloc gives exact-size page-locked memory that torch sees as
+    pinned, so copies from it are asynchronous."""
+    ar = lfm.HostArena(5 * (1 << 20) + 17)
+    try:
+        a = ar.take(1 << 20, torch.float32)
+        b = ar.take(5, torch.uint8)
+        assert a.is_pinned() and b.is_pinned()
+        assert a.data_ptr() % 256 == 0 and b.data_ptr() % 256 == 0
+        a.copy_(torch.arange(a.numel(), dtype=torch.float32))
+        d = a.to("cuda", non_blocking=True)
+        torch.cuda.synchronize()
+        assert torch.equal(d.cpu(), a)
+        with pytest.raises(ValueError):
+            ar.take(1 << 20, torch.float32)
+    finally:
+        ar.close()
