@@ -432,16 +432,28 @@ def main():
         for _ in range(args.warmup):
             tr.process_host(host, out=hout, tuning=tuning)
         barrier(ws)
+        steps_ms = []
         t0 = time.perf_counter()
         for _ in range(args.steps):
+            ta = time.perf_counter()
             tr.process_host(host, out=hout, tuning=tuning)
+            steps_ms.append((time.perf_counter() - ta) * 1e3)
         e2e_s = max_over_ranks(ws, time.perf_counter() - t0) / args.steps
+        # the host link alone: one copy of the x array to the device
+        dx = torch.empty(host.x.numel(), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        dx.copy_(host.x, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_gbps = host.x.numel() * 4 / (time.perf_counter() - ta) / 1e9
+        del dx
         h2d = sum(int(t.numel() * t.element_size()) for t in
                   (host.raw_offsets, host.x, host.z, host.dxdy, host.w, host.plane, host.trk_offsets,
                    host.sx, host.sy, host.stx, host.sty, host.sqop))
         d2h = sum(int(t.numel() * t.element_size()) for t in hout.values())
         e2e = {"value": ws * n_ev / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": 1e3 * e2e_s, "api": "lf_process_host (chunked; copies in, compute and copies out on three streams)"}
+               "ms_per_step": 1e3 * e2e_s, "step_ms": steps_ms, "h2d_gbps_x_copy": h2d_gbps,
+               "api": "lf_process_host (chunked; copies in, compute and copies out on three streams)"}
         n_hits, n_trk = host.n_hits, host.n_tracks
         cpu_src = host
         e2e["host_memory"] = "cudaHostAlloc (lf_host_alloc)"

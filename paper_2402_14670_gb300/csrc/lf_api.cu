@@ -46,6 +46,10 @@ struct lf_ctx {
         cudaStream_t stream = nullptr;
     };
     std::map<GraphKey, GraphEntry> graphs;
+    // launch shapes seen once: a shape is captured into a graph only when it
+    // comes back (a serving loop's batch sizes rarely repeat)
+    std::map<GraphKey, unsigned long long> seen;
+    unsigned long long seen_clock = 0;
     // end-to-end host pipeline: a compute sub-context (own scratch), three
     // streams (copies in, compute, copies out), events chaining them, and
     // three device staging arenas
@@ -444,6 +448,17 @@ lf_status lf_find_tracks_batched(lf_ctx* c, const lf_batch* b, const lf_output* 
                             (const void*)(uintptr_t)c->generation);
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
+        // first use of this shape: launch directly and remember it (bounded)
+        if (c->seen.find(key) == c->seen.end()) {
+            if (c->seen.size() >= 256) {
+                auto oldest = c->seen.begin();
+                for (auto jt = c->seen.begin(); jt != c->seen.end(); ++jt)
+                    if (jt->second < oldest->second) oldest = jt;
+                c->seen.erase(oldest);
+            }
+            c->seen[key] = ++c->seen_clock;
+            return launch_batched(c, b, o, sh, s);
+        }
         cudaStream_t cap;
         LF_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;

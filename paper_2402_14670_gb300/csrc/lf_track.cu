@@ -286,33 +286,70 @@ __device__ __forceinline__ Scratch scratch_at(char* base, int i) {
     return s;
 }
 
+// Asynchronous 4-byte copy global -> shared (cp.async, cached in L1); the
+// copying lane waits for its copies with cp_async_wait_all.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Copy x and z of the window hits into the slot: the (layer, hit) pairs of
 // the windows (all twelve, or the six x layers when XONLY) are flattened over
-// the lanes so that several loads are in flight per lane; a window whose
-// hits do not all share one z is flagged.
+// the lanes and every pair is one asynchronous copy per array, so all of a
+// track's copies are in flight at once (stage_issue); stage_finish waits for
+// them and flags a window whose hits do not all share one z.
 template <bool XONLY = false>
-__device__ __forceinline__ void stage_windows(const KParams& k, const KBatch& b, const Slot& m, int lane) {
+__device__ __forceinline__ void stage_issue(const KParams& k, const KBatch& b, const Slot& m, int lane) {
     const int cap = k.cap;
     int off[NL + 1];
     off[0] = 0;
 #pragma unroll
     for (int l = 0; l < NL; ++l) off[l + 1] = off[l] + ((XONLY && !is_x(l)) ? 0 : m.h->wcnt[l]);
-    if (lane < NL) m.h->zuni[lane] = 1;
-    __syncwarp();
     const int total = off[NL];
-#pragma unroll 4
+#pragma unroll 2
     for (int q = lane; q < total; q += 32) {
-        int l = 0;
+        int l = 0, lo = 0;   // the window of pair q (offsets are non-decreasing)
 #pragma unroll
-        for (int i = 1; i < NL; ++i) l += (q >= off[i]) ? 1 : 0;
-        int j = q - off[l];
-        int src = m.h->wbeg[l] + j;
-        float zz = __ldg(b.z + src);
-        m.wx[l * cap + j] = __ldg(b.x + src);
-        m.wz[l * cap + j] = zz;
-        if (zz != __ldg(b.z + m.h->wbeg[l])) m.h->zuni[l] = 0;
+        for (int i = 1; i < NL; ++i)
+            if (q >= off[i]) {
+                l = i;
+                lo = off[i];
+            }
+        const int j = q - lo;
+        const int src = m.h->wbeg[l] + j;
+        cp_async4(m.wx + l * cap + j, b.x + src);
+        cp_async4(m.wz + l * cap + j, b.z + src);
     }
+}
+
+// z-uniformity flag of window l of a staged slot (lane-private loop)
+template <bool XONLY = false>
+__device__ __forceinline__ void window_zuni(const KParams& k, const Slot& m, int l) {
+    int u = 1;
+    if (!(XONLY && !is_x(l))) {
+        const float* wz = m.wz + l * k.cap;
+        const int n = m.h->wcnt[l];
+        for (int j = 1; j < n; ++j) u &= (wz[j] == wz[0]) ? 1 : 0;
+    }
+    m.h->zuni[l] = u;
+}
+
+// Wait for the staging copies of the warp's TPW slots (lanes 16q.. of slot q)
+// and set their z-uniformity flags.
+template <int TPW, bool XONLY = false>
+__device__ __forceinline__ void stage_finish(const KParams& k, const Slot* sl, int lane) {
+    cp_async_wait_all();
     __syncwarp();
+    const int q = lane >> 4, l = lane & 15;
+    if (q < TPW && l < NL) window_zuni<XONLY>(k, (TPW == 2 && q == 1) ? sl[TPW - 1] : sl[0], l);
+    __syncwarp();
+}
+
+template <bool XONLY = false>
+__device__ __forceinline__ void stage_windows(const KParams& k, const KBatch& b, const Slot& m, int lane) {
+    stage_issue<XONLY>(k, b, m, lane);
+    stage_finish<1, XONLY>(k, &m, lane);
 }
 
 __device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
@@ -969,21 +1006,37 @@ __device__ __forceinline__ void extend_tracks(const KParams& k, const KBatch& b,
                                               const uint8_t* __restrict__ wcnt, const uint64_t* __restrict__ keys,
                                               const uint8_t* __restrict__ ntrip, CandRec* cands, const KOut& o,
                                               const Slot* sl, int t0, int lane) {
-#pragma unroll
-    for (int qq = 0; qq < TPW; ++qq) {
-        int tq = t0 + qq;
-        if (tq < b.n_tracks) {
-            load_windows(wbeg, wcnt, tq, sl[qq], lane);
-            stage_windows(k, b, sl[qq], lane);
+    // the window descriptors of the TPW tracks in one round trip (lanes 16q..
+    // for track q; a track past the end gets empty windows), then every
+    // staging copy of both tracks in flight at once
+    {
+        const int qw = lane >> 4, lw = lane & 15, tw = t0 + qw;
+        int wb = 0, wc = 0;
+        if (qw < TPW && lw < NL && tw < b.n_tracks) {
+            wb = wbeg[(size_t)tw * NL + lw];
+            wc = wcnt[(size_t)tw * NL + lw];
         }
+        if (qw < TPW && lw < NL) {
+            const Slot& mw = (TPW == 2 && qw == 1) ? sl[TPW - 1] : sl[0];
+            mw.h->wbeg[lw] = wb;
+            mw.h->wcnt[lw] = wc;
+        }
+        __syncwarp();
     }
+#pragma unroll
+    for (int qq = 0; qq < TPW; ++qq) stage_issue(k, b, sl[qq], lane);
     constexpr int G = 32 / TPW;
     const int q = lane / G, r = lane % G;
     const int t = t0 + q;
     Slot mq = sl[0];
     if (TPW == 2 && q == 1) mq = sl[TPW - 1];
     const bool live = t < b.n_tracks;
+    // this lane's candidate inputs load while the copies are in flight
     const bool act = live && r < ntrip[t];
+    const uint64_t key = act ? keys[(size_t)t * k.n_trip + r] : NOKEY;
+    TState s = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (act) s = load_state(b, t);
+    stage_finish<TPW>(k, sl, lane);
     Cand cd;
     cd.status = 9;
     cd.Q = 0.0f;
@@ -992,10 +1045,7 @@ __device__ __forceinline__ void extend_tracks(const KParams& k, const KBatch& b,
     for (int p = 0; p < 6; ++p) cd.st[p] = 0.0f;
 #pragma unroll
     for (int l = 0; l < NL; ++l) cd.hl[l] = -1;
-    if (act) {
-        TState s = load_state(b, t);
-        extend_fit(k, b, s, mq, keys[(size_t)t * k.n_trip + r], cd);
-    }
+    if (act) extend_fit(k, b, s, mq, key, cd);
     if (SEL) {
         int hg[NL];
 #pragma unroll

@@ -24,7 +24,6 @@ from __future__ import annotations
 
 import dataclasses
 import time
-from collections import deque
 from types import SimpleNamespace
 from typing import Dict, List, Optional
 
@@ -128,23 +127,18 @@ class Server:
             s.close()
 
     # -------------------------------------------------------------- batches
-    def _take(self, pending: deque) -> Optional[tuple]:
-        """Events of the next batch: a run of consecutive pending events
-        (arrival order is pool order) within the slot capacity and budget."""
-        e0 = pending[0][0]
-        e1 = e0
-        h_room, t_room = self.max_hits, self.max_tracks
-        while pending and e1 - e0 < self.max_events and pending[0][0] == e1:
-            nh = self.ro[e1 + 1] - self.ro[e1]
-            nt = self.to[e1 + 1] - self.to[e1]
-            if nh > h_room or nt > t_room:
-                break
-            h_room -= nh
-            t_room -= nt
-            pending.popleft()
-            e1 += 1
-        if e1 == e0:
-            raise RuntimeError("event %d does not fit a slot" % e0)
+    def _take(self, head: int, avail: int) -> tuple:
+        """The next batch: the longest run of the pending events head ..
+        head+avail-1 (arrival order is pool order) within the slot's event,
+        hit and track capacity."""
+        k = min(avail, self.max_events)
+        ch = self.ro[head + 1:head + k + 1] - self.ro[head]
+        ct = self.to[head + 1:head + k + 1] - self.to[head]
+        k = min(k, int(np.searchsorted(ch, self.max_hits, side="right")),
+                int(np.searchsorted(ct, self.max_tracks, side="right")))
+        if k == 0:
+            raise RuntimeError("event %d does not fit a slot" % head)
+        e0, e1 = head, head + k
         h0, h1, t0, t1 = int(self.ro[e0]), int(self.ro[e1]), int(self.to[e0]), int(self.to[e1])
         nbytes = (h1 - h0) * BYTES_PER_HIT + (t1 - t0) * BYTES_PER_TRACK
         return e0, e1, h0, h1, t0, t1, nbytes
@@ -224,16 +218,14 @@ class Server:
         the given times (seconds from start, non-decreasing)."""
         n = len(arrivals)
         done_at = np.zeros(n)
-        pending: deque = deque()
-        nxt = 0
+        nxt = 0            # events [0, nxt) have arrived
+        head = 0           # events [head, nxt) are pending (arrived, not scheduled)
         completed = 0
         batches: List[int] = []
         t_start = time.perf_counter()
         while completed < n:
             now = time.perf_counter() - t_start
-            while nxt < n and arrivals[nxt] <= now:
-                pending.append((first_event + nxt, arrivals[nxt]))
-                nxt += 1
+            nxt = int(np.searchsorted(arrivals, now, side="right"))
             progressed = False
             for s in self.slots:
                 if s.busy and s.done.query():
@@ -244,21 +236,19 @@ class Server:
                     completed += e1 - e0
                     progressed = True
             for s in self.slots:
-                if not pending:
+                if head >= nxt:
                     break
                 if s.busy:
                     continue
-                b = self._take(pending)
+                b = self._take(first_event + head, nxt - head)
                 if self.inflight_bytes + b[6] > self.budget and self.inflight_bytes > 0:
-                    # not admitted yet: put the events back and wait for memory
-                    for e in range(b[1] - 1, b[0] - 1, -1):
-                        pending.appendleft((e, arrivals[e - first_event]))
-                    break
+                    break      # not admitted yet: wait for memory
                 self._launch(s, b)
+                head += b[1] - b[0]
                 batches.append(b[1] - b[0])
                 progressed = True
             if not progressed:
-                if nxt < n and not pending and not any(s.busy for s in self.slots):
+                if nxt < n and head >= nxt and not any(s.busy for s in self.slots):
                     delay = arrivals[nxt] - (time.perf_counter() - t_start)
                     if delay > 0:
                         time.sleep(min(delay, 0.001))
