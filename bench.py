@@ -529,6 +529,10 @@ def main():
             dt, _ = time_oracle(sample, threads)
             cpu = {"value": n_s / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
                    "sample": "first %d events of the same batch: pack + find + compact" % n_s}
+            n_1 = min(300, n_s)
+            dt1, _ = time_oracle(cpu_src.select_events(range(n_1)), 1)
+            cpu["single_thread"] = {"value": n_1 / dt1, "unit": UNIT, "cores": 1,
+                                    "sample": "first %d events, one thread" % n_1}
         except Exception as e:  # the oracle is test infrastructure; report why it did not run
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "error": str(e)}
 

@@ -49,17 +49,24 @@ constexpr int PACK_WARPS = PACK_THREADS / 32;
 constexpr int NBB_MIN = 16;                 // x bins per bucket, fewest
 constexpr int NBB_MAX = 512;                // x bins per bucket, most
 constexpr int NBIN_MAX = NB * NBB_MAX;      // bins of an event, most
-constexpr int CHUNK = 20480;                // hits sorted together in shared memory
 constexpr int UNROLL = 4;                   // hits per thread with loads in flight together
 constexpr int ID_BITS = 27;                 // raw index inside the event; the bucket sits above
 constexpr uint32_t ID_MASK = (1u << ID_BITS) - 1u;
-static_assert(CHUNK >= BLOCK_SORT_MAX, "a sortable bucket must fit one chunk");
-static_assert(CHUNK <= 2 * (NBIN_MAX + 4), "the inverse map of one chunk fits the bins' area");
+constexpr int RANGE_SAMPLE = 1024;          // hits sampled for the event's x range
 
-// shared memory: bin counters / starts (NBIN_MAX + 1, padded), then x and
-// (bucket << ID_BITS | raw index) of a chunk's hits in bin order
-constexpr size_t BINS_BYTES = 4 * (size_t)(NBIN_MAX + 4);
-constexpr size_t AREA_BYTES = BINS_BYTES + (size_t)CHUNK * 8;
+// Shared memory: the bin counters / starts (nbin + 1 of them), then x and
+// (bucket << ID_BITS | raw index) of a chunk's hits in bin order.  An event of
+// at most 65535 hits keeps 16-bit bins (every start fits), which leaves room
+// for chunks of CHUNK_N hits; a larger event keeps 32-bit bins and chunks of
+// CHUNK_W hits.  Either layout fills AREA_BYTES.
+constexpr size_t BINS16_BYTES = 2 * (size_t)(NBIN_MAX + 8);
+constexpr size_t BINS32_BYTES = 4 * (size_t)(NBIN_MAX + 4);
+constexpr int CHUNK_N = 25856;
+constexpr int CHUNK_W = 22784;
+constexpr size_t AREA_BYTES = BINS16_BYTES + (size_t)CHUNK_N * 8;
+static_assert(BINS32_BYTES + (size_t)CHUNK_W * 8 <= AREA_BYTES, "wide layout fits");
+static_assert(CHUNK_W >= BLOCK_SORT_MAX, "a sortable bucket must fit one chunk");
+static_assert(CHUNK_N <= 65535, "positions of a one-piece event fit 16 bits");
 
 struct EvShared {
     unsigned red_mn[PACK_WARPS], red_mx[PACK_WARPS];
@@ -135,6 +142,27 @@ __device__ __forceinline__ void sort_bin2(float* xs, uint32_t* ks, int s, int e)
         ks[j + 1] = kv;
     }
 }
+// Bin counters of one event: 16-bit halves of 32-bit words (narrow) or
+// 32-bit words (wide); the halves never carry into each other because no
+// count or start of a narrow event exceeds 65535.
+struct Bins {
+    char* base;
+    bool wide;
+    __device__ __forceinline__ int get(int b) const {
+        return wide ? reinterpret_cast<const int*>(base)[b] : (int)reinterpret_cast<const uint16_t*>(base)[b];
+    }
+    __device__ __forceinline__ void set(int b, int v) const {
+        if (wide) reinterpret_cast<int*>(base)[b] = v;
+        else reinterpret_cast<uint16_t*>(base)[b] = (uint16_t)v;
+    }
+    // old value, then +1
+    __device__ __forceinline__ int add(int b) const {
+        if (wide) return atomicAdd(reinterpret_cast<int*>(base) + b, 1);
+        const unsigned old = atomicAdd(reinterpret_cast<unsigned*>(base) + (b >> 1), (b & 1) ? 0x10000u : 1u);
+        return (b & 1) ? (int)(old >> 16) : (int)(old & 0xffffu);
+    }
+};
+
 __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
     const int* __restrict__ raw_offsets, const float* __restrict__ x, const float* __restrict__ z,
     const float* __restrict__ dxdy, const float* __restrict__ w, const uint8_t* __restrict__ plane, int n_events,
@@ -142,9 +170,6 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
     int* status) {
     extern __shared__ __align__(16) char smem[];
     __shared__ EvShared sh;
-    int* bins = reinterpret_cast<int*>(smem);
-    float* xs = reinterpret_cast<float*>(smem + BINS_BYTES);
-    uint32_t* ks = reinterpret_cast<uint32_t*>(smem + BINS_BYTES + (size_t)CHUNK * 4);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (blockIdx.x == 0 && tid == 0) hit_offsets[(size_t)n_events * NB] = raw_offsets[n_events];
     if (tid == 0) sh.next = atomicAdd(cursor, 1);
@@ -184,23 +209,22 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
             for (int i = tid; i < n; i += PACK_THREADS) perm[(size_t)rb + i] = -1;
             continue;
         }
+        const Bins bins{smem, n > 65535};
+        const int chunk = bins.wide ? CHUNK_W : CHUNK_N;
+        float* xs = reinterpret_cast<float*>(smem + (bins.wide ? BINS32_BYTES : BINS16_BYTES));
+        uint32_t* ks = reinterpret_cast<uint32_t*>(xs + chunk);
 
-        // x range of the event
+        // x range of the event from a strided sample, widened by 1/128 of it
+        // on each side: it only shapes the bins (a hit outside it lands in an
+        // edge bin, which the ordering inside bins absorbs)
         unsigned mn = 0xffffffffu, mx = 0u;
-        for (int base = 0; base < n; base += PACK_THREADS * UNROLL) {
-            float xu[UNROLL];
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) {
-                const int i = base + u * PACK_THREADS + tid;
-                xu[u] = i < n ? x[rb + i] : 0.0f;
-            }
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) {
-                if (base + u * PACK_THREADS + tid < n) {
-                    const unsigned ov = ordered(xu[u] + 0.0f);
-                    mn = min(mn, ov);
-                    mx = max(mx, ov);
-                }
+        {
+            const int ns = n < RANGE_SAMPLE ? n : RANGE_SAMPLE;
+            const int stride = n / ns;
+            if (tid < ns) {
+                const unsigned ov = ordered(x[rb + tid * stride] + 0.0f);
+                mn = ov;
+                mx = ov;
             }
         }
         mn = __reduce_min_sync(FULL, mn);
@@ -213,16 +237,22 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
         int nbb = NBB_MIN;
         while (nbb < NBB_MAX && nbb * NB < n) nbb <<= 1;
         const int nbin = nbb * NB;
-        for (int b = tid; b <= nbin; b += PACK_THREADS) bins[b] = 0;
+        if (bins.wide) {
+            for (int b = tid; b <= nbin; b += PACK_THREADS) bins.set(b, 0);
+        } else {
+            for (int b = tid; b <= nbin / 2; b += PACK_THREADS) reinterpret_cast<unsigned*>(smem)[b] = 0u;
+        }
         __syncthreads();
         mn = sh.red_mn[lane];
         mx = sh.red_mx[lane];
         mn = __reduce_min_sync(FULL, mn);
         mx = __reduce_max_sync(FULL, mx);
-        float lo = 0.0f, scale = 0.0f;
-        if (n > 0) {
-            lo = unordered(mn);
-            const float hi = unordered(mx);
+        float lo, scale;
+        {
+            const float slo = unordered(mn), shi = unordered(mx);
+            const float pad = (shi - slo) * (1.0f / 128.0f);
+            lo = slo - pad;
+            const float hi = shi + pad;
             scale = hi > lo ? (float)nbb / (hi - lo) : 0.0f;
         }
 
@@ -245,18 +275,19 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
             for (int u = 0; u < UNROLL; ++u) {
                 if (pu[u] < 0) continue;
                 const int q = bucket_code(pu[u], bad);
-                atomicAdd(&bins[q * nbb + bin_of(xu[u] + 0.0f, lo, scale, nbb)], 1);
+                bins.add(q * nbb + bin_of(xu[u] + 0.0f, lo, scale, nbb));
             }
         }
         if (bad) atomicOr(status, LF_FLAG_PLANE_RANGE);
         __syncthreads();
 
         // exclusive scan of the nbin counters: thread tid owns a run of per
+        // (an even number, so a 16-bit pair has a single owner)
         {
-            const int per = (nbin + PACK_THREADS - 1) / PACK_THREADS;
+            const int per = 2 * ((nbin + 2 * PACK_THREADS - 1) / (2 * PACK_THREADS));
             const int s0 = min(tid * per, nbin), s1 = min(s0 + per, nbin);
             int sum = 0;
-            for (int b = s0; b < s1; ++b) sum += bins[b];
+            for (int b = s0; b < s1; ++b) sum += bins.get(b);
             const int inc = wscan_incl(sum, lane);
             if (lane == 31) sh.warp_tot[warp] = inc;
             __syncthreads();
@@ -264,19 +295,19 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
             const int winc = wscan_incl(wt, lane);
             int excl = inc - sum + __shfl_sync(FULL, winc - wt, warp);
             for (int b = s0; b < s1; ++b) {
-                const int c = bins[b];
-                bins[b] = excl;
+                const int c = bins.get(b);
+                bins.set(b, excl);
                 excl += c;
             }
-            if (tid == 0) bins[nbin] = n;
+            if (tid == 0) bins.set(nbin, n);
         }
         __syncthreads();
         if (tid <= NB) {
-            const int s = bins[tid * nbb];
+            const int s = bins.get(tid * nbb);
             sh.boff[tid] = s;
             if (tid < NB) {
                 hit_offsets[(size_t)e * NB + tid] = rb + s;
-                if (bins[(tid + 1) * nbb] - s > BLOCK_SORT_MAX) {
+                if (bins.get((tid + 1) * nbb) - s > BLOCK_SORT_MAX) {
                     atomicOr(&sh.flagged, 1u << tid);
                     atomicOr(status, LF_FLAG_BUCKET_OVERFLOW);
                 }
@@ -285,8 +316,8 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
         __syncthreads();
 
         const unsigned flagged = sh.flagged;
-        if (n <= CHUNK && flagged == 0u) {
-            // ---- the whole event in one chunk: placed straight into shared memory
+        if (n <= chunk && flagged == 0u) {
+            // ---- the whole event in one piece: placed straight into shared memory
             for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
                 int pu[UNROLL];
                 float xu[UNROLL];
@@ -307,7 +338,7 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
                     bool bb = false;
                     const int q = bucket_code(pu[u], bb);
                     const float xv = xu[u] + 0.0f;
-                    const int pos = atomicAdd(&bins[q * nbb + bin_of(xv, lo, scale, nbb)], 1);
+                    const int pos = bins.add(q * nbb + bin_of(xv, lo, scale, nbb));
                     xs[pos] = xv;
                     ks[pos] = ((uint32_t)q << ID_BITS) | (uint32_t)i;
                 }
@@ -315,23 +346,24 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
             __syncthreads();
             // bins[b] now holds the end of bin b; order each bin by (x, raw
             // index) (the bucket bits are equal inside a bin)
-            for (int b = tid; b < nbin; b += PACK_THREADS)
-                sort_bin2(xs, ks, b == 0 ? 0 : bins[b - 1], bins[b]);
+            for (int b = tid; b < nbin; b += PACK_THREADS) sort_bin2(xs, ks, b == 0 ? 0 : bins.get(b - 1), bins.get(b));
             __syncthreads();
-            // x, layer and perm straight from shared memory, and the inverse map
-            // (raw index -> position) over the bins' area, free now
+            // x, layer and perm straight from shared memory
             const size_t o0 = (size_t)rb;
-            uint16_t* inv = reinterpret_cast<uint16_t*>(bins);
             for (int j = tid; j < n; j += PACK_THREADS) {
                 const uint32_t k = ks[j];
                 ox[o0 + j] = xs[j];
                 ol[o0 + j] = (uint8_t)((k >> ID_BITS) % NL);
                 perm[o0 + j] = rb + (int)(k & ID_MASK);
-                inv[k & ID_MASK] = (uint16_t)j;
             }
             __syncthreads();
+            // the inverse map (raw index -> position) over x's area
+            uint16_t* inv = reinterpret_cast<uint16_t*>(xs);
+            for (int j = tid; j < n; j += PACK_THREADS) inv[ks[j] & ID_MASK] = (uint16_t)j;
+            __syncthreads();
             // z, dxdy and w: coalesced reads of the raw arrays, transposed
-            // through shared memory (x's area), coalesced writes
+            // through shared memory (the keys' area), coalesced writes
+            float* tmp = reinterpret_cast<float*>(ks);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const float* src = a == 0 ? z : (a == 1 ? dxdy : w);
@@ -346,19 +378,19 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
 #pragma unroll
                     for (int u = 0; u < UNROLL; ++u) {
                         const int i = ib + u * PACK_THREADS + tid;
-                        if (i < n) xs[inv[i]] = v[u];
+                        if (i < n) tmp[inv[i]] = v[u];
                     }
                 }
                 __syncthreads();
-                for (int j = tid; j < n; j += PACK_THREADS) dst[o0 + j] = xs[j];
+                for (int j = tid; j < n; j += PACK_THREADS) dst[o0 + j] = tmp[j];
                 __syncthreads();
             }
             continue;
         }
 
         // ---- a larger event (or one with a flagged bucket): chunks of
-        // consecutive bins of at most CHUNK hits; per chunk one pass over the
-        // raw hits places the chunk's hits in shared memory, and after the
+        // consecutive bins of at most `chunk` hits; per chunk one pass over
+        // the raw hits places the chunk's hits in shared memory, and after the
         // ordering and the x, layer and perm writes, a second pass reads the
         // payload coalesced and stores each hit's z, dxdy and w at its position
         int b0 = 0;
@@ -378,25 +410,25 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
                 b0 = (q0 + 1) * nbb;
                 continue;
             }
-            const int base = bins[b0];
+            const int base = bins.get(b0);
             if (tid == 0) {
                 // the chunk stops before the next flagged bucket
                 int limit = nbin;
                 const unsigned later = flagged & ~((2u << q0) - 1u);
                 if (later) limit = (__ffs(later) - 1) * nbb;
-                // largest b1 in (b0, limit] with bins[b1] - base <= CHUNK (bins
+                // largest b1 in (b0, limit] with bins[b1] - base <= chunk (bins
                 // past b0 still hold their starts, monotone in b; a single bin
                 // of an unflagged bucket always fits)
                 int l = b0 + 1, h = limit;
                 while (l < h) {
                     const int m = (l + h + 1) >> 1;
-                    if (bins[m] - base <= CHUNK) l = m; else h = m - 1;
+                    if (bins.get(m) - base <= chunk) l = m; else h = m - 1;
                 }
                 sh.b1 = l;
             }
             __syncthreads();
             const int b1 = sh.b1;
-            const int tot = bins[b1] - base;
+            const int tot = bins.get(b1) - base;
             __syncthreads();   // every thread has read bins[b0], bins[b1]
             for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
                 int pu[UNROLL];
@@ -420,7 +452,7 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
                     const float xv = xu[u] + 0.0f;
                     const int b = q * nbb + bin_of(xv, lo, scale, nbb);
                     if (b >= b0 && b < b1) {
-                        const int pos = atomicAdd(&bins[b], 1) - base;
+                        const int pos = bins.add(b) - base;
                         xs[pos] = xv;
                         ks[pos] = ((uint32_t)q << ID_BITS) | (uint32_t)i;
                     }
@@ -429,7 +461,7 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
             __syncthreads();
             // bins[b] now holds the end of bin b for b in [b0, b1)
             for (int b = b0 + tid; b < b1; b += PACK_THREADS)
-                sort_bin2(xs, ks, (b == b0 ? base : bins[b - 1]) - base, bins[b] - base);
+                sort_bin2(xs, ks, (b == b0 ? base : bins.get(b - 1)) - base, bins.get(b) - base);
             __syncthreads();
             const size_t o0 = (size_t)rb + base;
             for (int j = tid; j < tot; j += PACK_THREADS) {
@@ -463,8 +495,8 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
                     const int b = q * nbb + bin_of(xu[u] + 0.0f, lo, scale, nbb);
                     if (b < b0 || b >= b1) continue;
                     const uint32_t key = ((uint32_t)q << ID_BITS) | (uint32_t)i;
-                    const int en = bins[b] - base;
-                    int j = (b == b0 ? base : bins[b - 1]) - base;
+                    const int en = bins.get(b) - base;
+                    int j = (b == b0 ? base : bins.get(b - 1)) - base;
                     while (j < en && ks[j] != key) ++j;
                     if (j < en) {
                         oz[o0 + j] = zu[u];
