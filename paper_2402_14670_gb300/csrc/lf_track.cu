@@ -8,7 +8,10 @@
 // together, and the extension runs two tracks per warp).
 //
 //   windows    Sec. "Defining the search windows": lanes 0..11 each open one
-//              layer's window with binary searches in the x-sorted bucket.
+//              layer's window with binary searches in the x-sorted bucket
+//              (lanes 12..23 the upper bounds, in the same loop); the
+//              persistent kernel runs two tracks per warp with their
+//              searches interleaved, so twice the loads are in flight.
 //   staging    x and z of the window hits (<= n_hits_window per layer) are
 //              copied into the track's shared-memory slot, once per track;
 //              dxdy and w are read from L2 for the hits a candidate uses.
@@ -81,22 +84,34 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
     return v;
 }
 
-// first index in [lo, hi) with x >= v
-__device__ __forceinline__ int lb_global(const float* __restrict__ x, int lo, int hi, float v) {
+// first index in [lo, hi) whose x is not left of v: left means x < v (lower
+// bound, upper = false) or !(x > v) (upper bound, upper = true); one loop for
+// both, so lanes searching lower and upper bounds do not diverge
+__device__ __forceinline__ int bound_global(const float* __restrict__ x, int lo, int hi, float v, bool upper) {
     while (lo < hi) {
-        int mid = lo + ((hi - lo) >> 1);
-        if (__ldg(x + mid) < v) lo = mid + 1; else hi = mid;
+        const int mid = lo + ((hi - lo) >> 1);
+        const float xm = __ldg(x + mid);
+        if (upper ? !(xm > v) : (xm < v)) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
-// first index in [lo, hi) with x > v
-__device__ __forceinline__ int ub_global(const float* __restrict__ x, int lo, int hi, float v) {
-    while (lo < hi) {
-        int mid = lo + ((hi - lo) >> 1);
-        if (!(__ldg(x + mid) > v)) lo = mid + 1; else hi = mid;
+// two independent bound searches in lockstep (more loads in flight per lane)
+__device__ __forceinline__ void bound2_global(const float* __restrict__ x, int& lo0, int hi0, float v0, int& lo1,
+                                              int hi1, float v1, bool upper) {
+    while (lo0 < hi0 || lo1 < hi1) {
+        const bool a0 = lo0 < hi0, a1 = lo1 < hi1;
+        const int m0 = lo0 + ((hi0 - lo0) >> 1), m1 = lo1 + ((hi1 - lo1) >> 1);
+        const float x0 = a0 ? __ldg(x + m0) : 0.0f;
+        const float x1 = a1 ? __ldg(x + m1) : 0.0f;
+        if (a0) {
+            if (upper ? !(x0 > v0) : (x0 < v0)) lo0 = m0 + 1; else hi0 = m0;
+        }
+        if (a1) {
+            if (upper ? !(x1 > v1) : (x1 < v1)) lo1 = m1 + 1; else hi1 = m1;
+        }
     }
-    return lo;
 }
+// first index in [0, n) of a window in shared memory with x >= v
 __device__ __forceinline__ int lb_smem(const float* x, int n, float v) {
     int lo = 0, hi = n;
     while (lo < hi) {
@@ -105,6 +120,7 @@ __device__ __forceinline__ int lb_smem(const float* x, int n, float v) {
     }
     return lo;
 }
+// first index in [0, n) with x > v
 __device__ __forceinline__ int ub_smem(const float* x, int n, float v) {
     int lo = 0, hi = n;
     while (lo < hi) {
@@ -225,8 +241,7 @@ __device__ __forceinline__ void warp_windows(const KParams& k, const KBatch& b, 
     const int* off = b.hit_offsets + (size_t)e * NB + zone * NL + l;
     const int bb = __ldg(off), be = __ldg(off + 1);
     int v = 0;
-    if (lane < NL) v = lb_global(b.x, bb, be, xmin);
-    else if (lane < 2 * NL) v = ub_global(b.x, bb, be, xmax);
+    if (lane < 2 * NL) v = bound_global(b.x, bb, be, lane < NL ? xmin : xmax, lane >= NL);
     int hi = __shfl_sync(FULL, v, (lane + NL) & 31);
     begin = 0;
     count = 0;
@@ -235,7 +250,7 @@ __device__ __forceinline__ void warp_windows(const KParams& k, const KBatch& b, 
         if (hi < lo) hi = lo;
         int cnt = hi - lo, start = lo;
         if (cnt > k.cap) {
-            int c = lb_global(b.x, lo, hi, centre);
+            int c = bound_global(b.x, lo, hi, centre, false);
             start = c - k.cap / 2;
             if (start > hi - k.cap) start = hi - k.cap;
             if (start < lo) start = lo;
@@ -860,6 +875,58 @@ __device__ __forceinline__ void windows_track(const KParams& k, const KBatch& b,
     }
 }
 
+// windows of tracks t0 and t0 + 1 (if it exists) with interleaved searches
+__device__ __forceinline__ void windows_track2(const KParams& k, const KBatch& b, const int* __restrict__ trk_event,
+                                               int* wbeg, uint8_t* wcnt, int t0, int lane) {
+    const bool has1 = t0 + 1 < b.n_tracks;
+    const TState s0 = load_state(b, t0);
+    const TState s1 = has1 ? load_state(b, t0 + 1) : s0;
+    const int e0 = __ldg(trk_event + t0), e1 = has1 ? __ldg(trk_event + t0 + 1) : e0;
+    const int l = lane < NL ? lane : (lane < 2 * NL ? lane - NL : 0);
+    float xmin0, xmax0, c0, xmin1, xmax1, c1;
+    window_limits<false>(k, s0, l, 0, xmin0, xmax0, c0);
+    window_limits<false>(k, s1, l, 0, xmin1, xmax1, c1);
+    const int* off0 = b.hit_offsets + (size_t)e0 * NB + ((s0.tys >= 0.0f) ? 1 : 0) * NL + l;
+    const int* off1 = b.hit_offsets + (size_t)e1 * NB + ((s1.tys >= 0.0f) ? 1 : 0) * NL + l;
+    int v0 = 0, v1 = 0;
+    if (lane < 2 * NL) {
+        v0 = __ldg(off0);
+        v1 = has1 ? __ldg(off1) : 0;
+        const int h0 = __ldg(off0 + 1), h1 = has1 ? __ldg(off1 + 1) : 0;
+        const bool up = lane >= NL;
+        bound2_global(b.x, v0, h0, up ? xmax0 : xmin0, v1, h1, up ? xmax1 : xmin1, up);
+    }
+    int hi0 = __shfl_sync(FULL, v0, (lane + NL) & 31), hi1 = __shfl_sync(FULL, v1, (lane + NL) & 31);
+    if (lane < NL) {
+        const int lo0 = v0, lo1 = v1;
+        if (hi0 < lo0) hi0 = lo0;
+        if (hi1 < lo1) hi1 = lo1;
+        // the capped windows' centre searches, together
+        int cc0 = lo0, cc1 = lo1;
+        const bool cap0 = hi0 - lo0 > k.cap, cap1 = has1 && hi1 - lo1 > k.cap;
+        bound2_global(b.x, cc0, cap0 ? hi0 : lo0, c0, cc1, cap1 ? hi1 : lo1, c1, false);
+        int st0 = lo0, n0 = hi0 - lo0, st1 = lo1, n1 = hi1 - lo1;
+        if (cap0) {
+            st0 = cc0 - k.cap / 2;
+            if (st0 > hi0 - k.cap) st0 = hi0 - k.cap;
+            if (st0 < lo0) st0 = lo0;
+            n0 = k.cap;
+        }
+        if (cap1) {
+            st1 = cc1 - k.cap / 2;
+            if (st1 > hi1 - k.cap) st1 = hi1 - k.cap;
+            if (st1 < lo1) st1 = lo1;
+            n1 = k.cap;
+        }
+        wbeg[(size_t)t0 * NL + lane] = st0;
+        wcnt[(size_t)t0 * NL + lane] = (uint8_t)n0;
+        if (has1) {
+            wbeg[(size_t)(t0 + 1) * NL + lane] = st1;
+            wcnt[(size_t)(t0 + 1) * NL + lane] = (uint8_t)n1;
+        }
+    }
+}
+
 // stage 1: windows (warp per track)
 template <bool P, bool NOUT>
 __global__ void k_windows(KParams k, KBatch b, const int* __restrict__ trk_event, int* wbeg, uint8_t* wcnt,
@@ -868,6 +935,14 @@ __global__ void k_windows(KParams k, KBatch b, const int* __restrict__ trk_event
     if (!P) {
         const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         if (t < b.n_tracks) windows_track<NOUT>(k, b, trk_event, wbeg, wcnt, t, lane);
+        return;
+    }
+    if (!NOUT) {
+        for (;;) {
+            const int t0 = queue_take(cursor, 2, lane);
+            if (t0 >= b.n_tracks) break;
+            windows_track2(k, b, trk_event, wbeg, wcnt, t0, lane);
+        }
         return;
     }
     for (;;) {
