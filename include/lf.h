@@ -231,6 +231,14 @@ typedef struct {
     uint8_t* found; uint8_t* nhits; int32_t* hit_idx; float* state; float* quality;
 } lf_host_output;
 
+/* Size the context's scratch for persistent-form batches of up to n_events
+ * events and n_tracks input tracks (with this tuning; NULL for the defaults),
+ * so that later calls within those sizes allocate nothing.  Growing scratch
+ * inside a call frees and reallocates device memory, and cudaFree
+ * synchronises the whole device, so a serving loop reserves once at start.
+ * LF_ERR_OOM when the allocation fails. */
+lf_status lf_reserve(lf_ctx* ctx, int32_t n_events, int32_t n_tracks, const lf_tuning* tuning);
+
 /* Page-locked host memory of exactly `bytes` bytes (cudaHostAlloc, portable
  * across devices) for the host-side buffers of lf_process_host and of a
  * serving loop: copies from it run asynchronously and overlap device work.

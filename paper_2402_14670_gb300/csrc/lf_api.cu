@@ -519,6 +519,17 @@ lf_status lf_sync_status(lf_ctx* c, void* stream, int32_t* flags) {
     return LF_OK;
 }
 
+lf_status lf_reserve(lf_ctx* c, int32_t n_events, int32_t n_tracks, const lf_tuning* tuning) {
+    if (!c) return LF_ERR_ARG;
+    if (n_events < 0 || n_tracks < 0) return fail(c, LF_ERR_ARG, "negative size");
+    Shape sh;
+    lf_status st;
+    if ((st = resolve_shape(c, tuning, sh)) != LF_OK) return st;
+    lf_batch big{n_events, 0, n_tracks, nullptr, nullptr, nullptr, nullptr, nullptr,
+                 nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    return prepare_batched(c, &big, sh);
+}
+
 lf_status lf_host_alloc(size_t bytes, void** out) {
     if (!out) return LF_ERR_ARG;
     *out = nullptr;

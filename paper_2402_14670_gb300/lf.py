@@ -113,6 +113,8 @@ _lib.lf_process_host.restype = C.c_int
 _lib.lf_find_tracks_static.argtypes = [C.POINTER(lf_geometry), C.POINTER(lf_params), C.POINTER(lf_batch),
                                        C.POINTER(lf_output), _P]
 _lib.lf_find_tracks_static.restype = C.c_int
+_lib.lf_reserve.argtypes = [_P, C.c_int32, C.c_int32, C.POINTER(lf_tuning)]
+_lib.lf_reserve.restype = C.c_int
 _lib.lf_host_alloc.argtypes = [C.c_size_t, C.POINTER(_P)]
 _lib.lf_host_alloc.restype = C.c_int
 _lib.lf_host_free.argtypes = [_P]
@@ -120,7 +122,7 @@ _lib.lf_host_free.restype = None
 
 EXPORTED = ["lf_create", "lf_destroy", "lf_last_error", "lf_device_sm_count", "lf_pack_hits", "lf_find_tracks",
             "lf_find_tracks_batched", "lf_debug_stages", "lf_sync_status", "lf_process_host",
-            "lf_find_tracks_static", "lf_host_alloc", "lf_host_free"]
+            "lf_find_tracks_static", "lf_host_alloc", "lf_host_free", "lf_reserve"]
 
 
 class LFError(RuntimeError):
@@ -219,6 +221,10 @@ def lf_last_error(ctx) -> str:
 
 def lf_device_sm_count() -> int:
     return int(_lib.lf_device_sm_count())
+
+
+def lf_reserve(ctx, n_events: int, n_tracks: int, tuning: Optional["lf_tuning"] = None) -> None:
+    _check(ctx, _lib.lf_reserve(ctx, int(n_events), int(n_tracks), C.byref(tuning) if tuning else None))
 
 
 def lf_host_alloc(nbytes: int) -> int:
@@ -412,6 +418,14 @@ class Tracker:
 
     def status(self, stream=None) -> int:
         return lf_sync_status(self.ctx, _stream(stream))
+
+    def reserve(self, n_events: int, n_tracks: int, tuning: Optional[dict] = None) -> None:
+        """Size the persistent form's scratch for batches up to these sizes."""
+        tu = None
+        if tuning:
+            tu = lf_tuning(int(tuning.get("warps_per_block", 0)), int(tuning.get("blocks_per_sm", 0)),
+                           int(tuning.get("grain", 0)), int(tuning.get("queue", 0)))
+        lf_reserve(self.ctx, n_events, n_tracks, tu)
 
     @staticmethod
     def _hptr(t: torch.Tensor):

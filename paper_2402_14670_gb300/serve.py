@@ -11,7 +11,11 @@ capacity); its copies in are queued on the first stream, its pack and find
 bucket) on the compute stream after them, and the copies of its per-track
 results on the third stream after the compute, chained by events.  So the
 copies in of one batch, the compute of another and the copies out of a third
-overlap on the device.  A batch is
+overlap on the device.
+
+The pool may also be device-resident (events that arrive straight in GPU
+memory, as from a network card writing to it): batches are then views of the
+pool, no copies in are made, and only the per-track results leave the device.  A batch is
 admitted only while the device bytes of the batches in flight stay within the
 memory budget.  Latency is measured per event from its arrival time to the
 moment the server sees its batch complete with results in host memory.
@@ -56,6 +60,9 @@ class ServeStats:
 class _Slot:
     def __init__(self, max_events: int, max_hits: int, max_tracks: int, geometry, params, dev):
         self.tr = lf.Tracker(geometry, params)
+        # scratch sized once: growing it mid-stream would free device memory,
+        # which synchronises the device
+        self.tr.reserve(max_events, max_tracks)
         e = lambda n, dt: torch.empty(n, dtype=dt, device=dev)
         self.raw = dict(x=e(max_hits, torch.float32), z=e(max_hits, torch.float32), dxdy=e(max_hits, torch.float32),
                         w=e(max_hits, torch.float32), plane=e(max_hits, torch.uint8),
@@ -96,8 +103,9 @@ class Server:
                  keep_results: bool = False, device: str = "cuda"):
         self.pool = pool
         self.dev = torch.device(device)
-        self.ro = pool.raw_offsets.numpy().astype(np.int64)
-        self.to = pool.trk_offsets.numpy().astype(np.int64)
+        self.device_pool = pool.x.is_cuda
+        self.ro = pool.raw_offsets.cpu().numpy().astype(np.int64)
+        self.to = pool.trk_offsets.cpu().numpy().astype(np.int64)
         self.budget = int(budget_bytes)
         free, _ = torch.cuda.mem_get_info(self.dev)
         nh = np.diff(self.ro)
@@ -147,27 +155,36 @@ class Server:
         e0, e1, h0, h1, t0, t1, nbytes = batch
         ne, nh, nt = e1 - e0, h1 - h0, t1 - t0
         p = self.pool
-        s.h_ro[:ne + 1].copy_(torch.from_numpy((self.ro[e0:e1 + 1] - h0).astype(np.int32)))
-        s.h_to[:ne + 1].copy_(torch.from_numpy((self.to[e0:e1 + 1] - t0).astype(np.int32)))
-        # a slot is launched only when its previous batch has completed, so
-        # its buffers are free
-        with torch.cuda.stream(self.s_in):
-            for f in ("x", "z", "dxdy", "w", "plane"):
-                s.raw[f][:nh].copy_(getattr(p, f)[h0:h1], non_blocking=True)
-            s.raw["raw_offsets"][:ne + 1].copy_(s.h_ro[:ne + 1], non_blocking=True)
-            s.st["trk_offsets"][:ne + 1].copy_(s.h_to[:ne + 1], non_blocking=True)
-            for f in ("sx", "sy", "stx", "sty", "sqop"):
-                s.st[f][:nt].copy_(getattr(p, f)[t0:t1], non_blocking=True)
-            s.ev_in.record(self.s_in)
+        if self.device_pool:
+            # the events are in device memory already: the batch is a view of
+            # the pool, with its offsets rebased on the device
+            with torch.cuda.stream(self.s_in):
+                torch.sub(p.raw_offsets[e0:e1 + 1], p.raw_offsets[e0:e0 + 1], out=s.raw["raw_offsets"][:ne + 1])
+                torch.sub(p.trk_offsets[e0:e1 + 1], p.trk_offsets[e0:e0 + 1], out=s.st["trk_offsets"][:ne + 1])
+                s.ev_in.record(self.s_in)
+            src_h = {f: getattr(p, f)[h0:h1] for f in ("x", "z", "dxdy", "w", "plane")}
+            src_t = {f: getattr(p, f)[t0:t1] for f in ("sx", "sy", "stx", "sty", "sqop")}
+        else:
+            s.h_ro[:ne + 1].copy_(torch.from_numpy((self.ro[e0:e1 + 1] - h0).astype(np.int32)))
+            s.h_to[:ne + 1].copy_(torch.from_numpy((self.to[e0:e1 + 1] - t0).astype(np.int32)))
+            # a slot is launched only when its previous batch has completed, so
+            # its buffers are free
+            with torch.cuda.stream(self.s_in):
+                for f in ("x", "z", "dxdy", "w", "plane"):
+                    s.raw[f][:nh].copy_(getattr(p, f)[h0:h1], non_blocking=True)
+                s.raw["raw_offsets"][:ne + 1].copy_(s.h_ro[:ne + 1], non_blocking=True)
+                s.st["trk_offsets"][:ne + 1].copy_(s.h_to[:ne + 1], non_blocking=True)
+                for f in ("sx", "sy", "stx", "sty", "sqop"):
+                    s.st[f][:nt].copy_(getattr(p, f)[t0:t1], non_blocking=True)
+                s.ev_in.record(self.s_in)
+            src_h = {f: s.raw[f][:nh] for f in ("x", "z", "dxdy", "w", "plane")}
+            src_t = {f: s.st[f][:nt] for f in ("sx", "sy", "stx", "sty", "sqop")}
         self.s_comp.wait_event(s.ev_in)
         with torch.cuda.stream(self.s_comp):
-            raw = SimpleNamespace(n_events=ne, raw_offsets=s.raw["raw_offsets"][:ne + 1], x=s.raw["x"][:nh],
-                                  z=s.raw["z"][:nh], dxdy=s.raw["dxdy"][:nh], w=s.raw["w"][:nh],
-                                  plane=s.raw["plane"][:nh])
+            raw = SimpleNamespace(n_events=ne, raw_offsets=s.raw["raw_offsets"][:ne + 1], **src_h)
             pk = {k: (v[:24 * ne + 1] if k == "hit_offsets" else v[:nh]) for k, v in s.packed.items()}
             s.tr.pack(raw, self.s_comp, out=pk)
-            st = SimpleNamespace(trk_offsets=s.st["trk_offsets"][:ne + 1], sx=s.st["sx"][:nt], sy=s.st["sy"][:nt],
-                                 stx=s.st["stx"][:nt], sty=s.st["sty"][:nt], sqop=s.st["sqop"][:nt])
+            st = SimpleNamespace(trk_offsets=s.st["trk_offsets"][:ne + 1], **src_t)
             out = {k: v for k, v in s.out.items()}
             for k in ("found", "nhits", "hit_idx", "state", "quality"):
                 out[k] = s.out[k][:nt]

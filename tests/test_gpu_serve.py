@@ -76,3 +76,20 @@ def test_admission_budget_limits_inflight(mods):
     srv.close()
     assert st.n_events == 64
     assert st.max_inflight_bytes <= max(budget, 0) or st.n_batches >= 4
+
+
+def test_device_resident_pool_matches_host_pool(mods):
+    """Events already in device memory (batches are views of the pool) give
+    the same per-event results as events copied in from host memory."""
+    lf, serve = mods
+    pool = synth.generate(1, n_events=80)
+    res = []
+    for p in (pool.pin_memory(), pool.to("cuda")):
+        srv = serve.Server(p, n_slots=3, max_events=24, keep_results=True, budget_bytes=4 << 30)
+        st = srv.run(np.zeros(80))
+        assert st.n_events == 80 and st.mean_batch_events > 8
+        res.append(dict(srv.results))
+        srv.close()
+    assert len(res[0]) == len(res[1]) == 80
+    for e in range(80):
+        _same(res[0][e], res[1][e])
