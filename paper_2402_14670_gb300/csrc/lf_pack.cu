@@ -19,22 +19,26 @@
 //            the result is the exact (bucket, x, raw index) order whatever
 //            the data (a skewed x distribution costs time, never exactness);
 //   write    x, layer and perm leave coalesced.
-// An event of at most CHUNK hits is placed straight into shared memory; its
-// z, dxdy and w are then read coalesced from the raw arrays (prefetched into
-// L2 when the event was taken) and transposed through shared memory with an
-// inverse map (raw index -> position), one array at a time.  A larger event
-// is sorted in chunks of consecutive bins of at most CHUNK hits: per chunk a
-// pass over the raw hits places the chunk's hits in shared memory, and after
-// the ordering a second pass reads the payload coalesced and stores each of
-// the chunk's hits' z, dxdy and w at its position.  (Staging a larger event
-// once through its output range instead costs five scattered 4-byte stores
-// per hit, which measured slower than the repeated coalesced passes.)
+// An event of at most CHUNK_N hits is placed straight into shared memory as
+// (x, 16-bit raw index), 6 bytes per hit; its z, dxdy and w are then read
+// coalesced from the raw arrays (prefetched into L2 when the event was taken)
+// into shared memory, one array at a time, and written in sorted order,
+// gathered by raw index.  A larger event is sorted in chunks of consecutive
+// bins: per chunk a pass over the raw hits places the chunk's hits in shared
+// memory, and after the ordering a second pass reads the payload coalesced and
+// stores each of the chunk's hits' z, dxdy and w at its position inside its
+// bin.  (Staging a larger event once through its output range instead costs
+// five scattered 4-byte stores per hit, which measured slower than the
+// repeated coalesced passes.)  An event above 65535 hits uses 32-bit bins and
+// indices.  The layer of an output position is the bucket whose offsets
+// contain it.
 // While an event is processed, the block has already taken its next event
 // from the queue and prefetched that event's plane codes and x into L2.
 // A bucket above LF_MAX_BUCKET hits is not sorted: it is flagged (status bit
 // 0x1), its perm entries are set to -1 and its other outputs to 0; a plane
 // code >= 24 is flagged (0x2) and counted in the last bucket.
 #include <cstdint>
+#include <type_traits>
 
 #include "lf.h"
 #include "lf_internal.h"
@@ -50,23 +54,23 @@ constexpr int NBB_MIN = 16;                 // x bins per bucket, fewest
 constexpr int NBB_MAX = 512;                // x bins per bucket, most
 constexpr int NBIN_MAX = NB * NBB_MAX;      // bins of an event, most
 constexpr int UNROLL = 4;                   // hits per thread with loads in flight together
-constexpr int ID_BITS = 27;                 // raw index inside the event; the bucket sits above
-constexpr uint32_t ID_MASK = (1u << ID_BITS) - 1u;
+constexpr uint32_t ID_MASK = (1u << 27) - 1u;  // largest event (hits) the pack sorts
 constexpr int RANGE_SAMPLE = 1024;          // hits sampled for the event's x range
 
-// Shared memory: the bin counters / starts (nbin + 1 of them), then x and
-// (bucket << ID_BITS | raw index) of a chunk's hits in bin order.  An event of
-// at most 65535 hits keeps 16-bit bins (every start fits), which leaves room
-// for chunks of CHUNK_N hits; a larger event keeps 32-bit bins and chunks of
-// CHUNK_W hits.  Either layout fills AREA_BYTES.
+// Shared memory: the bin counters / starts (nbin + 1 of them), then x and the
+// raw index (inside the event) of a chunk's hits in bin order.  An event of at
+// most 65535 hits keeps 16-bit bins and 16-bit raw indices (6 B per hit),
+// which leaves room to sort CHUNK_N hits at once; a larger event keeps 32-bit
+// bins and indices and chunks of CHUNK_W hits.  Either layout fits AREA_BYTES.
 constexpr size_t BINS16_BYTES = 2 * (size_t)(NBIN_MAX + 8);
 constexpr size_t BINS32_BYTES = 4 * (size_t)(NBIN_MAX + 4);
-constexpr int CHUNK_N = 25856;
-constexpr int CHUNK_W = 22784;
-constexpr size_t AREA_BYTES = BINS16_BYTES + (size_t)CHUNK_N * 8;
+constexpr int CHUNK_N = 34432;
+constexpr int CHUNK_W = 22752;
+constexpr size_t AREA_BYTES = BINS16_BYTES + (size_t)CHUNK_N * 6;
 static_assert(BINS32_BYTES + (size_t)CHUNK_W * 8 <= AREA_BYTES, "wide layout fits");
 static_assert(CHUNK_W >= BLOCK_SORT_MAX, "a sortable bucket must fit one chunk");
-static_assert(CHUNK_N <= 65535, "positions of a one-piece event fit 16 bits");
+static_assert(CHUNK_N <= 65535, "positions and raw indices of a narrow event fit 16 bits");
+static_assert((CHUNK_N * 4) % 16 == 0, "the index area stays aligned");
 
 struct EvShared {
     unsigned red_mn[PACK_WARPS], red_mx[PACK_WARPS];
@@ -123,16 +127,17 @@ __device__ __forceinline__ int bucket_code(int p, bool& bad) {
     return p;
 }
 
-// insertion sort of the bin [s, e) by (x, key) (keys of one bin share their
-// bucket bits, so key order is raw-index order)
-__device__ __forceinline__ void sort_bin2(float* xs, uint32_t* ks, int s, int e) {
+// insertion sort of the bin [s, e) by (x, raw index) (the hits of one bin
+// share their bucket)
+template <typename K>
+__device__ __forceinline__ void sort_bin(float* xs, K* ks, int s, int e) {
     for (int i = s + 1; i < e; ++i) {
         const float xv = xs[i];
-        const uint32_t kv = ks[i];
+        const K kv = ks[i];
         int j = i - 1;
         while (j >= s) {
             const float xj = xs[j];
-            const uint32_t kj = ks[j];
+            const K kj = ks[j];
             if (!(xv < xj || (xv == xj && kv < kj))) break;
             xs[j + 1] = xj;
             ks[j + 1] = kj;
@@ -142,26 +147,357 @@ __device__ __forceinline__ void sort_bin2(float* xs, uint32_t* ks, int s, int e)
         ks[j + 1] = kv;
     }
 }
-// Bin counters of one event: 16-bit halves of 32-bit words (narrow) or
-// 32-bit words (wide); the halves never carry into each other because no
-// count or start of a narrow event exceeds 65535.
+
+// bucket of event position j: the last q with boff[q] <= j (an empty bucket
+// shares its offset with the next one)
+__device__ __forceinline__ int bucket_at(const int* boff, int j) {
+    int lo = 0, hi = NB - 1;
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {   // 2^5 >= 24 buckets
+        const int mid = (lo + hi + 1) >> 1;
+        if (lo < hi) {
+            if (boff[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+    }
+    return lo;
+}
+
+// Bin counters of one event: 16-bit halves of 32-bit words (WIDE = false) or
+// 32-bit words; the halves never carry into each other because no count or
+// start of a narrow event exceeds 65535.
+template <bool WIDE>
 struct Bins {
     char* base;
-    bool wide;
     __device__ __forceinline__ int get(int b) const {
-        return wide ? reinterpret_cast<const int*>(base)[b] : (int)reinterpret_cast<const uint16_t*>(base)[b];
+        return WIDE ? reinterpret_cast<const int*>(base)[b] : (int)reinterpret_cast<const uint16_t*>(base)[b];
     }
     __device__ __forceinline__ void set(int b, int v) const {
-        if (wide) reinterpret_cast<int*>(base)[b] = v;
+        if (WIDE) reinterpret_cast<int*>(base)[b] = v;
         else reinterpret_cast<uint16_t*>(base)[b] = (uint16_t)v;
     }
     // old value, then +1
     __device__ __forceinline__ int add(int b) const {
-        if (wide) return atomicAdd(reinterpret_cast<int*>(base) + b, 1);
+        if (WIDE) return atomicAdd(reinterpret_cast<int*>(base) + b, 1);
         const unsigned old = atomicAdd(reinterpret_cast<unsigned*>(base) + (b >> 1), (b & 1) ? 0x10000u : 1u);
         return (b & 1) ? (int)(old >> 16) : (int)(old & 0xffffu);
     }
+    __device__ __forceinline__ void clear(int nbin, int tid) const {
+        if (WIDE) {
+            for (int b = tid; b <= nbin; b += PACK_THREADS) set(b, 0);
+        } else {
+            for (int b = tid; b <= nbin / 2; b += PACK_THREADS) reinterpret_cast<unsigned*>(base)[b] = 0u;
+        }
+    }
 };
+
+struct PackIO {
+    const float* __restrict__ x;
+    const float* __restrict__ z;
+    const float* __restrict__ dxdy;
+    const float* __restrict__ w;
+    const uint8_t* __restrict__ plane;
+    int* hit_offsets;
+    float *ox, *oz, *od, *ow;
+    uint8_t* ol;
+    int* perm;
+    int* status;
+};
+
+// Sort one event of n >= 1 hits starting at raw index rb (event e).
+template <bool WIDE>
+__device__ __forceinline__ void sort_event(const PackIO& io, EvShared& sh, char* smem, int e, int rb, int n,
+                                           int tid, int lane, int warp) {
+    using K = typename std::conditional<WIDE, uint32_t, uint16_t>::type;
+    const Bins<WIDE> bins{smem};
+    constexpr int chunk = WIDE ? CHUNK_W : CHUNK_N;
+    float* xs = reinterpret_cast<float*>(smem + (WIDE ? BINS32_BYTES : BINS16_BYTES));
+    K* ks = reinterpret_cast<K*>(xs + chunk);
+    const float* __restrict__ x = io.x;
+    const uint8_t* __restrict__ plane = io.plane;
+
+    // x range of the event from a strided sample, widened by 1/128 of it on
+    // each side: it only shapes the bins (a hit outside it lands in an edge
+    // bin, which the ordering inside bins absorbs)
+    unsigned mn = 0xffffffffu, mx = 0u;
+    {
+        const int ns = n < RANGE_SAMPLE ? n : RANGE_SAMPLE;
+        const int stride = n / ns;
+        if (tid < ns) {
+            const unsigned ov = ordered(x[rb + tid * stride] + 0.0f);
+            mn = ov;
+            mx = ov;
+        }
+    }
+    mn = __reduce_min_sync(FULL, mn);
+    mx = __reduce_max_sync(FULL, mx);
+    if (lane == 0) {
+        sh.red_mn[warp] = mn;
+        sh.red_mx[warp] = mx;
+    }
+    // bins per bucket: a power of two near n / 24
+    int nbb = NBB_MIN;
+    while (nbb < NBB_MAX && nbb * NB < n) nbb <<= 1;
+    const int nbin = nbb * NB;
+    bins.clear(nbin, tid);
+    __syncthreads();
+    mn = sh.red_mn[lane];
+    mx = sh.red_mx[lane];
+    mn = __reduce_min_sync(FULL, mn);
+    mx = __reduce_max_sync(FULL, mx);
+    float lo, scale;
+    {
+        const float slo = unordered(mn), shi = unordered(mx);
+        const float pad = (shi - slo) * (1.0f / 128.0f);
+        lo = slo - pad;
+        const float hi = shi + pad;
+        scale = hi > lo ? (float)nbb / (hi - lo) : 0.0f;
+    }
+
+    // count per bin
+    bool bad = false;
+    for (int base = 0; base < n; base += PACK_THREADS * UNROLL) {
+        int pu[UNROLL];
+        float xu[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const int i = base + u * PACK_THREADS + tid;
+            pu[u] = -1;
+            xu[u] = 0.0f;
+            if (i < n) {
+                pu[u] = plane[rb + i];
+                xu[u] = x[rb + i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            if (pu[u] < 0) continue;
+            const int q = bucket_code(pu[u], bad);
+            bins.add(q * nbb + bin_of(xu[u] + 0.0f, lo, scale, nbb));
+        }
+    }
+    if (bad) atomicOr(io.status, LF_FLAG_PLANE_RANGE);
+    __syncthreads();
+
+    // exclusive scan of the nbin counters: thread tid owns a run of per (an
+    // even number, so a 16-bit pair has a single owner)
+    {
+        const int per = 2 * ((nbin + 2 * PACK_THREADS - 1) / (2 * PACK_THREADS));
+        const int s0 = min(tid * per, nbin), s1 = min(s0 + per, nbin);
+        int sum = 0;
+        for (int b = s0; b < s1; ++b) sum += bins.get(b);
+        const int inc = wscan_incl(sum, lane);
+        if (lane == 31) sh.warp_tot[warp] = inc;
+        __syncthreads();
+        int wt = sh.warp_tot[lane];
+        const int winc = wscan_incl(wt, lane);
+        int excl = inc - sum + __shfl_sync(FULL, winc - wt, warp);
+        for (int b = s0; b < s1; ++b) {
+            const int c = bins.get(b);
+            bins.set(b, excl);
+            excl += c;
+        }
+        if (tid == 0) bins.set(nbin, n);
+    }
+    __syncthreads();
+    if (tid <= NB) {
+        const int s = bins.get(tid * nbb);
+        sh.boff[tid] = s;
+        if (tid < NB) {
+            io.hit_offsets[(size_t)e * NB + tid] = rb + s;
+            if (bins.get((tid + 1) * nbb) - s > BLOCK_SORT_MAX) {
+                atomicOr(&sh.flagged, 1u << tid);
+                atomicOr(io.status, LF_FLAG_BUCKET_OVERFLOW);
+            }
+        }
+    }
+    __syncthreads();
+
+    const unsigned flagged = sh.flagged;
+    if (n <= chunk && flagged == 0u) {
+        // ---- the whole event in one piece: placed straight into shared memory
+        for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
+            int pu[UNROLL];
+            float xu[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int i = ib + u * PACK_THREADS + tid;
+                pu[u] = -1;
+                xu[u] = 0.0f;
+                if (i < n) {
+                    pu[u] = plane[rb + i];
+                    xu[u] = x[rb + i];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                if (pu[u] < 0) continue;
+                const int i = ib + u * PACK_THREADS + tid;
+                bool bb = false;
+                const int q = bucket_code(pu[u], bb);
+                const float xv = xu[u] + 0.0f;
+                const int pos = bins.add(q * nbb + bin_of(xv, lo, scale, nbb));
+                xs[pos] = xv;
+                ks[pos] = (K)i;
+            }
+        }
+        __syncthreads();
+        // bins[b] now holds the end of bin b; order each bin by (x, raw index)
+        for (int b = tid; b < nbin; b += PACK_THREADS) sort_bin(xs, ks, b == 0 ? 0 : bins.get(b - 1), bins.get(b));
+        __syncthreads();
+        // x, layer and perm straight from shared memory
+        const size_t o0 = (size_t)rb;
+        for (int j = tid; j < n; j += PACK_THREADS) {
+            io.ox[o0 + j] = xs[j];
+            io.ol[o0 + j] = (uint8_t)(bucket_at(sh.boff, j) % NL);
+            io.perm[o0 + j] = rb + (int)ks[j];
+        }
+        __syncthreads();
+        // z, dxdy and w: each raw array is read coalesced into shared memory
+        // (x's area) and written in sorted order, gathered by raw index
+        float* tmp = xs;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float* __restrict__ src = a == 0 ? io.z : (a == 1 ? io.dxdy : io.w);
+            float* dst = a == 0 ? io.oz : (a == 1 ? io.od : io.ow);
+            for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
+                float v[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const int i = ib + u * PACK_THREADS + tid;
+                    v[u] = i < n ? src[rb + i] : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const int i = ib + u * PACK_THREADS + tid;
+                    if (i < n) tmp[i] = v[u];
+                }
+            }
+            __syncthreads();
+            for (int j = tid; j < n; j += PACK_THREADS) dst[o0 + j] = tmp[ks[j]];
+            __syncthreads();
+        }
+        return;
+    }
+
+    // ---- a larger event (or one with a flagged bucket): chunks of consecutive
+    // bins of at most `chunk` hits; per chunk one pass over the raw hits places
+    // the chunk's hits in shared memory, and after the ordering and the x,
+    // layer and perm writes, a second pass reads the payload coalesced and
+    // stores each of the chunk's hits' z, dxdy and w at its position
+    int b0 = 0;
+    while (b0 < nbin) {
+        const int q0 = b0 / nbb;
+        if ((flagged >> q0) & 1u) {   // b0 is the bucket's first bin
+            const int o0 = sh.boff[q0], o1 = sh.boff[q0 + 1];
+            for (int j = o0 + tid; j < o1; j += PACK_THREADS) {
+                const size_t o = (size_t)rb + j;
+                io.perm[o] = -1;
+                io.ox[o] = 0.0f;
+                io.oz[o] = 0.0f;
+                io.od[o] = 0.0f;
+                io.ow[o] = 0.0f;
+                io.ol[o] = (uint8_t)(q0 % NL);
+            }
+            b0 = (q0 + 1) * nbb;
+            continue;
+        }
+        const int base = bins.get(b0);
+        if (tid == 0) {
+            // the chunk stops before the next flagged bucket
+            int limit = nbin;
+            const unsigned later = flagged & ~((2u << q0) - 1u);
+            if (later) limit = (__ffs(later) - 1) * nbb;
+            // largest b1 in (b0, limit] with bins[b1] - base <= chunk (bins past
+            // b0 still hold their starts, monotone in b; a single bin of an
+            // unflagged bucket always fits)
+            int l = b0 + 1, h = limit;
+            while (l < h) {
+                const int m = (l + h + 1) >> 1;
+                if (bins.get(m) - base <= chunk) l = m; else h = m - 1;
+            }
+            sh.b1 = l;
+        }
+        __syncthreads();
+        const int b1 = sh.b1;
+        const int tot = bins.get(b1) - base;
+        __syncthreads();   // every thread has read bins[b0], bins[b1]
+        for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
+            int pu[UNROLL];
+            float xu[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int i = ib + u * PACK_THREADS + tid;
+                pu[u] = -1;
+                xu[u] = 0.0f;
+                if (i < n) {
+                    pu[u] = plane[rb + i];
+                    xu[u] = x[rb + i];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                if (pu[u] < 0) continue;
+                const int i = ib + u * PACK_THREADS + tid;
+                bool bb = false;
+                const int q = bucket_code(pu[u], bb);
+                const float xv = xu[u] + 0.0f;
+                const int b = q * nbb + bin_of(xv, lo, scale, nbb);
+                if (b >= b0 && b < b1) {
+                    const int pos = bins.add(b) - base;
+                    xs[pos] = xv;
+                    ks[pos] = (K)i;
+                }
+            }
+        }
+        __syncthreads();
+        // bins[b] now holds the end of bin b for b in [b0, b1)
+        for (int b = b0 + tid; b < b1; b += PACK_THREADS)
+            sort_bin(xs, ks, (b == b0 ? base : bins.get(b - 1)) - base, bins.get(b) - base);
+        __syncthreads();
+        const size_t o0 = (size_t)rb + base;
+        for (int j = tid; j < tot; j += PACK_THREADS) {
+            io.ox[o0 + j] = xs[j];
+            io.ol[o0 + j] = (uint8_t)(bucket_at(sh.boff, base + j) % NL);
+            io.perm[o0 + j] = rb + (int)ks[j];
+        }
+        for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
+            int pu[UNROLL];
+            float xu[UNROLL], zu[UNROLL], du[UNROLL], wu[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int i = ib + u * PACK_THREADS + tid;
+                pu[u] = -1;
+                xu[u] = zu[u] = du[u] = wu[u] = 0.0f;
+                if (i < n) {
+                    pu[u] = plane[rb + i];
+                    xu[u] = x[rb + i];
+                    zu[u] = io.z[rb + i];
+                    du[u] = io.dxdy[rb + i];
+                    wu[u] = io.w[rb + i];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                if (pu[u] < 0) continue;
+                const int i = ib + u * PACK_THREADS + tid;
+                bool bb = false;
+                const int q = bucket_code(pu[u], bb);
+                const int b = q * nbb + bin_of(xu[u] + 0.0f, lo, scale, nbb);
+                if (b < b0 || b >= b1) continue;
+                const int en = bins.get(b) - base;
+                int j = (b == b0 ? base : bins.get(b - 1)) - base;
+                while (j < en && (int)ks[j] != i) ++j;
+                if (j < en) {
+                    io.oz[o0 + j] = zu[u];
+                    io.od[o0 + j] = du[u];
+                    io.ow[o0 + j] = wu[u];
+                }
+            }
+        }
+        __syncthreads();
+        b0 = b1;
+    }
+}
 
 __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
     const int* __restrict__ raw_offsets, const float* __restrict__ x, const float* __restrict__ z,
@@ -209,305 +545,9 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
             for (int i = tid; i < n; i += PACK_THREADS) perm[(size_t)rb + i] = -1;
             continue;
         }
-        const Bins bins{smem, n > 65535};
-        const int chunk = bins.wide ? CHUNK_W : CHUNK_N;
-        float* xs = reinterpret_cast<float*>(smem + (bins.wide ? BINS32_BYTES : BINS16_BYTES));
-        uint32_t* ks = reinterpret_cast<uint32_t*>(xs + chunk);
-
-        // x range of the event from a strided sample, widened by 1/128 of it
-        // on each side: it only shapes the bins (a hit outside it lands in an
-        // edge bin, which the ordering inside bins absorbs)
-        unsigned mn = 0xffffffffu, mx = 0u;
-        {
-            const int ns = n < RANGE_SAMPLE ? n : RANGE_SAMPLE;
-            const int stride = n / ns;
-            if (tid < ns) {
-                const unsigned ov = ordered(x[rb + tid * stride] + 0.0f);
-                mn = ov;
-                mx = ov;
-            }
-        }
-        mn = __reduce_min_sync(FULL, mn);
-        mx = __reduce_max_sync(FULL, mx);
-        if (lane == 0) {
-            sh.red_mn[warp] = mn;
-            sh.red_mx[warp] = mx;
-        }
-        // bins per bucket: a power of two near n / 24
-        int nbb = NBB_MIN;
-        while (nbb < NBB_MAX && nbb * NB < n) nbb <<= 1;
-        const int nbin = nbb * NB;
-        if (bins.wide) {
-            for (int b = tid; b <= nbin; b += PACK_THREADS) bins.set(b, 0);
-        } else {
-            for (int b = tid; b <= nbin / 2; b += PACK_THREADS) reinterpret_cast<unsigned*>(smem)[b] = 0u;
-        }
-        __syncthreads();
-        mn = sh.red_mn[lane];
-        mx = sh.red_mx[lane];
-        mn = __reduce_min_sync(FULL, mn);
-        mx = __reduce_max_sync(FULL, mx);
-        float lo, scale;
-        {
-            const float slo = unordered(mn), shi = unordered(mx);
-            const float pad = (shi - slo) * (1.0f / 128.0f);
-            lo = slo - pad;
-            const float hi = shi + pad;
-            scale = hi > lo ? (float)nbb / (hi - lo) : 0.0f;
-        }
-
-        // count per bin
-        bool bad = false;
-        for (int base = 0; base < n; base += PACK_THREADS * UNROLL) {
-            int pu[UNROLL];
-            float xu[UNROLL];
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) {
-                const int i = base + u * PACK_THREADS + tid;
-                pu[u] = -1;
-                xu[u] = 0.0f;
-                if (i < n) {
-                    pu[u] = plane[rb + i];
-                    xu[u] = x[rb + i];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) {
-                if (pu[u] < 0) continue;
-                const int q = bucket_code(pu[u], bad);
-                bins.add(q * nbb + bin_of(xu[u] + 0.0f, lo, scale, nbb));
-            }
-        }
-        if (bad) atomicOr(status, LF_FLAG_PLANE_RANGE);
-        __syncthreads();
-
-        // exclusive scan of the nbin counters: thread tid owns a run of per
-        // (an even number, so a 16-bit pair has a single owner)
-        {
-            const int per = 2 * ((nbin + 2 * PACK_THREADS - 1) / (2 * PACK_THREADS));
-            const int s0 = min(tid * per, nbin), s1 = min(s0 + per, nbin);
-            int sum = 0;
-            for (int b = s0; b < s1; ++b) sum += bins.get(b);
-            const int inc = wscan_incl(sum, lane);
-            if (lane == 31) sh.warp_tot[warp] = inc;
-            __syncthreads();
-            int wt = sh.warp_tot[lane];
-            const int winc = wscan_incl(wt, lane);
-            int excl = inc - sum + __shfl_sync(FULL, winc - wt, warp);
-            for (int b = s0; b < s1; ++b) {
-                const int c = bins.get(b);
-                bins.set(b, excl);
-                excl += c;
-            }
-            if (tid == 0) bins.set(nbin, n);
-        }
-        __syncthreads();
-        if (tid <= NB) {
-            const int s = bins.get(tid * nbb);
-            sh.boff[tid] = s;
-            if (tid < NB) {
-                hit_offsets[(size_t)e * NB + tid] = rb + s;
-                if (bins.get((tid + 1) * nbb) - s > BLOCK_SORT_MAX) {
-                    atomicOr(&sh.flagged, 1u << tid);
-                    atomicOr(status, LF_FLAG_BUCKET_OVERFLOW);
-                }
-            }
-        }
-        __syncthreads();
-
-        const unsigned flagged = sh.flagged;
-        if (n <= chunk && flagged == 0u) {
-            // ---- the whole event in one piece: placed straight into shared memory
-            for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
-                int pu[UNROLL];
-                float xu[UNROLL];
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u) {
-                    const int i = ib + u * PACK_THREADS + tid;
-                    pu[u] = -1;
-                    xu[u] = 0.0f;
-                    if (i < n) {
-                        pu[u] = plane[rb + i];
-                        xu[u] = x[rb + i];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u) {
-                    if (pu[u] < 0) continue;
-                    const int i = ib + u * PACK_THREADS + tid;
-                    bool bb = false;
-                    const int q = bucket_code(pu[u], bb);
-                    const float xv = xu[u] + 0.0f;
-                    const int pos = bins.add(q * nbb + bin_of(xv, lo, scale, nbb));
-                    xs[pos] = xv;
-                    ks[pos] = ((uint32_t)q << ID_BITS) | (uint32_t)i;
-                }
-            }
-            __syncthreads();
-            // bins[b] now holds the end of bin b; order each bin by (x, raw
-            // index) (the bucket bits are equal inside a bin)
-            for (int b = tid; b < nbin; b += PACK_THREADS) sort_bin2(xs, ks, b == 0 ? 0 : bins.get(b - 1), bins.get(b));
-            __syncthreads();
-            // x, layer and perm straight from shared memory
-            const size_t o0 = (size_t)rb;
-            for (int j = tid; j < n; j += PACK_THREADS) {
-                const uint32_t k = ks[j];
-                ox[o0 + j] = xs[j];
-                ol[o0 + j] = (uint8_t)((k >> ID_BITS) % NL);
-                perm[o0 + j] = rb + (int)(k & ID_MASK);
-            }
-            __syncthreads();
-            // the inverse map (raw index -> position) over x's area
-            uint16_t* inv = reinterpret_cast<uint16_t*>(xs);
-            for (int j = tid; j < n; j += PACK_THREADS) inv[ks[j] & ID_MASK] = (uint16_t)j;
-            __syncthreads();
-            // z, dxdy and w: coalesced reads of the raw arrays, transposed
-            // through shared memory (the keys' area), coalesced writes
-            float* tmp = reinterpret_cast<float*>(ks);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float* src = a == 0 ? z : (a == 1 ? dxdy : w);
-                float* dst = a == 0 ? oz : (a == 1 ? od : ow);
-                for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
-                    float v[UNROLL];
-#pragma unroll
-                    for (int u = 0; u < UNROLL; ++u) {
-                        const int i = ib + u * PACK_THREADS + tid;
-                        v[u] = i < n ? src[rb + i] : 0.0f;
-                    }
-#pragma unroll
-                    for (int u = 0; u < UNROLL; ++u) {
-                        const int i = ib + u * PACK_THREADS + tid;
-                        if (i < n) tmp[inv[i]] = v[u];
-                    }
-                }
-                __syncthreads();
-                for (int j = tid; j < n; j += PACK_THREADS) dst[o0 + j] = tmp[j];
-                __syncthreads();
-            }
-            continue;
-        }
-
-        // ---- a larger event (or one with a flagged bucket): chunks of
-        // consecutive bins of at most `chunk` hits; per chunk one pass over
-        // the raw hits places the chunk's hits in shared memory, and after the
-        // ordering and the x, layer and perm writes, a second pass reads the
-        // payload coalesced and stores each hit's z, dxdy and w at its position
-        int b0 = 0;
-        while (b0 < nbin) {
-            const int q0 = b0 / nbb;
-            if ((flagged >> q0) & 1u) {   // b0 is the bucket's first bin
-                const int o0 = sh.boff[q0], o1 = sh.boff[q0 + 1];
-                for (int j = o0 + tid; j < o1; j += PACK_THREADS) {
-                    const size_t o = (size_t)rb + j;
-                    perm[o] = -1;
-                    ox[o] = 0.0f;
-                    oz[o] = 0.0f;
-                    od[o] = 0.0f;
-                    ow[o] = 0.0f;
-                    ol[o] = (uint8_t)(q0 % NL);
-                }
-                b0 = (q0 + 1) * nbb;
-                continue;
-            }
-            const int base = bins.get(b0);
-            if (tid == 0) {
-                // the chunk stops before the next flagged bucket
-                int limit = nbin;
-                const unsigned later = flagged & ~((2u << q0) - 1u);
-                if (later) limit = (__ffs(later) - 1) * nbb;
-                // largest b1 in (b0, limit] with bins[b1] - base <= chunk (bins
-                // past b0 still hold their starts, monotone in b; a single bin
-                // of an unflagged bucket always fits)
-                int l = b0 + 1, h = limit;
-                while (l < h) {
-                    const int m = (l + h + 1) >> 1;
-                    if (bins.get(m) - base <= chunk) l = m; else h = m - 1;
-                }
-                sh.b1 = l;
-            }
-            __syncthreads();
-            const int b1 = sh.b1;
-            const int tot = bins.get(b1) - base;
-            __syncthreads();   // every thread has read bins[b0], bins[b1]
-            for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
-                int pu[UNROLL];
-                float xu[UNROLL];
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u) {
-                    const int i = ib + u * PACK_THREADS + tid;
-                    pu[u] = -1;
-                    xu[u] = 0.0f;
-                    if (i < n) {
-                        pu[u] = plane[rb + i];
-                        xu[u] = x[rb + i];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u) {
-                    if (pu[u] < 0) continue;
-                    const int i = ib + u * PACK_THREADS + tid;
-                    bool bb = false;
-                    const int q = bucket_code(pu[u], bb);
-                    const float xv = xu[u] + 0.0f;
-                    const int b = q * nbb + bin_of(xv, lo, scale, nbb);
-                    if (b >= b0 && b < b1) {
-                        const int pos = bins.add(b) - base;
-                        xs[pos] = xv;
-                        ks[pos] = ((uint32_t)q << ID_BITS) | (uint32_t)i;
-                    }
-                }
-            }
-            __syncthreads();
-            // bins[b] now holds the end of bin b for b in [b0, b1)
-            for (int b = b0 + tid; b < b1; b += PACK_THREADS)
-                sort_bin2(xs, ks, (b == b0 ? base : bins.get(b - 1)) - base, bins.get(b) - base);
-            __syncthreads();
-            const size_t o0 = (size_t)rb + base;
-            for (int j = tid; j < tot; j += PACK_THREADS) {
-                const uint32_t k = ks[j];
-                ox[o0 + j] = xs[j];
-                ol[o0 + j] = (uint8_t)((k >> ID_BITS) % NL);
-                perm[o0 + j] = rb + (int)(k & ID_MASK);
-            }
-            for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
-                int pu[UNROLL];
-                float xu[UNROLL], zu[UNROLL], du[UNROLL], wu[UNROLL];
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u) {
-                    const int i = ib + u * PACK_THREADS + tid;
-                    pu[u] = -1;
-                    xu[u] = zu[u] = du[u] = wu[u] = 0.0f;
-                    if (i < n) {
-                        pu[u] = plane[rb + i];
-                        xu[u] = x[rb + i];
-                        zu[u] = z[rb + i];
-                        du[u] = dxdy[rb + i];
-                        wu[u] = w[rb + i];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u) {
-                    if (pu[u] < 0) continue;
-                    const int i = ib + u * PACK_THREADS + tid;
-                    bool bb = false;
-                    const int q = bucket_code(pu[u], bb);
-                    const int b = q * nbb + bin_of(xu[u] + 0.0f, lo, scale, nbb);
-                    if (b < b0 || b >= b1) continue;
-                    const uint32_t key = ((uint32_t)q << ID_BITS) | (uint32_t)i;
-                    const int en = bins.get(b) - base;
-                    int j = (b == b0 ? base : bins.get(b - 1)) - base;
-                    while (j < en && ks[j] != key) ++j;
-                    if (j < en) {
-                        oz[o0 + j] = zu[u];
-                        od[o0 + j] = du[u];
-                        ow[o0 + j] = wu[u];
-                    }
-                }
-            }
-            __syncthreads();
-            b0 = b1;
-        }
+        const PackIO io{x, z, dxdy, w, plane, hit_offsets, ox, oz, od, ow, ol, perm, status};
+        if (n > 65535) sort_event<true>(io, sh, smem, e, rb, n, tid, lane, warp);
+        else sort_event<false>(io, sh, smem, e, rb, n, tid, lane, warp);
     }
 }
 

@@ -156,12 +156,13 @@ def _batch_of(parts, n_states=0):
 
 def test_pack_paths_exact(lfm):
     """Both pack paths against the oracle, bit for bit: events sorted in one
-    piece in shared memory (up to 20480 hits) and larger events staged
-    through their output range in chunks; ties in x (ordered by raw index),
-    -0.0 and +0.0, a skewed x distribution and random plane codes."""
+    piece in shared memory (up to 34432 hits), larger events sorted in chunks
+    of consecutive bins, and an event above 65535 hits (32-bit bins and
+    indices); ties in x (ordered by raw index), -0.0 and +0.0, a skewed x
+    distribution and random plane codes."""
     rng = np.random.default_rng(11)
     parts = []
-    for n in (1, 3000, 20480, 20481, 50000):
+    for n in (1, 3000, 34432, 34433, 50000, 70000):
         x = rng.uniform(-3000.0, 3000.0, n)
         if n >= 3000:
             x[: n // 3] = np.round(x[: n // 3] * 2.0) / 2.0     # many exact ties
