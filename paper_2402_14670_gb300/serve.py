@@ -4,11 +4,11 @@ Events arrive over time into a host-resident pool (pinned memory).  The
 server keeps S slots, each with its own library context and device buffers
 allocated once (hit, state and output buffers stay resident; geometry and
 parameters live in the contexts), and three CUDA streams shared by the slots:
-copies in, compute, copies out.  Whenever a slot is free it takes every event
-that has arrived and is not yet scheduled (up to the slot's event and hit
-capacity); its copies in are queued on the first stream, its pack and find
-(persistent form, launch shape from the autotuner for the batch's size
-bucket) on the compute stream after them, and the copies of its per-track
+copies in, compute (two of these, alternating over the slots), copies out.
+Whenever a slot is free it takes every event that has arrived and is not yet
+scheduled (up to the slot's event and hit capacity); its copies in are queued
+on the first stream, its pack and find (persistent form, launch shape from the
+autotuner for the batch's size bucket) on its compute stream after them, and the copies of its per-track
 results on the third stream after the compute, chained by events.  So the
 copies in of one batch, the compute of another and the copies out of a third
 overlap on the device.
@@ -122,7 +122,12 @@ class Server:
         self.slots = [_Slot(max_events, self.max_hits, self.max_tracks, geometry, params, self.dev)
                       for _ in range(n_slots)]
         self.s_in = torch.cuda.Stream(device=self.dev)
-        self.s_comp = torch.cuda.Stream(device=self.dev)
+        # two compute streams, alternating over the slots: one batch's
+        # persistent kernels fill the SMs the other's tail leaves idle (each
+        # slot has its own context, so their work is independent)
+        self.s_comps = [torch.cuda.Stream(device=self.dev), torch.cuda.Stream(device=self.dev)]
+        for i, sl in enumerate(self.slots):
+            sl.s_comp = self.s_comps[i % 2]
         self.s_out = torch.cuda.Stream(device=self.dev)
         self.tuner = tuner or Autotuner()
         self.keep_results = keep_results
@@ -179,11 +184,12 @@ class Server:
                 s.ev_in.record(self.s_in)
             src_h = {f: s.raw[f][:nh] for f in ("x", "z", "dxdy", "w", "plane")}
             src_t = {f: s.st[f][:nt] for f in ("sx", "sy", "stx", "sty", "sqop")}
-        self.s_comp.wait_event(s.ev_in)
-        with torch.cuda.stream(self.s_comp):
+        s_comp = s.s_comp
+        s_comp.wait_event(s.ev_in)
+        with torch.cuda.stream(s_comp):
             raw = SimpleNamespace(n_events=ne, raw_offsets=s.raw["raw_offsets"][:ne + 1], **src_h)
             pk = {k: (v[:24 * ne + 1] if k == "hit_offsets" else v[:nh]) for k, v in s.packed.items()}
-            s.tr.pack(raw, self.s_comp, out=pk)
+            s.tr.pack(raw, s_comp, out=pk)
             st = SimpleNamespace(trk_offsets=s.st["trk_offsets"][:ne + 1], **src_t)
             out = {k: v for k, v in s.out.items()}
             for k in ("found", "nhits", "hit_idx", "state", "quality"):
@@ -191,8 +197,8 @@ class Server:
             out["out_offsets"] = s.out["out_offsets"][:ne + 1]
             out["out_trk"] = s.out["out_trk"][:max(nt, 1)]
             tuning = self.tuner.lookup(ne, nt)
-            s.tr.find(pk, st, ne, "batched", tuning, self.s_comp, out=out)
-            s.ev_comp.record(self.s_comp)
+            s.tr.find(pk, st, ne, "batched", tuning, s_comp, out=out)
+            s.ev_comp.record(s_comp)
         self.s_out.wait_event(s.ev_comp)
         with torch.cuda.stream(self.s_out):
             # the per-track results come back to the host for every batch
