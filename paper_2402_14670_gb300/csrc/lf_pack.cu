@@ -20,10 +20,10 @@
 //            the data (a skewed x distribution costs time, never exactness);
 //   write    x, layer and perm leave coalesced.
 // An event of at most CHUNK_N hits is placed straight into shared memory as
-// (x, 16-bit raw index), 6 bytes per hit; its z, dxdy and w are then read
-// coalesced from the raw arrays (prefetched into L2 when the event was taken)
-// into shared memory, one array at a time, and written in sorted order,
-// gathered by raw index.  A larger event is sorted in chunks of consecutive
+// (x, 16-bit raw index), 6 bytes per hit; its z, dxdy and w are then copied
+// from the raw arrays (prefetched into L2 when the event was taken) into
+// shared memory with cp.async, one array at a time, and written in sorted
+// order, gathered by raw index.  A larger event is sorted in chunks of consecutive
 // bins: per chunk a pass over the raw hits places the chunk's hits in shared
 // memory, and after the ordering a second pass reads the payload coalesced and
 // stores each of the chunk's hits' z, dxdy and w at its position inside its
@@ -352,26 +352,19 @@ __device__ __forceinline__ void sort_event(const PackIO& io, EvShared& sh, char*
             io.perm[o0 + j] = rb + (int)ks[j];
         }
         __syncthreads();
-        // z, dxdy and w: each raw array is read coalesced into shared memory
-        // (x's area) and written in sorted order, gathered by raw index
+        // z, dxdy and w: each raw array is copied into shared memory (x's
+        // area) with asynchronous 4-byte copies, all of them in flight at
+        // once, and written in sorted order, gathered by raw index
         float* tmp = xs;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const float* __restrict__ src = a == 0 ? io.z : (a == 1 ? io.dxdy : io.w);
             float* dst = a == 0 ? io.oz : (a == 1 ? io.od : io.ow);
-            for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
-                float v[UNROLL];
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u) {
-                    const int i = ib + u * PACK_THREADS + tid;
-                    v[u] = i < n ? src[rb + i] : 0.0f;
-                }
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u) {
-                    const int i = ib + u * PACK_THREADS + tid;
-                    if (i < n) tmp[i] = v[u];
-                }
+            for (int i = tid; i < n; i += PACK_THREADS) {
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(tmp + i);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(src + rb + i) : "memory");
             }
+            asm volatile("cp.async.wait_all;" ::: "memory");
             __syncthreads();
             for (int j = tid; j < n; j += PACK_THREADS) dst[o0 + j] = tmp[ks[j]];
             __syncthreads();

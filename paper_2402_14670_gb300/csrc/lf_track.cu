@@ -25,6 +25,8 @@
 //              one per lane.  The exact filters on a superset give the same
 //              triplet set as enumerating every pair.
 //   extension  Sec. "Extending triplets to other layers" and "Quality Filter":
+//              the x of all twelve windows is staged (z, dxdy and w of the hits
+//              a candidate uses are read from global memory);
 //              lane r of a 16- or 32-lane group extends triplet r
 //              (three-point solution, missing x layers, weighted x refit,
 //              u/v layers, y line fit, Q).
@@ -314,7 +316,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // the lanes and every pair is one asynchronous copy per array, so all of a
 // track's copies are in flight at once (stage_issue); stage_finish waits for
 // them and flags a window whose hits do not all share one z.
-template <bool XONLY = false>
+template <bool XONLY = false, bool ZTOO = true>
 __device__ __forceinline__ void stage_issue(const KParams& k, const KBatch& b, const Slot& m, int lane) {
     const int cap = k.cap;
     int off[NL + 1];
@@ -334,7 +336,7 @@ __device__ __forceinline__ void stage_issue(const KParams& k, const KBatch& b, c
         const int j = q - lo;
         const int src = m.h->wbeg[l] + j;
         cp_async4(m.wx + l * cap + j, b.x + src);
-        cp_async4(m.wz + l * cap + j, b.z + src);
+        if (ZTOO) cp_async4(m.wz + l * cap + j, b.z + src);
     }
 }
 
@@ -352,13 +354,15 @@ __device__ __forceinline__ void window_zuni(const KParams& k, const Slot& m, int
 
 // Wait for the staging copies of the warp's TPW slots (lanes 16q.. of slot q)
 // and set their z-uniformity flags.
-template <int TPW, bool XONLY = false>
+template <int TPW, bool XONLY = false, bool ZTOO = true>
 __device__ __forceinline__ void stage_finish(const KParams& k, const Slot* sl, int lane) {
     cp_async_wait_all();
     __syncwarp();
-    const int q = lane >> 4, l = lane & 15;
-    if (q < TPW && l < NL) window_zuni<XONLY>(k, (TPW == 2 && q == 1) ? sl[TPW - 1] : sl[0], l);
-    __syncwarp();
+    if (ZTOO) {
+        const int q = lane >> 4, l = lane & 15;
+        if (q < TPW && l < NL) window_zuni<XONLY>(k, (TPW == 2 && q == 1) ? sl[TPW - 1] : sl[0], l);
+        __syncwarp();
+    }
 }
 
 template <bool XONLY = false>
@@ -612,8 +616,13 @@ __device__ __forceinline__ float model_x(float A, float T, float C, float u, flo
 // Extension and fit of one triplet (Sec. "Extending triplets to other
 // layers", "Quality Filter"); x and z of the window hits come from the
 // slot, dxdy and w of the hits used from global memory.
+template <bool ZG = false>
 __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, const TState& s, const Slot& m,
                                            uint64_t key, Cand& cd) {
+    // z of window hit j of layer l: staged, or read from global memory
+    auto zat = [&](int l, int j) -> float {
+        return ZG ? __ldg(b.z + m.h->wbeg[l] + j) : m.wz[l * k.cap + j];
+    };
     const int cap = k.cap;
     const float D = k.D;
     const int cfg = (int)((key >> 18) & 1);
@@ -627,9 +636,9 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
 
     // three-point solution through the triplet
     float x0 = m.wx[L0 * cap + j0], x1 = m.wx[L1 * cap + j1], x2 = m.wx[L2 * cap + j2];
-    float u0 = (m.wz[L0 * cap + j0] - k.z_ref) * 1e-3f;
-    float u1 = (m.wz[L1 * cap + j1] - k.z_ref) * 1e-3f;
-    float u2 = (m.wz[L2 * cap + j2] - k.z_ref) * 1e-3f;
+    float u0 = (zat(L0, j0) - k.z_ref) * 1e-3f;
+    float u1 = (zat(L1, j1) - k.z_ref) * 1e-3f;
+    float u2 = (zat(L2, j2) - k.z_ref) * 1e-3f;
     float g0 = f2_of(u0, D), g1 = f2_of(u1, D), g2 = f2_of(u2, D);
     float d1 = u1 - u0, d2 = u2 - u0;
     float e1 = g1 - g0, e2 = g2 - g0;
@@ -660,7 +669,7 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
     for (int l = 0; l < NL; ++l) {
         if (!is_x(l) || hl[l] < 0) continue;
         int q = l * cap + hl[l];
-        float u = (m.wz[q] - k.z_ref) * 1e-3f;
+        float u = (zat(l, hl[l]) - k.z_ref) * 1e-3f;
         float f = f2_of(u, D);
         float r = m.wx[q] - model_x(A, T, C, u, D);
         float wt = __ldg(b.w + m.h->wbeg[l] + hl[l]);
@@ -730,7 +739,7 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
         if (is_x(l) || hl[l] < 0) continue;
         int q = l * cap + hl[l];
         int g = m.h->wbeg[l] + hl[l];
-        float u = (m.wz[q] - k.z_ref) * 1e-3f;
+        float u = (zat(l, hl[l]) - k.z_ref) * 1e-3f;
         float dd = __ldg(b.dxdy + g);
         dv[l] = dd;
         float y = (model_x(A, T, C, u, D) - m.wx[q]) / dd;
@@ -759,7 +768,7 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
     for (int l = 0; l < NL; ++l) {
         if (hl[l] < 0) continue;
         int q = l * cap + hl[l];
-        float u = (m.wz[q] - k.z_ref) * 1e-3f;
+        float u = (zat(l, hl[l]) - k.z_ref) * 1e-3f;
         float xf = model_x(A, T, C, u, D);
         if (is_x(l)) {
             float r = m.wx[q] - xf;
@@ -1099,7 +1108,7 @@ __device__ __forceinline__ void extend_tracks(const KParams& k, const KBatch& b,
         __syncwarp();
     }
 #pragma unroll
-    for (int qq = 0; qq < TPW; ++qq) stage_issue(k, b, sl[qq], lane);
+    for (int qq = 0; qq < TPW; ++qq) stage_issue<false, false>(k, b, sl[qq], lane);
     constexpr int G = 32 / TPW;
     const int q = lane / G, r = lane % G;
     const int t = t0 + q;
@@ -1111,7 +1120,7 @@ __device__ __forceinline__ void extend_tracks(const KParams& k, const KBatch& b,
     const uint64_t key = act ? keys[(size_t)t * k.n_trip + r] : NOKEY;
     TState s = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     if (act) s = load_state(b, t);
-    stage_finish<TPW>(k, sl, lane);
+    stage_finish<TPW, false, false>(k, sl, lane);
     Cand cd;
     cd.status = 9;
     cd.Q = 0.0f;
@@ -1120,7 +1129,7 @@ __device__ __forceinline__ void extend_tracks(const KParams& k, const KBatch& b,
     for (int p = 0; p < 6; ++p) cd.st[p] = 0.0f;
 #pragma unroll
     for (int l = 0; l < NL; ++l) cd.hl[l] = -1;
-    if (act) extend_fit(k, b, s, mq, key, cd);
+    if (act) extend_fit<true>(k, b, s, mq, key, cd);
     if (SEL) {
         int hg[NL];
 #pragma unroll
