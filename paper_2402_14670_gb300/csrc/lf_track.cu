@@ -1002,7 +1002,7 @@ __device__ __forceinline__ void triplets_track(const KParams& k, const KBatch& b
 
 // stage 2: triplet seeding (warp per track)
 template <int NIT, bool P, bool NOUT>
-__global__ void k_triplets(KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ wcnt,
+__global__ void __launch_bounds__(PLAIN_WARPS * 32, 5) k_triplets(KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ wcnt,
                            uint64_t* keys, uint8_t* ntrip, int* cursor) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
