@@ -530,7 +530,7 @@ def main():
                       "warp_instructions_per_launch": inst,
                       "peak_kind": "%d SMs x 4 schedulers x %.0f MHz (median SM clock, timed region)" % (n_sm, mhz)}
     pk_algo = pack_bytes(n_ev, n_hits)
-    roof_pack = {"kernel": "k_pack_event (persistent per-event bin sort with the payload gather)", "bound": "hbm",
+    roof_pack = {"kernel": "k_pack_event (persistent per-event distribution sort, payload through shared memory)", "bound": "hbm",
                  "achieved": pk_algo / (pack_avg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                  "frac": pk_algo / (pack_avg / 1e3) / 1e9 / peak, "launch_ms": pack_avg,
                  "algorithmic_bytes": pk_algo}

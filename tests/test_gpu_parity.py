@@ -1,7 +1,7 @@
 """CUDA library against the oracle, element by element, on the same inputs.
 
-Both forms (plain: one kernel per stage; batched: persistent fused kernel)
-must give the oracle's packed hits bit for bit, the same windows and triplet
+Both forms (plain: one kernel per stage; batched: persistent stage kernels over
+device work queues) must give the oracle's packed hits bit for bit, the same windows and triplet
 lists, the same selected hit lists for every input track and the same states
 and Q (compared bit for bit, within 1e-4 relative at worst).
 """
