@@ -159,6 +159,7 @@ KParams make_kparams(const lf_geometry* g, const lf_params* p) {
     k.magtol_tx = p->magtol_tx;
     k.T_triplet = p->T_triplet;
     k.T_x = p->T_x;
+    k.inv_T_x = pow2_reciprocal(p->T_x);
     k.T_uv_scale = p->T_uv_scale;
     k.T_uv_min = p->T_uv_min;
     k.T_ty = p->T_ty;

@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -31,7 +32,19 @@ struct KParams {
     float pk;     // pol_f * kappa
     float pg;     // pol_f * gamma
     float D;      // dratio * 1000 (model in u = dz/1000)
+    float inv_T_x;  // 1/T_x when T_x is a power of two (then r^2 / T_x == r^2 * inv_T_x exactly), else 0
 };
+
+// 1/t when t is a power of two whose reciprocal is a normal float (dividing by
+// t and multiplying by 1/t then give the same correctly rounded result for any
+// operand), else 0
+inline float pow2_reciprocal(float t) {
+    if (!(t > 0.0f) || !(t < 1e30f)) return 0.0f;
+    int e = 0;
+    const float m = std::frexp(t, &e);   // t = m * 2^e, m in [0.5, 1)
+    if (m != 0.5f || e - 1 > 126 || e - 1 < -126) return 0.0f;
+    return std::ldexp(1.0f, 1 - e);
+}
 
 struct KBatch {
     int n_events, n_hits, n_tracks;

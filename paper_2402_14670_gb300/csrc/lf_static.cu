@@ -84,7 +84,7 @@ lfk::KParams kparams(const lf_geometry* g, const lf_params* p) {
     k.cap = p->n_hits_window; k.n_trip = p->n_triplets; k.min_hits = p->min_hits;
     k.K_first = p->K_first; k.K_last = p->K_last; k.p_bend = p->p_bend;
     k.magtol_min = p->magtol_min; k.magtol_max = p->magtol_max; k.magtol_c = p->magtol_c; k.magtol_tx = p->magtol_tx;
-    k.T_triplet = p->T_triplet; k.T_x = p->T_x; k.T_uv_scale = p->T_uv_scale; k.T_uv_min = p->T_uv_min;
+    k.T_triplet = p->T_triplet; k.T_x = p->T_x; k.inv_T_x = lfk::pow2_reciprocal(p->T_x); k.T_uv_scale = p->T_uv_scale; k.T_uv_min = p->T_uv_min;
     k.T_ty = p->T_ty; k.T_y = p->T_y; k.T_Q = p->T_Q;
     for (int i = 0; i < 4; ++i) k.C_n[i] = p->C_n[i];
     k.no_ut = 0;

@@ -772,7 +772,8 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
         float xf = model_x(A, T, C, u, D);
         if (is_x(l)) {
             float r = m.wx[q] - xf;
-            qx = qx + (r * r) / k.T_x;
+            // T_x a power of two: the product by its reciprocal is the quotient
+            qx = qx + (k.inv_T_x != 0.0f ? (r * r) * k.inv_T_x : (r * r) / k.T_x);
         } else {
             float yf = Y0 + TY * u;
             float r = m.wx[q] - (xf - yf * dv[l]);
