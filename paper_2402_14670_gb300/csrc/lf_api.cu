@@ -58,6 +58,11 @@ struct lf_ctx {
     cudaStream_t pipe_stream[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t ev_in[NSLOT] = {}, ev_comp[NSLOT] = {}, ev_out[NSLOT] = {};
     DevBuf arena[NSLOT];
+    // page-locked host block of the chunks' rebased offsets, kept between
+    // calls (pinning and unpinning memory on every call costs time and
+    // cudaFreeHost can wait on the device)
+    int32_t* host_pin = nullptr;
+    size_t host_pin_cap = 0;
 };
 
 namespace {
@@ -290,6 +295,7 @@ void lf_destroy(lf_ctx* c) {
         if (c->ev_out[i]) cudaEventDestroy(c->ev_out[i]);
         if (c->arena[i].p) cudaFree(c->arena[i].p);
     }
+    if (c->host_pin) cudaFreeHost(c->host_pin);
     for (auto& kv : c->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     DevBuf* bufs[] = {&c->trk_event, &c->wbeg, &c->wcnt, &c->keys, &c->ntrip,
@@ -595,9 +601,16 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
     }
     // rebased offsets of every chunk, in one pinned block
     const size_t n_chunks = cut.size() - 1;
-    int32_t* pin = nullptr;
     const size_t pin_n = 2 * ((size_t)hb->n_events + n_chunks);
-    LF_CUDA(c, cudaMallocHost(&pin, pin_n * sizeof(int32_t)));
+    if (c->host_pin_cap < pin_n) {
+        if (c->host_pin) cudaFreeHost(c->host_pin);
+        c->host_pin = nullptr;
+        c->host_pin_cap = 0;
+        const size_t want = pin_n + pin_n / 8;
+        LF_CUDA(c, cudaMallocHost(&c->host_pin, want * sizeof(int32_t)));
+        c->host_pin_cap = want;
+    }
+    int32_t* pin = c->host_pin;
     std::vector<size_t> pin_off(n_chunks);
     {
         size_t q = 0;
@@ -635,10 +648,7 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
     size_t o_ot = sz; sz += al(4 * (T + 1));
     size_t o_no = sz; sz += al(4);
     for (int i = 0; i < NS; ++i) {
-        if ((st = ensure(c, c->arena[i], sz)) != LF_OK) {
-            cudaFreeHost(pin);
-            return st;
-        }
+        if ((st = ensure(c, c->arena[i], sz)) != LF_OK) return st;
     }
     // three-stage pipeline over NS arena slots: chunk k's copies in (stream
     // s_in) wait until the slot's previous chunk has left (its copies out),
@@ -699,7 +709,6 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
         cudaError_t e2 = cudaStreamSynchronize(c->pipe_stream[i]);
         if (ce == cudaSuccess) ce = e2;
     }
-    cudaFreeHost(pin);
     if (rc != LF_OK) return fail(c, rc, "chunk failed: %s", lf_last_error(sc));
     if (ce != cudaSuccess) return fail(c, LF_ERR_CUDA, "host pipeline: %s", cudaGetErrorString(ce));
     int32_t flags = 0;
