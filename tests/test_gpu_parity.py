@@ -94,6 +94,35 @@ def test_launch_shapes_identical(lfm, tuning):
     run_both(tr, b, mode="batched", tuning=tuning)
 
 
+def test_repeated_launch_shape_direct_capture_replay(lfm):
+    """The persistent form launches a new launch shape directly, captures it
+    into a CUDA graph when it comes back and replays the graph after that:
+    the three calls give identical outputs, also after the inputs change in
+    place (a graph reads the buffers, not copies of them)."""
+    b = synth.generate(1, n_events=150).to("cuda")
+    tr = _tracker(lfm)
+    packed = tr.pack(b)
+    out = tr.alloc_output(b.n_tracks, b.n_events, "cuda")
+    res = []
+    for _ in range(3):
+        out["found"].fill_(7)
+        tr.find(packed, b, b.n_events, "batched", out=out)
+        torch.cuda.synchronize()
+        res.append({k: to_np(v).copy() for k, v in out.items()})
+    for r in res[1:]:
+        f = res[0]["found"].astype(bool)
+        assert np.array_equal(r["found"], res[0]["found"])
+        assert np.array_equal(r["hit_idx"][f], res[0]["hit_idx"][f])
+        assert np.array_equal(r["state"][f].view(np.uint32), res[0]["state"][f].view(np.uint32))
+        assert np.array_equal(r["out_trk"][:int(r["n_out"][0])], res[0]["out_trk"][:int(res[0]["n_out"][0])])
+    # new input values in the same buffers: the replayed graph follows them
+    b.sqop.mul_(-1.0)                                  # flip every charge: different windows and tracks
+    tr.find(packed, b, b.n_events, "batched", out=out)
+    torch.cuda.synchronize()
+    ref = oracle.run_batch(b, dumps=False)
+    compare_outputs(out, ref)
+
+
 def test_ragged_and_empty_events(lfm):
     geo = synth.Geometry()
     tx, ty, q = 0.1, 0.05, 1 / 8.0
