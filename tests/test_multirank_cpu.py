@@ -50,6 +50,27 @@ def test_partition_covers_every_event_once_and_balances():
         assert loads.max() - loads.mean() <= costs.max()
 
 
+def test_partition_edge_cases():
+    # more ranks than events, events without hits or tracks (each factor at least 1), a single event
+    ro = np.array([0, 0, 5, 5, 9])
+    to = np.array([0, 0, 0, 3, 3])
+    costs = shard.event_costs(ro, to)
+    assert costs.tolist() == [1, 5, 3, 4]
+    parts = shard.partition(costs, 6)
+    assert sorted(np.concatenate(parts).tolist()) == [0, 1, 2, 3]
+    assert sum(len(p) == 0 for p in parts) == 2
+    assert [len(p) for p in shard.partition([7.0], 3)] == [1, 0, 0]
+    with pytest.raises(ValueError):
+        shard.partition(costs, 0)
+    # gather puts results in batch order and refuses a missing event
+    parts = shard.partition(costs, 2)
+    res = {r: {int(e): ("ev", int(e)) for e in p} for r, p in enumerate(parts)}
+    assert shard.gather(res, parts, 4) == [("ev", e) for e in range(4)]
+    del res[0][int(parts[0][0])]
+    with pytest.raises((ValueError, KeyError)):
+        shard.gather(res, parts, 4)
+
+
 def _event_results(batch_cpu, res):
     """Per event: found flags, hit lists as raw indices inside the event,
     state and Q bits of the found tracks."""
