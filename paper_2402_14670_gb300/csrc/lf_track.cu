@@ -1110,6 +1110,24 @@ __device__ __forceinline__ void extend_tracks(const KParams& k, const KBatch& b,
     }
 #pragma unroll
     for (int qq = 0; qq < TPW; ++qq) stage_issue<false, false>(k, b, sl[qq], lane);
+    // the z, dxdy and w lines of every window go to L2 while x is staged: the
+    // candidates read them for the hits they use
+    {
+        const int qw = lane >> 4, lw = lane & 15;
+        if (qw < TPW && lw < NL) {
+            const Slot& mw = (TPW == 2 && qw == 1) ? sl[TPW - 1] : sl[0];
+            const int wb = mw.h->wbeg[lw], wc = mw.h->wcnt[lw];
+            if (wc > 0) {
+                const uintptr_t lines[3] = {reinterpret_cast<uintptr_t>(b.z + wb), reinterpret_cast<uintptr_t>(b.dxdy + wb),
+                                            reinterpret_cast<uintptr_t>(b.w + wb)};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const uintptr_t p0 = lines[a] & ~uintptr_t(127), p1 = lines[a] + (uintptr_t)wc * 4;
+                    for (uintptr_t q = p0; q < p1; q += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+                }
+            }
+        }
+    }
     constexpr int G = 32 / TPW;
     const int q = lane / G, r = lane % G;
     const int t = t0 + q;
