@@ -154,6 +154,35 @@ __device__ __forceinline__ int closest_smem(const float* x, int n, float e) {
     return best;
 }
 
+// the same search, out of line, on a window given by its shared-memory address
+__device__ __noinline__ int closest_shared(unsigned xs, int n, float e) {
+    auto at = [&](int i) -> float {
+        float v;
+        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(xs + 4u * (unsigned)i));
+        return v;
+    };
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = lo + ((hi - lo) >> 1);
+        if (at(mid) < e) lo = mid + 1; else hi = mid;
+    }
+    const int j = lo;
+    int best = -1;
+    float bd = 0.0f;
+    if (j > 0) {
+        int q = j - 1;
+        float d = fabsf(at(q) - e);
+        while (q > 0 && fabsf(at(q - 1) - e) == d) --q;
+        best = q;
+        bd = d;
+    }
+    if (j < n) {
+        float d = fabsf(at(j) - e);
+        if (best < 0 || d < bd) best = j;
+    }
+    return best;
+}
+
 // ----------------------------------------------------------- stage: windows
 
 // x of the input track extrapolated to layer l (straight line to the magnet
@@ -652,15 +681,19 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
     float C = (d1 * r2 - d2 * r1) / det;
     float A = (x0 - T * u0) - C * g0;
 
-    // missing x layers
+    // missing x layers: 3, 7, 11 after configuration 0; 0, 4, 8 after configuration 1
 #pragma unroll
-    for (int l = 0; l < NL; ++l) {
-        if (!is_x(l) || l == L0 || l == L1 || l == L2) continue;
-        float xe = model_x(A, T, C, (k.z[l] - k.z_ref) * 1e-3f, D);
-        int j = closest_smem(m.wx + l * cap, m.h->wcnt[l], xe);
-        if (j < 0) continue;
-        float dx = m.wx[l * cap + j] - xe;
-        if (dx * dx < k.T_x) hl[l] = j;
+    for (int i = 0; i < 3; ++i) {
+        const int l = 4 * i + (cfg ? 0 : 3);
+        const float zl = cfg ? k.z[4 * i] : k.z[4 * i + 3];
+        float xe = model_x(A, T, C, (zl - k.z_ref) * 1e-3f, D);
+        int j = closest_shared((unsigned)__cvta_generic_to_shared(m.wx + l * cap), m.h->wcnt[l], xe);
+        int jm = -1;
+        if (j >= 0) {
+            float dx = m.wx[l * cap + j] - xe;
+            if (dx * dx < k.T_x) jm = j;
+        }
+        if (cfg) hl[4 * i] = jm; else hl[4 * i + 3] = jm;
     }
 
     // weighted refit on the x hits, as a correction to the three-point solution
@@ -701,7 +734,7 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
         if (is_x(l)) continue;
         float yl = s.ys + s.tys * (k.z[l] - k.z_state);
         float xe = model_x(A, T, C, (k.z[l] - k.z_ref) * 1e-3f, D) - yl * k.dxdy[l];
-        int j = closest_smem(m.wx + l * cap, m.h->wcnt[l], xe);
+        int j = closest_shared((unsigned)__cvta_generic_to_shared(m.wx + l * cap), m.h->wcnt[l], xe);
         if (j < 0) continue;
         float dx = m.wx[l * cap + j] - xe;
         if (dx * dx < T_uv) hl[l] = j;
