@@ -154,6 +154,10 @@ __device__ __forceinline__ int closest_smem(const float* x, int n, float e) {
     return best;
 }
 
+// IEEE quotient, out of line (keeps rarely taken or repeated divisions out of
+// the unrolled loops' code)
+__device__ __noinline__ float div_call(float a, float b) { return a / b; }
+
 // the same search, out of line, on a window given by its shared-memory address
 __device__ __noinline__ int closest_shared(unsigned xs, int n, float e) {
     auto at = [&](int i) -> float {
@@ -806,13 +810,13 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
         if (is_x(l)) {
             float r = m.wx[q] - xf;
             // T_x a power of two: the product by its reciprocal is the quotient
-            qx = qx + (k.inv_T_x != 0.0f ? (r * r) * k.inv_T_x : (r * r) / k.T_x);
+            qx = qx + (k.inv_T_x != 0.0f ? (r * r) * k.inv_T_x : div_call(r * r, k.T_x));
         } else {
             float yf = Y0 + TY * u;
             float r = m.wx[q] - (xf - yf * dv[l]);
-            qx = qx + (r * r) / T_uv;
+            qx = qx + div_call(r * r, T_uv);
             float ry = yv[l] - yf;
-            qy = qy + (ry * ry) / k.T_y;
+            qy = qy + div_call(ry * ry, k.T_y);
         }
     }
     float Cn = n == 9 ? k.C_n[0] : n == 10 ? k.C_n[1] : n == 11 ? k.C_n[2] : k.C_n[3];
