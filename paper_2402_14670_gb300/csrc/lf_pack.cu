@@ -4,7 +4,9 @@
 // One persistent kernel, k_pack_event: a block of 1024 threads takes one
 // event at a time from a device work queue and sorts it as a distribution
 // sort whose bins are ordered like the result:
-//   range    the event's x range (one pass over x);
+//   range    the x range of a strided sample of at most 1024 of the event's
+//            hits, widened by 1/128 of it on each side (a hit outside it
+//            lands in an edge bin);
 //   bins     every bucket gets nbb equal x bins over that range (nbb a power
 //            of two between 16 and 512, about one hit per bin); the global
 //            bin of a hit is bucket * nbb + bin, a monotone function of
