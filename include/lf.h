@@ -204,10 +204,12 @@ lf_status lf_find_tracks(lf_ctx* ctx, const lf_batch* batch, const lf_output* ou
 /* Persistent form: persistent kernels over device work queues (by default a
  * pipeline of one persistent kernel per stage; see lf_tuning.queue), then
  * compaction.  The first call with a given launch shape (tuning, sizes and
- * batch buffers) launches the kernels directly; when the same shape comes
- * back it is captured into a CUDA graph, which later calls replay (at most
- * 64 graphs and 256 remembered shapes per context).  tuning may be NULL
- * (defaults).  Results are identical to lf_find_tracks. */
+ * every batch and output pointer) launches the kernels directly; when the
+ * same shape comes back it is captured into a CUDA graph, which later calls
+ * replay (at most 64 graphs and 256 remembered shapes per context), reading
+ * the buffers' current contents.  A call that changes any pointer or size is
+ * a new shape.  tuning may be NULL (defaults).  Results are identical to
+ * lf_find_tracks. */
 lf_status lf_find_tracks_batched(lf_ctx* ctx, const lf_batch* batch, const lf_output* out,
                                  const lf_tuning* tuning, void* stream);
 

@@ -4,9 +4,9 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <array>
 #include <cstdint>
 #include <map>
-#include <tuple>
 #include <vector>
 
 #include "lf.h"
@@ -21,9 +21,11 @@ struct DevBuf {
     size_t cap = 0;
 };
 
+// A captured graph holds every pointer and size of its launch, so its key is
+// the launch shape, the sizes, the scratch generation and every batch and
+// output pointer: a call that changes any of them is a new shape.
 struct GraphKey {
-    std::tuple<int, int, int, int, int, int, const void*, const void*, const void*, const void*, const void*,
-               const void*, const void*> v;
+    std::array<uintptr_t, 26> v;
     bool operator<(const GraphKey& o) const { return v < o.v; }
 };
 
@@ -449,10 +451,15 @@ lf_status lf_find_tracks_batched(lf_ctx* c, const lf_batch* b, const lf_output* 
     if ((st = prepare_batched(c, b, sh)) != LF_OK) return st;
 
     GraphKey key;
-    key.v = std::make_tuple(sh.wpb, sh.bps, sh.grain + 64 * sh.queue, b->n_events, b->n_tracks, b->n_hits,
-                            (const void*)b->hit_offsets, (const void*)b->x, (const void*)b->trk_offsets,
-                            (const void*)b->sx, (const void*)o->found, (const void*)o->out_trk,
-                            (const void*)(uintptr_t)c->generation);
+    {
+        const auto u = [](const void* q) { return (uintptr_t)q; };
+        key.v = {(uintptr_t)sh.wpb, (uintptr_t)sh.bps, (uintptr_t)(sh.grain + 64 * sh.queue),
+                 (uintptr_t)b->n_events, (uintptr_t)b->n_tracks, (uintptr_t)b->n_hits, (uintptr_t)c->generation,
+                 u(b->hit_offsets), u(b->x), u(b->z), u(b->dxdy), u(b->w), u(b->trk_offsets),
+                 u(b->sx), u(b->sy), u(b->stx), u(b->sty), u(b->sqop),
+                 u(o->found), u(o->nhits), u(o->hit_idx), u(o->state), u(o->quality),
+                 u(o->out_offsets), u(o->out_trk), u(o->n_out)};
+    }
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         // first use of this shape: launch directly and remember it (bounded)

@@ -121,6 +121,15 @@ def test_repeated_launch_shape_direct_capture_replay(lfm):
     torch.cuda.synchronize()
     ref = oracle.run_batch(b, dumps=False)
     compare_outputs(out, ref)
+    # one output buffer replaced, the others kept: a new launch shape, so the
+    # results land in the new buffers (a replay would fill the old ones)
+    out2 = dict(out)
+    out2["hit_idx"] = torch.full_like(out["hit_idx"], -7)
+    out2["state"] = torch.full_like(out["state"], 7.0)
+    for _ in range(2):
+        tr.find(packed, b, b.n_events, "batched", out=out2)
+        torch.cuda.synchronize()
+        compare_outputs(out2, ref)
 
 
 def test_ragged_and_empty_events(lfm):
