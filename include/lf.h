@@ -260,7 +260,11 @@ void lf_host_free(void* p);
  * the compute of chunk k and the copies out of chunk k-1 overlap.  The
  * staging slots and the compute scratch belong to the context and are sized
  * before the first copy.  Synchronous: returns after the results are in host
- * memory.  chunk_hits <= 0 selects 1<<26. */
+ * memory.  chunk_hits <= 0 selects 1<<26.  LF_ERR_ARG, before anything is
+ * copied, when the offsets do not start at 0, decrease or do not end at
+ * n_hits / n_tracks, or when an input array the sizes need is NULL (a NULL
+ * output array is skipped); LF_ERR_CUDA on a copy or launch error, after
+ * the internal streams have drained. */
 lf_status lf_process_host(lf_ctx* ctx, const lf_host_batch* batch, const lf_host_output* out,
                           const lf_tuning* tuning, int64_t chunk_hits);
 

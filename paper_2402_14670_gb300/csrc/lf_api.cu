@@ -568,6 +568,14 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
     if (!hb->raw_offsets || !hb->trk_offsets) return fail(c, LF_ERR_ARG, "offsets are NULL");
     if (hb->raw_offsets[hb->n_events] != hb->n_hits || hb->trk_offsets[hb->n_events] != hb->n_tracks)
         return fail(c, LF_ERR_ARG, "offsets do not end at n_hits / n_tracks");
+    if (hb->raw_offsets[0] != 0 || hb->trk_offsets[0] != 0) return fail(c, LF_ERR_ARG, "offsets do not start at 0");
+    for (int e = 0; e < hb->n_events; ++e)
+        if (hb->raw_offsets[e + 1] < hb->raw_offsets[e] || hb->trk_offsets[e + 1] < hb->trk_offsets[e])
+            return fail(c, LF_ERR_ARG, "offsets decrease at event %d", e);
+    if (hb->n_hits > 0 && (!hb->x || !hb->z || !hb->dxdy || !hb->w || !hb->plane))
+        return fail(c, LF_ERR_ARG, "hit arrays are NULL");
+    if (hb->n_tracks > 0 && (!hb->sx || !hb->sy || !hb->stx || !hb->sty || !hb->sqop))
+        return fail(c, LF_ERR_ARG, "state arrays are NULL");
     if (hb->n_events == 0) return LF_OK;
     if (chunk_hits <= 0) chunk_hits = (int64_t)1 << 26;
     constexpr int NS = lf_ctx::NSLOT;

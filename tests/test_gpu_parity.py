@@ -329,6 +329,23 @@ def test_end_to_end_host_pipeline(lfm, chunk_hits):
     assert np.array_equal(res["found"].astype(bool), found)
 
 
+def test_end_to_end_refuses_bad_offsets(lfm):
+    """lf_process_host checks the host offsets before any copy: decreasing
+    offsets are refused with LF_ERR_ARG and the context stays usable."""
+    b = synth.generate(1, n_events=8)             # host tensors
+    tr = _tracker(lfm)
+    ro = b.raw_offsets.clone()
+    assert int(ro[2]) < int(ro[3])
+    b.raw_offsets[2] = ro[3]
+    b.raw_offsets[3] = ro[2]                      # same ends, decreasing at event 2
+    with pytest.raises(lfm.LFError) as ei:
+        tr.process_host(b)
+    assert ei.value.status == lfm.LF_ERR_ARG
+    b.raw_offsets.copy_(ro)
+    ho = tr.process_host(b)
+    assert int(ho["found"].sum()) > 0
+
+
 def test_host_arena_is_page_locked(lfm):
     """lf_host_alloc gives exact-size page-locked memory that torch sees as
     pinned, so copies from it are asynchronous."""
