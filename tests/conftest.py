@@ -11,3 +11,11 @@ if HERE not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
+
+
+def pytest_sessionstart(session):
+    # modules of the package load the CUDA library when imported: build it
+    # (a host compile, no GPU needed; a no-op when up to date) before any test
+    # module is collected
+    from paper_2402_14670_gb300 import build
+    build.build()
