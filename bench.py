@@ -231,6 +231,28 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def pack_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lf_pack.cu", "lf_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2402_14670_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def pack_traffic_per_launch(units_hits: int):
+    """DRAM bytes of k_pack_event from the committed ncu capture, scaled to
+    this launch by hits, or None when the pack kernel changed since."""
+    p = os.path.join(ROOT, "profiles", "find_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("pack_source_sha256_16") != pack_source_hash():
+        return None
+    k = [v for n, v in d.get("kernels", {}).items() if "k_pack" in n]
+    if len(k) != 1:
+        return None
+    return (float(k[0]["read_gb"]) + float(k[0]["write_gb"])) * 1e9 * units_hits / float(d["hits"])
+
+
 def find_profile():
     """The committed ncu figures of the find kernels (DRAM bytes and warp
     instructions of one launch on a 10 000-event slice), or None when the
@@ -533,7 +555,7 @@ def main():
     roof_pack = {"kernel": "k_pack_event (persistent per-event distribution sort, payload through shared memory)", "bound": "hbm",
                  "achieved": pk_algo / (pack_avg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                  "frac": pk_algo / (pack_avg / 1e3) / 1e9 / peak, "launch_ms": pack_avg,
-                 "algorithmic_bytes": pk_algo}
+                 "algorithmic_bytes": pk_algo, "traffic": pack_traffic_per_launch(n_hits)}
 
     # ---------------- CPU oracle on a bounded sample (rank 0, N = 1)
     cpu = None
