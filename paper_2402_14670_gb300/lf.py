@@ -243,7 +243,9 @@ def lf_host_free(ptr: int) -> None:
 class HostArena:
     """Page-locked host memory of an exact size from lf_host_alloc, carved
     into torch tensors (torch's own pinned allocator rounds multi-GB requests
-    up to a power of two)."""
+    up to a power of two).  The tensors are views of the arena's memory, not
+    owners of it: none may be used after close() (or the end of a ``with``
+    block), and no copy from or to them may still be in flight then."""
 
     def __init__(self, nbytes: int):
         self.nbytes = max(int(nbytes), 4096)
@@ -265,6 +267,12 @@ class HostArena:
             self.base = None
             lf_host_free(self.ptr)
             self.ptr = 0
+
+    def __enter__(self) -> "HostArena":
+        return self
+
+    def __exit__(self, *exc) -> None:
+        self.close()
 
 
 def lf_pack_hits(ctx, raw: lf_raw_hits, packed: lf_packed, stream) -> None:
