@@ -64,19 +64,6 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
     unsigned lo = __shfl_sync(FULL, (unsigned)v, src), hi = __shfl_sync(FULL, (unsigned)(v >> 32), src);
     return ((uint64_t)hi << 32) | lo;
 }
-__device__ __forceinline__ uint64_t shfl64_up(uint64_t v, int d) {
-    unsigned lo = __shfl_up_sync(FULL, (unsigned)v, d), hi = __shfl_up_sync(FULL, (unsigned)(v >> 32), d);
-    return ((uint64_t)hi << 32) | lo;
-}
-__device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        uint64_t u = ((uint64_t)__shfl_xor_sync(FULL, (unsigned)(v >> 32), o) << 32) |
-                     __shfl_xor_sync(FULL, (unsigned)v, o);
-        v = u < v ? u : v;
-    }
-    return v;
-}
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
