@@ -189,6 +189,90 @@ def pin_window_edges(orc):
             assert got[l] == sorted(expect[l]), ("window", p, q, pol, l, got[l], expect[l])
 
 
+def pin_window_edges_inclusive(orc):
+    """Reading R10 of Sec. "Defining the search windows": a window holds the
+    hits with xmin <= x <= xmax, so a hit lying exactly on either edge is
+    inside and the next binary32 value beyond the edge is outside.  The edges
+    are the ones the oracle reports for the track (their values are pinned by
+    pin_window_edges); the hits are placed on them bit for bit."""
+    for (tx, ty, qop) in ((0.05, 0.1, 0.1), (-0.12, -0.07, -1.0 / 4.0)):
+        st = synth.state_of(tx, ty, qop)
+        zone = 1 if ty >= 0 else 0
+        probe = orc.run_batch(make_batch([dict(hits=[(0, zone, 0.0)], states=[st])]))
+        xmin = probe["win_xmin"][0].astype(np.float32)
+        xmax = probe["win_xmax"][0].astype(np.float32)
+        hits, expect = [], {}
+        for l in range(12):
+            lo, hi = np.float32(xmin[l]), np.float32(xmax[l])
+            below = np.nextafter(lo, np.float32(-np.inf), dtype=np.float32)
+            above = np.nextafter(hi, np.float32(np.inf), dtype=np.float32)
+            expect[l] = [len(hits) + 1, len(hits) + 2]
+            for xv in (below, lo, hi, above):
+                hits.append((l, zone, float(xv)))
+        res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]))
+        got = raw_ids_in_windows(res, 0)
+        assert np.array_equal(res["win_xmin"][0], probe["win_xmin"][0])
+        for l in range(12):
+            assert got[l] == expect[l], ("inclusive window edges", tx, ty, qop, l, got[l], expect[l])
+
+
+def _extension_track(tx=0.05, ty=0.1, p=10.0, drop=(11,), offsets=None):
+    """Noise-free hits of one particle without the layers in `drop` (layer 11
+    dropped: configuration (3, 7, 11) cannot seed, so the only candidate is the
+    triplet (0, 4, 8), extended into layers 3 and 7 and the six stereo layers)."""
+    layers = [l for l in range(12) if l not in drop]
+    hits = track_hits(tx, ty, 1.0 / p, layers=layers, offsets=offsets)
+    return hits, synth.state_of(tx, ty, 1.0 / p)
+
+
+def pin_extension_T_x(orc):
+    """Sec. "Extending triplets to other layers": a hit in a missing x layer is
+    added when (x_hit - x_expected)^2 < T_x, x_expected from the three-point
+    solution through the triplet.  The particle's hits lie on the exact
+    trajectory model, so x_expected is the true x up to binary32 rounding
+    (~1e-4 mm); the layer-3 hit is moved by sqrt(T_x)*(1 -+ 1e-3) and must be
+    kept just inside and dropped just outside (T_x = 2 mm^2)."""
+    T_x = oracle.default_params()["T_x"]
+    for sign in (1.0, -1.0):
+        for f, kept in ((1.0 - 1e-3, True), (1.0 + 1e-3, False)):
+            d = sign * f * np.sqrt(T_x)
+            hits, st = _extension_track(offsets={3: d})
+            res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]))
+            assert res["found"][0], ("T_x", d)
+            assert res["n_trip"][0] == 1 and res["trip"][0, 0, 0] == 0
+            assert (res["hit_idx"][0, 3] >= 0) == kept, ("T_x acceptance", d, res["hit_idx"][0, 3])
+            assert res["nhits"][0] == (11 if kept else 10)
+            assert res["hit_idx"][0, 7] >= 0 and res["hit_idx"][0, 11] < 0
+
+
+def pin_extension_T_uv(orc):
+    """Sec. "Extending triplets to other layers" and Table tolerances: a stereo
+    hit is added when its squared distance (measured coordinate) to the x model
+    corrected by y_in * dxdy is below T_uv = max(T_uv_min, 50 (|t_x| + |t_y|)).
+    The layer-5 hit of a noise-free particle is moved by sqrt(T_uv)(1 -+ 1e-3):
+    kept just inside, dropped just outside; once with slopes that put T_uv on
+    its floor (2 mm^2) and once above it."""
+    p = oracle.default_params()
+    for tx, ty in ((0.008, 0.006), (0.09, 0.06)):
+        st = synth.state_of(tx, ty, 0.1)
+        t_uv = np.float32(p["T_uv_scale"]) * (np.float32(abs(np.float32(st[2]))) +
+                                              np.float32(abs(np.float32(st[3]))))
+        t_uv = max(np.float32(p["T_uv_min"]), np.float32(t_uv))
+        if tx < 0.05:
+            assert t_uv == np.float32(p["T_uv_min"])
+        else:
+            assert t_uv > 2.5 * p["T_uv_min"]
+        for sign in (1.0, -1.0):
+            for f, kept in ((1.0 - 1e-3, True), (1.0 + 1e-3, False)):
+                d = sign * f * float(np.sqrt(np.float64(t_uv)))
+                hits, st = _extension_track(tx, ty, offsets={5: d})
+                res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]))
+                assert res["found"][0], ("T_uv", tx, d)
+                assert (res["hit_idx"][0, 5] >= 0) == kept, ("T_uv acceptance", tx, d)
+                assert res["nhits"][0] == (11 if kept else 10)
+                assert res["hit_idx"][0, 6] >= 0
+
+
 def pin_window_cap(orc):
     tx, ty, qop = 0.05, 0.1, 1.0 / 20.0
     _, y, xm = synth.trajectory(tx, ty, qop)
@@ -619,7 +703,8 @@ def pin_no_ut_qop_unused(orc):
     assert r0["found"].sum() > 10
 
 
-ALL_PINS = [pin_pack_lexsort, pin_closed_form, pin_closed_form_md, pin_window_edges, pin_window_cap,
+ALL_PINS = [pin_pack_lexsort, pin_closed_form, pin_closed_form_md, pin_window_edges,
+            pin_window_edges_inclusive, pin_extension_T_x, pin_extension_T_uv, pin_window_cap,
             pin_closest_tie, pin_triplet_chi2_K, pin_top_n, pin_bending_filter,
             pin_magnet_tolerance, pin_known_residual_Q, pin_T_Q, pin_ty_cut, pin_invariants,
             pin_true_hits_in_window, pin_fit32_vs_fit64, pin_compact,

@@ -19,6 +19,18 @@ MUTANTS = [
     ("stereo correction with the wrong sign",
      "centre = (xn + tx_f * (g->z[l] - g->z[n])) - yl * g->dxdy[l];",
      "centre = (xn + tx_f * (g->z[l] - g->z[n])) + yl * g->dxdy[l];", ["pin_window_edges"]),
+    ("window lower edge exclusive", "while (i < hi && x[i] < v) ++i;", "while (i < hi && x[i] <= v) ++i;",
+     ["pin_window_edges_inclusive"]),
+    ("window upper edge exclusive", "while (i < hi && !(x[i] > v)) ++i;", "while (i < hi && x[i] < v) ++i;",
+     ["pin_window_edges_inclusive"]),
+    ("x-layer extension cut four times T_x", "if (dx * dx < p->T_x) cd->hit[l] = h;",
+     "if (dx * dx < 4.0f * p->T_x) cd->hit[l] = h;", ["pin_extension_T_x"]),
+    ("x-layer extension cut inclusive", "if (dx * dx < p->T_x) cd->hit[l] = h;",
+     "if (dx * dx <= 1.005f * p->T_x) cd->hit[l] = h;", ["pin_extension_T_x"]),
+    ("stereo extension cut four times T_uv", "if (dx * dx < T_uv) cd->hit[l] = h;",
+     "if (dx * dx < 4.0f * T_uv) cd->hit[l] = h;", ["pin_extension_T_uv"]),
+    ("stereo extension cut without the slope term", "T_uv = fmaxf(p->T_uv_min, T_uv);\n    for",
+     "T_uv = p->T_uv_min;\n    for", ["pin_extension_T_uv"]),
     ("window cap not symmetric", "start = c - cap / 2;", "start = c - cap / 4;", ["pin_window_cap"]),
     ("window cap not clamped at the low end", "if (start < lo) start = lo;", "", ["pin_window_cap"]),
     ("closest-hit tie to the higher index", "if (best < 0 || d < bd)", "if (best < 0 || d <= bd)",
