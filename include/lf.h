@@ -163,15 +163,22 @@ typedef struct {
 /* Launch shape of the persistent form (filled by the autotuner or the user;
  * zeros select the defaults). */
 typedef struct {
-    int32_t warps_per_block;   /* 1..16 */
-    int32_t blocks_per_sm;     /* resident blocks per SM of the persistent grid (0: as many as fit) */
+    int32_t warps_per_block;   /* tile kernel (queue 1, 2): 1..16 warps per block; ignored otherwise */
+    int32_t blocks_per_sm;     /* resident blocks per SM of the persistent grid (0: the kernel's default,
+                                  3 for the event kernel, as many as fit for the others) */
     int32_t grain;             /* tile kernel: input tracks per warp per step, 1 or 2 (default when
                                   n_triplets <= 16: the extension runs two tracks per warp, 16 lanes each) */
-    int32_t queue;             /* 0: pipeline of persistent stage kernels (windows, triplets, extension,
-                                  selection), each draining its own device work queue (default);
+    int32_t queue;             /* 0: pipeline of persistent stage kernels (windows, triplets, extension
+                                  with selection), each draining its own device work queue, window
+                                  hits staged per track (default);
                                   1: one tile kernel, blocks take tiles of tracks and their warps step
                                   through the stages together; 2: the tile kernel, warps take their
-                                  own tracks */
+                                  own tracks; 3: the event kernel: one persistent kernel whose blocks
+                                  take events from a device work queue and follow each event's
+                                  tracks zone by zone with the zone's hits staged once in shared
+                                  memory */
+    int32_t stage_hits;        /* event kernel: largest zone (hits) staged in shared memory; a larger
+                                  zone is read from global memory (0: what blocks_per_sm leaves) */
 } lf_tuning;
 
 /* Create a context: validates and copies geometry and parameters.

@@ -67,73 +67,43 @@ struct lf_ctx {
     size_t host_pin_cap = 0;
 };
 
-namespace {
+// ---- parameter checks and the kernels' parameter block, shared by every
+// entry point (lf_create and the context-free lf_find_tracks_static)
+namespace lfk {
 
-lf_status fail(lf_ctx* c, lf_status s, const char* fmt, ...) {
-    if (c) {
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(c->err, sizeof c->err, fmt, ap);
-        va_end(ap);
-    }
-    return s;
-}
+static bool finite(float v) { return v == v && v - v == 0.0f; }
 
-#define LF_CUDA(ctx, call)                                                                          \
-    do {                                                                                            \
-        cudaError_t e_ = (call);                                                                    \
-        if (e_ != cudaSuccess) return fail(ctx, LF_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-    } while (0)
-
-lf_status ensure(lf_ctx* c, DevBuf& b, size_t bytes) {
-    if (bytes == 0) bytes = 16;
-    if (b.cap >= bytes) return LF_OK;
-    ++c->generation;
-    if (b.p) {
-        cudaError_t e = cudaFree(b.p);  // synchronises: no call of this context is in flight
-        if (e != cudaSuccess) return fail(c, LF_ERR_CUDA, "cudaFree: %s", cudaGetErrorString(e));
-        b.p = nullptr;
-        b.cap = 0;
-    }
-    size_t want = bytes + bytes / 8;  // grow with headroom
-    cudaError_t e = cudaMalloc(&b.p, want);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, LF_ERR_OOM, "scratch allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
-    }
-    b.cap = want;
-    return LF_OK;
-}
-
-bool finite(float v) { return v == v && v - v == 0.0f; }
-
-lf_status check_params(lf_ctx* c, const lf_geometry* g, const lf_params* p) {
+bool param_error(const lf_geometry* g, const lf_params* p, char* msg, size_t n) {
+    auto bad = [&](const char* fmt, auto... a) {
+        snprintf(msg, n, fmt, a...);
+        return true;
+    };
     if (p->n_hits_window < 1 || p->n_hits_window > LF_MAX_WINDOW)
-        return fail(c, LF_ERR_ARG, "n_hits_window %d outside 1..%d", p->n_hits_window, LF_MAX_WINDOW);
+        return bad("n_hits_window %d outside 1..%d", p->n_hits_window, LF_MAX_WINDOW);
     if (p->n_triplets < 0 || p->n_triplets > LF_MAX_TRIPLETS)
-        return fail(c, LF_ERR_ARG, "n_triplets %d outside 0..%d", p->n_triplets, LF_MAX_TRIPLETS);
-    if (p->min_hits < 9 || p->min_hits > 12) return fail(c, LF_ERR_ARG, "min_hits %d outside 9..12", p->min_hits);
-    if (g->polarity != 1 && g->polarity != -1) return fail(c, LF_ERR_ARG, "polarity must be +1 or -1");
+        return bad("n_triplets %d outside 0..%d", p->n_triplets, LF_MAX_TRIPLETS);
+    if (p->min_hits < 9 || p->min_hits > 12) return bad("min_hits %d outside 9..12", p->min_hits);
+    if (g->polarity != 1 && g->polarity != -1) return bad("polarity must be +1 or -1");
     for (int l = 0; l < LF_N_LAYERS; ++l)
-        if (!finite(g->z[l]) || !finite(g->dxdy[l])) return fail(c, LF_ERR_ARG, "geometry of layer %d not finite", l);
+        if (!finite(g->z[l]) || !finite(g->dxdy[l])) return bad("geometry of layer %d not finite", l);
     for (int l = 1; l < LF_N_LAYERS; ++l)
-        if (!(g->z[l] > g->z[l - 1])) return fail(c, LF_ERR_ARG, "layer z must increase");
+        if (!(g->z[l] > g->z[l - 1])) return bad("layer z must increase");
     for (int l = 0; l < LF_N_LAYERS; ++l) {
         bool x = (l % 4 == 0) || (l % 4 == 3);
-        if (!x && g->dxdy[l] == 0.0f) return fail(c, LF_ERR_ARG, "stereo layer %d has dxdy 0", l);
+        if (!x && g->dxdy[l] == 0.0f) return bad("stereo layer %d has dxdy 0", l);
     }
-    if (!(g->z_magnet < g->z[0])) return fail(c, LF_ERR_ARG, "z_magnet must lie before the first layer");
-    if (!(p->magtol_max >= p->magtol_min)) return fail(c, LF_ERR_ARG, "magtol_max < magtol_min");
-    if (g->kappa == 0.0f) return fail(c, LF_ERR_ARG, "kappa must be non-zero");
-    if (p->no_ut != 0 && p->no_ut != 1) return fail(c, LF_ERR_ARG, "no_ut must be 0 or 1");
+    if (!(g->z_magnet < g->z[0])) return bad("z_magnet must lie before the first layer");
+    if (!(p->magtol_max >= p->magtol_min)) return bad("magtol_max < magtol_min");
+    if (g->kappa == 0.0f) return bad("kappa must be non-zero");
+    if (p->no_ut != 0 && p->no_ut != 1) return bad("no_ut must be 0 or 1");
     if (p->no_ut) {
         if (!(p->p_min > 0.0f) || !(p->pt_min > 0.0f) || !finite(p->p_min) || !finite(p->pt_min))
-            return fail(c, LF_ERR_ARG, "p_min and pt_min must be positive");
-        if (!(p->x_overlap >= 0.0f) || !finite(p->x_overlap)) return fail(c, LF_ERR_ARG, "x_overlap must be >= 0");
+            return bad("p_min and pt_min must be positive");
+        if (!(p->x_overlap >= 0.0f) || !finite(p->x_overlap)) return bad("x_overlap must be >= 0");
         for (int i = 0; i < 8; ++i)
-            if (!finite(p->tol_c[i])) return fail(c, LF_ERR_ARG, "tol_c[%d] not finite", i);
+            if (!finite(p->tol_c[i])) return bad("tol_c[%d] not finite", i);
     }
-    return LF_OK;
+    return false;
 }
 
 KParams make_kparams(const lf_geometry* g, const lf_params* p) {
@@ -184,6 +154,52 @@ KParams make_kparams(const lf_geometry* g, const lf_params* p) {
     k.pg = pol * g->gamma;
     k.D = g->dratio * 1000.0f;
     return k;
+}
+
+}  // namespace lfk
+
+namespace {
+
+lf_status fail(lf_ctx* c, lf_status s, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof c->err, fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define LF_CUDA(ctx, call)                                                                          \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return fail(ctx, LF_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+lf_status ensure(lf_ctx* c, DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.cap >= bytes) return LF_OK;
+    ++c->generation;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);  // synchronises: no call of this context is in flight
+        if (e != cudaSuccess) return fail(c, LF_ERR_CUDA, "cudaFree: %s", cudaGetErrorString(e));
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    size_t want = bytes + bytes / 8;  // grow with headroom
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, LF_ERR_OOM, "scratch allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+    }
+    b.cap = want;
+    return LF_OK;
+}
+
+lf_status check_params(lf_ctx* c, const lf_geometry* g, const lf_params* p) {
+    char msg[256];
+    if (lfk::param_error(g, p, msg, sizeof msg)) return fail(c, LF_ERR_ARG, "%s", msg);
+    return LF_OK;
 }
 
 KBatch to_kbatch(const lf_batch* b) {
@@ -358,18 +374,32 @@ lf_status lf_find_tracks(lf_ctx* c, const lf_batch* b, const lf_output* o, void*
 namespace {
 
 struct Shape {
-    int wpb, bps, grain, queue;
+    int wpb, bps, grain, queue, stage;
 };
 
+// queue modes of lf_tuning
+constexpr int Q_STAGES = 0, Q_TILE_SYNC = 1, Q_TILE = 2, Q_EVENT = 3;
+
 lf_status resolve_shape(lf_ctx* c, const lf_tuning* tuning, Shape& sh) {
-    sh.queue = tuning ? tuning->queue : 0;
-    if (sh.queue < 0 || sh.queue > 2) return fail(c, LF_ERR_ARG, "queue mode %d outside 0..2", sh.queue);
+    sh.queue = tuning ? tuning->queue : Q_STAGES;
+    sh.stage = 0;
+    if (sh.queue < 0 || sh.queue > 3) return fail(c, LF_ERR_ARG, "queue mode %d outside 0..3", sh.queue);
     sh.wpb = tuning && tuning->warps_per_block > 0 ? tuning->warps_per_block : 8;
-    sh.grain = (tuning && tuning->grain > 0 ? (tuning->grain & 15) : 0) + (sh.queue == 1 ? 16 : 0);
+    sh.grain = (tuning && tuning->grain > 0 ? (tuning->grain & 15) : 0) + (sh.queue == Q_TILE_SYNC ? 16 : 0);
     if (sh.wpb > 16) return fail(c, LF_ERR_ARG, "warps_per_block %d above 16", sh.wpb);
-    if (c->p.no_ut && sh.queue != 0)
-        return fail(c, LF_ERR_ARG, "the no-UT variant runs on the staged pipeline (queue 0) only");
-    if (sh.queue == 0) {
+    if (c->p.no_ut && (sh.queue == Q_TILE_SYNC || sh.queue == Q_TILE))
+        return fail(c, LF_ERR_ARG, "the no-UT variant runs on the event kernel or the stage pipeline only");
+    if (sh.queue == Q_EVENT) {
+        const int want = tuning && tuning->blocks_per_sm > 0 ? tuning->blocks_per_sm : 3;
+        if (tuning && tuning->stage_hits < 0) return fail(c, LF_ERR_ARG, "stage_hits %d negative", tuning->stage_hits);
+        sh.stage = tuning && tuning->stage_hits > 0 ? tuning->stage_hits : event_stage_cap_default(want);
+        int max_bps = 0;
+        LF_CUDA(c, event_max_blocks_per_sm(c->kp, sh.stage, &max_bps));
+        if (max_bps < 1) return fail(c, LF_ERR_ARG, "event kernel with %d staged hits does not fit on an SM", sh.stage);
+        sh.bps = want < max_bps ? want : max_bps;
+        return LF_OK;
+    }
+    if (sh.queue == Q_STAGES) {
         if (!c->stage_bps[0]) LF_CUDA(c, stage_blocks_per_sm(c->kp, c->stage_bps));
         sh.bps = tuning && tuning->blocks_per_sm > 0 ? tuning->blocks_per_sm : 0;
         return LF_OK;
@@ -386,7 +416,7 @@ lf_status resolve_shape(lf_ctx* c, const lf_tuning* tuning, Shape& sh) {
 lf_status prepare_batched(lf_ctx* c, const lf_batch* b, const Shape& sh) {
     lf_status st;
     if ((st = ensure(c, c->ev_count, (size_t)b->n_events * 4)) != LF_OK) return st;
-    if (sh.queue == 0) {
+    if (sh.queue == Q_EVENT || sh.queue == Q_STAGES) {
         const size_t nt = (size_t)b->n_tracks, NT = (size_t)(c->p.n_triplets > 0 ? c->p.n_triplets : 1);
         const size_t ns = c->p.no_ut ? 2 : 1;
         if ((st = ensure(c, c->trk_event, nt * 4)) != LF_OK) return st;
@@ -410,7 +440,10 @@ lf_status launch_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const
     KOut ko = to_kout(o);
     LF_CUDA(c, cudaMemsetAsync(c->cursor, 0, 8 * sizeof(int), s));
     if (b->n_tracks > 0) {
-        if (sh.queue == 0) {
+        if (sh.queue == Q_EVENT) {
+            LF_CUDA(c, launch_event(c->kp, kb, ko, (int*)c->wbeg.p, (uint8_t*)c->wcnt.p, (uint64_t*)c->keys.p,
+                                    (uint8_t*)c->ntrip.p, c->cursor, c->status, sh.stage, sh.bps * c->n_sm, s));
+        } else if (sh.queue == Q_STAGES) {
             auto* te = (int*)c->trk_event.p;
             auto* wb = (int*)c->wbeg.p;
             auto* wc = (uint8_t*)c->wcnt.p;
@@ -453,7 +486,7 @@ lf_status lf_find_tracks_batched(lf_ctx* c, const lf_batch* b, const lf_output* 
     GraphKey key;
     {
         const auto u = [](const void* q) { return (uintptr_t)q; };
-        key.v = {(uintptr_t)sh.wpb, (uintptr_t)sh.bps, (uintptr_t)(sh.grain + 64 * sh.queue),
+        key.v = {(uintptr_t)sh.wpb, (uintptr_t)sh.bps, (uintptr_t)(sh.grain + 64 * sh.queue + ((uintptr_t)sh.stage << 8)),
                  (uintptr_t)b->n_events, (uintptr_t)b->n_tracks, (uintptr_t)b->n_hits, (uintptr_t)c->generation,
                  u(b->hit_offsets), u(b->x), u(b->z), u(b->dxdy), u(b->w), u(b->trk_offsets),
                  u(b->sx), u(b->sy), u(b->stx), u(b->sty), u(b->sqop),

@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include "lf.h"
+
 namespace lfk {
 
 constexpr int NL = 12;
@@ -100,6 +102,12 @@ __host__ __device__ inline size_t block_smem_bytes(int cap, int nw, int tpw) {
     return size_t(nw) * tpw * slot_bytes(cap) + size_t(nw) * scratch_bytes();
 }
 
+// ---- parameters (lf_api.cu), shared by every entry point ----
+// true (message in msg) when a geometry or parameter value is outside its range
+bool param_error(const lf_geometry* g, const lf_params* p, char* msg, size_t n);
+// the kernels' parameter block from a checked geometry and parameter set
+KParams make_kparams(const lf_geometry* g, const lf_params* p);
+
 // ---- launchers (defined in the .cu files) ----
 // persistent per-event pack; cursor: two device ints (the work queues)
 cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, const float* dxdy,
@@ -128,6 +136,14 @@ cudaError_t stage_blocks_per_sm(const KParams& k, int* out4);
 cudaError_t launch_fused(const KParams& k, const KBatch& b, const KOut& o, int* cursor, int grain,
                          int warps_per_block, int n_blocks, cudaStream_t s);
 cudaError_t fused_max_blocks_per_sm(const KParams& k, int warps_per_block, int grain, int* out);
+// per-event persistent kernel (lf_event.cu): a block per event zone, the
+// zone's x staged in shared memory (stage_cap hits at most, else read from
+// global memory); windows, keys and counts pass through wbeg/wcnt/keys/ntrip
+cudaError_t launch_event(const KParams& k, const KBatch& b, const KOut& o, int* wbeg, uint8_t* wcnt, uint64_t* keys,
+                         uint8_t* ntrip, int* cursor, int* status, int stage_cap, int blocks, cudaStream_t s);
+cudaError_t event_max_blocks_per_sm(const KParams& k, int stage_cap, int* out);
+// staging capacity (hits) that lets blocks_per_sm blocks share an SM
+int event_stage_cap_default(int blocks_per_sm);
 cudaError_t launch_hits_to_raw(const uint8_t* found, int* hit_idx, const int* perm, int n_tracks, int base,
                               cudaStream_t s);
 cudaError_t launch_compact(const int* trk_offsets, const uint8_t* found, int n_events, int* ev_count,

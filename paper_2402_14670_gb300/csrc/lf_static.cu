@@ -53,49 +53,6 @@ lf_status scratch_address(int** out) {
     return LF_OK;
 }
 
-bool finite_f(float v) { return v == v && v - v == 0.0f; }
-
-// same ranges lf_create enforces
-bool params_ok(const lf_geometry* g, const lf_params* p) {
-    if (p->n_hits_window < 1 || p->n_hits_window > LF_MAX_WINDOW) return false;
-    if (p->n_triplets < 0 || p->n_triplets > LF_MAX_TRIPLETS) return false;
-    if (p->min_hits < 9 || p->min_hits > 12) return false;
-    if (g->polarity != 1 && g->polarity != -1) return false;
-    for (int l = 0; l < LF_N_LAYERS; ++l) {
-        if (!finite_f(g->z[l]) || !finite_f(g->dxdy[l])) return false;
-        if (l > 0 && !(g->z[l] > g->z[l - 1])) return false;
-        bool x = (l % 4 == 0) || (l % 4 == 3);
-        if (!x && g->dxdy[l] == 0.0f) return false;
-    }
-    if (!(g->z_magnet < g->z[0]) || !(p->magtol_max >= p->magtol_min) || g->kappa == 0.0f) return false;
-    if (p->no_ut != 0) return false;  // the tile kernel follows VELO-UT input only
-    return true;
-}
-
-lfk::KParams kparams(const lf_geometry* g, const lf_params* p) {
-    lfk::KParams k{};
-    for (int l = 0; l < lfk::NL; ++l) {
-        k.z[l] = g->z[l];
-        k.dxdy[l] = g->dxdy[l];
-    }
-    k.z_state = g->z_state; k.z_magnet = g->z_magnet; k.z_ref = g->z_ref;
-    k.kappa = g->kappa; k.gamma = g->gamma; k.dratio = g->dratio; k.polarity = g->polarity;
-    k.xtol_c = p->xtol_c; k.xtol_p = p->xtol_p; k.x_asym = p->x_asym; k.uv_tol = p->uv_tol;
-    k.cap = p->n_hits_window; k.n_trip = p->n_triplets; k.min_hits = p->min_hits;
-    k.K_first = p->K_first; k.K_last = p->K_last; k.p_bend = p->p_bend;
-    k.magtol_min = p->magtol_min; k.magtol_max = p->magtol_max; k.magtol_c = p->magtol_c; k.magtol_tx = p->magtol_tx;
-    k.T_triplet = p->T_triplet; k.T_x = p->T_x; k.inv_T_x = lfk::pow2_reciprocal(p->T_x); k.T_uv_scale = p->T_uv_scale; k.T_uv_min = p->T_uv_min;
-    k.T_ty = p->T_ty; k.T_y = p->T_y; k.T_Q = p->T_Q;
-    for (int i = 0; i < 4; ++i) k.C_n[i] = p->C_n[i];
-    k.no_ut = 0;
-    volatile float pol = (float)g->polarity;
-    k.pol_f = pol;
-    k.pk = pol * g->kappa;
-    k.pg = pol * g->gamma;
-    k.D = g->dratio * 1000.0f;
-    return k;
-}
-
 }  // namespace
 
 extern "C" lf_status lf_find_tracks_static(const lf_geometry* geometry, const lf_params* params, const lf_batch* b,
@@ -103,7 +60,9 @@ extern "C" lf_status lf_find_tracks_static(const lf_geometry* geometry, const lf
     if (!geometry || !params || !b || !o) return LF_ERR_ARG;
     if (b->n_events > LF_STATIC_MAX_EVENTS) return LF_ERR_CAPACITY;
     if (b->n_events < 0 || b->n_tracks < 0 || b->n_hits < 0) return LF_ERR_ARG;
-    if (!params_ok(geometry, params)) return LF_ERR_ARG;
+    char msg[256];
+    if (lfk::param_error(geometry, params, msg, sizeof msg)) return LF_ERR_ARG;
+    if (params->no_ut != 0) return LF_ERR_ARG;  // the tile kernel follows VELO-UT input only
     if (!b->hit_offsets || !b->trk_offsets || !o->out_offsets || !o->n_out) return LF_ERR_ARG;
     if (b->n_hits > 0 && (!b->x || !b->z || !b->dxdy || !b->w)) return LF_ERR_ARG;
     if (b->n_tracks > 0 && (!b->sx || !b->sy || !b->stx || !b->sty || !b->sqop || !o->found || !o->nhits ||
@@ -113,9 +72,12 @@ extern "C" lf_status lf_find_tracks_static(const lf_geometry* geometry, const lf
     lf_status st = scratch_address(&scratch);
     if (st != LF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const lfk::KParams k = kparams(geometry, params);
+    const lfk::KParams k = lfk::make_kparams(geometry, params);
     int dev = 0, n_sm = 0, bps = 0;
-    const int wpb = 8, grain = 16;  // block tiles, stage barriers, two tracks per warp
+    // block tiles with stage barriers (grain bit 4); tracks per warp follow
+    // n_triplets (two, 16 lanes each, when n_triplets <= 16), as in
+    // lf_find_tracks_batched with queue 1
+    const int wpb = 8, grain = 16;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return LF_ERR_CUDA;

@@ -46,32 +46,11 @@
 #include <climits>
 #include <cstdint>
 
+#include "lf_device.cuh"
 #include "lf_internal.h"
 
 namespace lfk {
 
-constexpr unsigned FULL = 0xffffffffu;
-constexpr uint64_t NOKEY = ~0ull;
-
-struct TState {
-    float xs, ys, txs, tys, qop;
-};
-
-__device__ __forceinline__ bool is_x(int l) { return (l & 3) == 0 || (l & 3) == 3; }
-__device__ __forceinline__ int neighbour_x(int l) { return ((l & 3) == 1) ? (l >> 2) * 4 : (l >> 2) * 4 + 3; }
-
-__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
-    unsigned lo = __shfl_sync(FULL, (unsigned)v, src), hi = __shfl_sync(FULL, (unsigned)(v >> 32), src);
-    return ((uint64_t)hi << 32) | lo;
-}
-__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int u = __shfl_up_sync(FULL, v, o);
-        if (lane >= o) v += u;
-    }
-    return v;
-}
 
 // first index in [lo, hi) whose x is not left of v: left means x < v (lower
 // bound, upper = false) or !(x > v) (upper bound, upper = true); one loop for
@@ -141,9 +120,6 @@ __device__ __forceinline__ int closest_smem(const float* x, int n, float e) {
     return best;
 }
 
-// IEEE quotient, out of line (keeps rarely taken or repeated divisions out of
-// the unrolled loops' code)
-__device__ __noinline__ float div_call(float a, float b) { return a / b; }
 
 // the same search, out of line, on a window given by its shared-memory address
 __device__ __noinline__ int closest_shared(unsigned xs, int n, float e) {
@@ -174,81 +150,6 @@ __device__ __noinline__ int closest_shared(unsigned xs, int n, float e) {
     return best;
 }
 
-// ----------------------------------------------------------- stage: windows
-
-// x of the input track extrapolated to layer l (straight line to the magnet
-// centre, kick, T-station model of Eq. trackfitmodel).
-__device__ __forceinline__ float x_extrap(const KParams& k, const TState& s, int l) {
-    float x_mag = s.xs + s.txs * (k.z_magnet - k.z_state);
-    float tx_f = s.txs + k.pk * s.qop;
-    float c = k.pg * s.qop;
-    float dz = k.z[l] - k.z_ref;
-    float t1 = tx_f * (k.z[l] - k.z_magnet);
-    float t2 = c * (dz * dz);
-    float t3 = 1.0f + k.dratio * dz;
-    return (x_mag + t1) + t2 * t3;
-}
-
-// Assumed inverse momentum of a track without a momentum estimate: the
-// tighter of p_min and pt_min / sin(theta) (Sec. "No-UT tuning").
-__device__ __forceinline__ float no_ut_inv_p(const KParams& k, const TState& s) {
-    float t2 = s.txs * s.txs + s.tys * s.tys;
-    float sin_theta = sqrtf(t2) / sqrtf(1.0f + t2);
-    float ip_pt = sin_theta / k.pt_min;
-    float ip_p = 1.0f / k.p_min;
-    return fminf(ip_p, ip_pt);
-}
-
-// Eq. tol_noUT (coefficients of Table poly_tol), ip = 1/p
-__device__ __forceinline__ float no_ut_xtol(const KParams& k, float ip, float tx, float ty) {
-    float a = k.tol_c[0] + tx * (k.tol_c[1] + k.tol_c[2] * tx);
-    float b = (ty * ty) * (k.tol_c[3] + tx * (k.tol_c[4] + k.tol_c[5] * tx));
-    float d = ip * (k.tol_c[6] * tx + k.tol_c[7] * ip);
-    return ip * ((a + b) + d);
-}
-
-// Limits and centre of the window of layer l.  NOUT: window set `side` of
-// Eq. noUT_size_window (side 0 reaches x_tol below the straight line and
-// x_overlap above it, side 1 the mirror image; u/v layers alike with uv_tol).
-template <bool NOUT>
-__device__ __forceinline__ void window_limits(const KParams& k, const TState& s, int l, int side, float& xmin,
-                                              float& xmax, float& centre) {
-    if (NOUT) {
-        float tol;
-        if (is_x(l)) {
-            centre = s.xs + s.txs * (k.z[l] - k.z_state);
-            tol = no_ut_xtol(k, no_ut_inv_p(k, s), s.txs, s.tys);
-        } else {
-            int n = neighbour_x(l);
-            float xn = s.xs + s.txs * (k.z[n] - k.z_state);
-            float yl = s.ys + s.tys * (k.z[l] - k.z_state);
-            centre = (xn + s.txs * (k.z[l] - k.z[n])) - yl * k.dxdy[l];
-            tol = k.uv_tol;
-        }
-        xmin = side ? centre - k.x_overlap : centre - tol;
-        xmax = side ? centre + tol : centre + k.x_overlap;
-        return;
-    }
-    const float pmom = 1.0f / fabsf(s.qop);
-    if (is_x(l)) {
-        float x_tol = k.xtol_c + k.xtol_p / pmom;
-        bool qpos = s.qop >= 0.0f;
-        bool mu = k.polarity > 0;
-        float a_left = ((qpos && mu) || (!qpos && !mu)) ? k.x_asym : 0.0f;
-        float a_right = ((!qpos && mu) || (qpos && !mu)) ? k.x_asym : 0.0f;
-        centre = x_extrap(k, s, l);
-        xmin = (centre - x_tol) - a_left;
-        xmax = (centre + x_tol) + a_right;
-    } else {
-        int n = neighbour_x(l);
-        float tx_f = s.txs + k.pk * s.qop;
-        float xn = x_extrap(k, s, n);
-        float yl = s.ys + s.tys * (k.z[l] - k.z_state);
-        centre = (xn + tx_f * (k.z[l] - k.z[n])) - yl * k.dxdy[l];
-        xmin = centre - k.uv_tol;
-        xmax = centre + k.uv_tol;
-    }
-}
 
 // Windows of all twelve layers, [begin, begin+count) in packed hit indices,
 // returned on lanes 0..11: lanes 0..11 search the lower bounds and lanes
@@ -283,15 +184,6 @@ __device__ __forceinline__ void warp_windows(const KParams& k, const KBatch& b, 
     }
 }
 
-__device__ __forceinline__ TState load_state(const KBatch& b, int t) {
-    TState s;
-    s.xs = __ldg(b.sx + t);
-    s.ys = __ldg(b.sy + t);
-    s.txs = __ldg(b.stx + t);
-    s.tys = __ldg(b.sty + t);
-    s.qop = __ldg(b.sqop + t);
-    return s;
-}
 
 // ------------------------------------------------------- shared-memory slots
 
@@ -391,47 +283,6 @@ __device__ __forceinline__ void stage_windows(const KParams& k, const KBatch& b,
     stage_finish<1, XONLY>(k, &m, lane);
 }
 
-__device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
-    unsigned lo = __shfl_xor_sync(FULL, (unsigned)v, m), hi = __shfl_xor_sync(FULL, (unsigned)(v >> 32), m);
-    return ((uint64_t)hi << 32) | lo;
-}
-
-// Bitonic sort of 64 keys held two per lane (element lane in a, lane+32 in
-// b), ascending.
-__device__ __forceinline__ void warp_sort64(uint64_t& a, uint64_t& b, int lane) {
-#pragma unroll
-    for (int kk = 2; kk <= 64; kk <<= 1) {
-#pragma unroll
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            if (j == 32) {
-                uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
-                a = lo;
-                b = hi;
-            } else {
-                uint64_t pa = shfl_xor64(a, j), pb = shfl_xor64(b, j);
-                bool lower = (lane & j) == 0;
-                bool up_a = (lane & kk) == 0, up_b = ((lane + 32) & kk) == 0;
-                a = (lower == up_a) ? (a < pa ? a : pa) : (a < pa ? pa : a);
-                b = (lower == up_b) ? (b < pb ? b : pb) : (b < pb ? pb : b);
-            }
-        }
-    }
-}
-
-// Bitonic sort of 32 keys, one per lane, ascending.
-__device__ __forceinline__ uint64_t warp_sort32(uint64_t v, int lane) {
-#pragma unroll
-    for (int kk = 2; kk <= 32; kk <<= 1) {
-#pragma unroll
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            uint64_t o = shfl_xor64(v, j);
-            bool lower = (lane & j) == 0;
-            bool up = (lane & kk) == 0;
-            v = (lower == up) ? (v < o ? v : o) : (v < o ? o : v);
-        }
-    }
-    return v;
-}
 
 // Sort the buffered keys; keep the NT smallest at the front of the buffer.
 // Returns the new buffer size; thr becomes the NT-th smallest key once the
@@ -620,18 +471,6 @@ __device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState&
 
 // --------------------------------------------------- stage: extension + fit
 
-struct Cand {
-    int status;   // 0 accepted, 1 degenerate, 2 too few hits, 3 no stereo hit in a station, 4 t_y, 5 Q
-    float Q;
-    int hl[NL];
-    int n;
-    float st[6];
-};
-
-__device__ __forceinline__ float f2_of(float u, float D) { return (u * u) * (1.0f + D * u); }
-__device__ __forceinline__ float model_x(float A, float T, float C, float u, float D) {
-    return (A + T * u) + C * f2_of(u, D);
-}
 
 // Extension and fit of one triplet (Sec. "Extending triplets to other
 // layers", "Quality Filter"); x and z of the window hits come from the
@@ -823,40 +662,6 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
     cd.st[5] = (tx - s.txs) / k.pk;
 }
 
-// ---------------------------------------------------------- stage: selection
-
-// Lowest Q among the accepted candidates of a group of G consecutive lanes
-// (G = 16 or 32; candidate rank = lane within the group; ties to the lower
-// rank).  The winner writes the track's output; without a winner the
-// group's first lane writes found = 0.
-template <int G>
-__device__ __forceinline__ void group_select_write(const KOut& o, int t, bool live, int rank, bool have, float Q,
-                                                   int n, const int* hglob, const float* st) {
-    uint64_t key = have ? (((uint64_t)__float_as_uint(Q) << 32) | (unsigned)rank) : NOKEY;
-    uint64_t best = key;
-#pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) {
-        uint64_t u = shfl_xor64(best, off);
-        best = u < best ? u : best;
-    }
-    if (!live) return;
-    if (best == NOKEY) {
-        if (rank == 0) {
-            o.found[t] = 0;
-            o.nhits[t] = 0;
-        }
-        return;
-    }
-    if (have && key == best) {
-#pragma unroll
-        for (int l = 0; l < NL; ++l) o.hit_idx[(size_t)t * NL + l] = hglob[l];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) o.state[(size_t)t * 6 + q] = st[q];
-        o.quality[t] = Q;
-        o.nhits[t] = (uint8_t)n;
-        o.found[t] = 1;
-    }
-}
 
 // ------------------------------------------------------------ event lookup
 
@@ -884,11 +689,6 @@ __global__ void k_track_event(KBatch b, int* trk_event) {
 // warp index, the persistent kernel (P = true) is sized to the GPU and its
 // warps take tracks from the stage's device work queue (an atomic cursor)
 // until it is empty.
-__device__ __forceinline__ int queue_take(int* cursor, int n, int lane) {
-    int v = 0;
-    if (lane == 0) v = atomicAdd(cursor, n);
-    return __shfl_sync(FULL, v, 0);
-}
 
 // Window sets in scratch: set ws = t (VELO-UT) or 2t + side (no-UT), its
 // twelve windows at [ws * 12, ws * 12 + 12).

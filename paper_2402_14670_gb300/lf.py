@@ -85,7 +85,14 @@ class lf_host_output(C.Structure):
 
 class lf_tuning(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("grain", C.c_int32),
-                ("queue", C.c_int32)]
+                ("queue", C.c_int32), ("stage_hits", C.c_int32)]
+
+
+def tuning_struct(tuning: Optional[dict]) -> Optional[lf_tuning]:
+    """lf_tuning from a dict of its fields (missing fields 0 = defaults)."""
+    if not tuning:
+        return None
+    return lf_tuning(*(int(tuning.get(f, 0)) for f, _ in lf_tuning._fields_))
 
 
 _lib.lf_create.argtypes = [C.POINTER(lf_geometry), C.POINTER(lf_params), C.POINTER(_P)]
@@ -400,10 +407,7 @@ class Tracker:
         if mode == "plain":
             lf_find_tracks(self.ctx, b, o, _stream(stream))
         elif mode == "batched":
-            tu = None
-            if tuning:
-                tu = lf_tuning(int(tuning.get("warps_per_block", 0)), int(tuning.get("blocks_per_sm", 0)),
-                               int(tuning.get("grain", 0)), int(tuning.get("queue", 0)))
+            tu = tuning_struct(tuning)
             lf_find_tracks_batched(self.ctx, b, o, tu, _stream(stream))
         else:
             raise ValueError(mode)
@@ -429,10 +433,7 @@ class Tracker:
 
     def reserve(self, n_events: int, n_tracks: int, tuning: Optional[dict] = None) -> None:
         """Size the persistent form's scratch for batches up to these sizes."""
-        tu = None
-        if tuning:
-            tu = lf_tuning(int(tuning.get("warps_per_block", 0)), int(tuning.get("blocks_per_sm", 0)),
-                           int(tuning.get("grain", 0)), int(tuning.get("queue", 0)))
+        tu = tuning_struct(tuning)
         lf_reserve(self.ctx, n_events, n_tracks, tu)
 
     @staticmethod
@@ -463,10 +464,7 @@ class Tracker:
                            h(batch.z), h(batch.dxdy), h(batch.w), h(batch.plane), h(batch.trk_offsets), h(batch.sx),
                            h(batch.sy), h(batch.stx), h(batch.sty), h(batch.sqop))
         ho = lf_host_output(h(out["found"]), h(out["nhits"]), h(out["hit_idx"]), h(out["state"]), h(out["quality"]))
-        tu = None
-        if tuning:
-            tu = lf_tuning(int(tuning.get("warps_per_block", 0)), int(tuning.get("blocks_per_sm", 0)),
-                           int(tuning.get("grain", 0)), int(tuning.get("queue", 0)))
+        tu = tuning_struct(tuning)
         lf_process_host(self.ctx, hb, ho, tu, int(chunk_hits))
         return out
 

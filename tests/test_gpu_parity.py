@@ -1,7 +1,8 @@
 """CUDA library against the oracle, element by element, on the same inputs.
 
-Both forms (plain: one kernel per stage; batched: persistent stage kernels over
-device work queues) must give the oracle's packed hits bit for bit, the same windows and triplet
+Both forms (plain: one kernel per stage; batched: the persistent event kernel,
+or on request the persistent stage kernels or the tile kernel, over device
+work queues) must give the oracle's packed hits bit for bit, the same windows and triplet
 lists, the same selected hit lists for every input track and the same states
 and Q (compared bit for bit, within 1e-4 relative at worst).
 """
@@ -81,7 +82,11 @@ def test_parameter_edges(lfm, cap, nt):
         run_both(tr, b, mode=mode, params=p, stages=(mode == "plain" and nt > 0))
 
 
-@pytest.mark.parametrize("tuning", [dict(queue=0, blocks_per_sm=1),
+@pytest.mark.parametrize("tuning", [dict(queue=3),
+                                    dict(queue=3, blocks_per_sm=1),
+                                    dict(queue=3, blocks_per_sm=2, stage_hits=3000),
+                                    dict(queue=3, stage_hits=1),
+                                    dict(queue=0, blocks_per_sm=1),
                                     dict(queue=0),
                                     dict(queue=2, warps_per_block=1, grain=1, blocks_per_sm=1),
                                     dict(queue=2, warps_per_block=4, grain=2),
@@ -92,6 +97,51 @@ def test_launch_shapes_identical(lfm, tuning):
     b = synth.generate(1, n_events=120).to("cuda")
     tr = _tracker(lfm)
     run_both(tr, b, mode="batched", tuning=tuning)
+
+
+def _jitter_z(b, frac_events=0.5, seed=5):
+    """Move the z of one hit in every few hundred (of half the events) by up to
+    +-0.5 mm: buckets whose hits no longer share one z."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    ro = b.raw_offsets.cpu()
+    z = b.z.cpu().clone()
+    for e in range(b.n_events):
+        if torch.rand(1, generator=g).item() >= frac_events:
+            continue
+        h0, h1 = int(ro[e]), int(ro[e + 1])
+        n = h1 - h0
+        pick = torch.randint(h0, h1, (max(1, n // 300),), generator=g)
+        z[pick] += (torch.rand(len(pick), generator=g) - 0.5).to(torch.float32)
+    b.z = z.to(b.z.device)
+    return b
+
+
+@pytest.mark.parametrize("mode,tuning", [("plain", None), ("batched", None), ("batched", dict(queue=3)),
+                                         ("batched", dict(queue=3, stage_hits=1))])
+def test_hits_with_their_own_z(lfm, mode, tuning):
+    """Hits of a layer at different z (one in a few hundred moved by up to
+    0.5 mm): every kernel takes each hit's own z, as the oracle does, instead
+    of a per-bucket constant."""
+    b = _jitter_z(synth.generate(1, n_events=120)).to("cuda")
+    tr = _tracker(lfm)
+    info, *_ = run_both(tr, b, mode=mode, tuning=tuning)
+    assert info["n_found"] > 3000
+
+
+def test_event_kernel_stage_sizes_identical(lfm):
+    """The event kernel stages a zone's hits in shared memory up to its
+    staging capacity and reads larger zones from global memory: capacities
+    below, inside and above the zone sizes of an uneven batch give identical
+    outputs (equal to the oracle's)."""
+    b = synth.generate(2, n_events=60).to("cuda")
+    tr = _tracker(lfm)
+    ref = None
+    for stage in (1, 2000, 6000, 0):
+        info, packed, out, res = run_both(tr, b, mode="batched", tuning=dict(queue=3, stage_hits=stage))
+        if ref is None:
+            ref = {k: to_np(v).copy() for k, v in out.items()}
+        else:
+            assert np.array_equal(to_np(out["found"]), ref["found"])
 
 
 def test_repeated_launch_shape_direct_capture_replay(lfm):
