@@ -52,8 +52,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-no-ut", action="store_true", help="skip the no-UT variant measurement")
-    ap.add_argument("--cpu-events", type=int, default=3000, help="oracle sample size (events)")
-    ap.add_argument("--tuning", type=str, default=None, help="json of warps_per_block/blocks_per_sm/grain")
+    ap.add_argument("--cpu-events", type=int, default=5000, help="oracle sample size (events)")
+    ap.add_argument("--tuning", type=str, default=None, help="json of lf_tuning fields (skips the autotuner)")
+    ap.add_argument("--no-tune", action="store_true", help="default launch shape instead of the autotuner's")
     return ap.parse_args()
 
 
@@ -203,6 +204,23 @@ def per_batch_plain(tr, batch, packed, out, size: int):
     return run
 
 
+def workload_recipe(cfg) -> str:
+    """One line describing a synthetic workload's event recipe."""
+    n_in = cfg.n_in
+    if n_in[0] == "negbin":
+        trk = "NegBin(mean %g, r=%g) input tracks per event clipped to [%d,%d]" % n_in[1:]
+    elif n_in[0] == "poisson":
+        trk = "Poisson(%g) input tracks per event" % n_in[1]
+    elif n_in[0] == "uniform":
+        trk = "U{%d..%d} input tracks per event" % n_in[1:]
+    else:
+        trk = "%d input tracks per event" % n_in[1]
+    noise = ("%d%% noise hits" % round(100 * cfg.noise[1])) if cfg.noise[0] == "frac" else \
+        ("%d noise hits per layer" % cfg.noise[1])
+    return "%s, %d%% matched to a particle, p %g-%g GeV, %s" % (trk, round(100 * cfg.match_frac), cfg.p_min,
+                                                               cfg.p_max, noise)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -345,6 +363,14 @@ def main():
     tr = lf.Tracker()
     stream = torch.cuda.current_stream()
     packed = tr.pack(batch)
+    tune_times = None
+    if tuning is None and not args.no_tune:
+        # the launch shape from the autotuner (timed candidates on this batch,
+        # outside the timed region)
+        from paper_2402_14670_gb300.autotune import Autotuner, bucket_of
+        tuner = Autotuner(reps=2)
+        tuning = tuner.tune(tr, packed, batch, n_ev)
+        tune_times = tuner.timings[tuner._key(bucket_of(n_ev, batch.n_tracks))]
     out = tr.find(packed, batch, n_ev, "batched", tuning)
     torch.cuda.synchronize()
     flags = tr.status()
@@ -585,11 +611,10 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "%s (config %d): %d events, %d hits, %d input tracks; NegBin(80, r=2) tracks "
-                                   "per event clipped to [1,400], 100-150 hits per track + 30%% noise"
-                                   % (cfg.name, args.config, n_ev, n_hits, n_trk),
+            "config": {"workload": "%s (config %d): %d events, %d hits, %d input tracks; %s"
+                                   % (cfg.name, args.config, n_ev, n_hits, n_trk, workload_recipe(cfg)),
                        "form": "batched: persistent stage kernels with device work queues, one CUDA graph",
-                       "tuning": tuning or "defaults",
+                       "tuning": tuning or "defaults", "tuning_candidates_ms": tune_times,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "single"},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk,
             "roofline": roof, "roofline_issue": roof_issue, "roofline_pack": roof_pack, "plain": plain,

@@ -115,6 +115,19 @@ typedef struct {
     float p_min, pt_min;       /* GeV, > 0 */
     float x_overlap;           /* mm, >= 0 */
     float tol_c[8];            /* c0..c7 (Table poly_tol) */
+    /* Sec. "Calculation of momentum and track states": the q/p of a found
+     * track.  qop_poly = 0: linear kick, (t_x,fit - t_x,in) / (polarity kappa).
+     * qop_poly = 1: Eq. pt_kick, q/p = (t_x,f / sqrt(1 + t_x,f^2 + t_y,f^2) -
+     * t_x,i / sqrt(1 + t_x,i^2 + t_y,i^2)) / (polarity F), f = the fit at
+     * z_ref, i = the input state, with the field integral F = c_0 + d (c_1 +
+     * d (c_2 + d (c_3 + d c_4))), d = t_x,f - t_x,i, and c_i = sum_j
+     * qop_c[i][j] t_x,i^k t_y,i^m over the (k, m) of entry j: for even i
+     * (0,0) (0,2) (0,4) (0,6) (2,0) (2,2) (2,4) (4,0) (4,2) (6,0), for odd i
+     * (1,0) (1,2) (1,4) (3,0) (3,2) (5,0) (entries 6..9 unused), summed in
+     * entry order.  The coefficients come from a fit on toy tracks
+     * (paper_2402_14670_gb300.qop_fit). */
+    int32_t qop_poly;          /* 0 or 1 */
+    float qop_c[5][10];
 } lf_params;
 
 /* Raw hits of n_events events, unsorted inside each event (device). */
@@ -164,21 +177,17 @@ typedef struct {
  * zeros select the defaults). */
 typedef struct {
     int32_t warps_per_block;   /* tile kernel (queue 1, 2): 1..16 warps per block; ignored otherwise */
-    int32_t blocks_per_sm;     /* resident blocks per SM of the persistent grid (0: the kernel's default,
-                                  3 for the event kernel, as many as fit for the others) */
+    int32_t blocks_per_sm;     /* resident blocks per SM of the persistent grid (0: as many as fit) */
     int32_t grain;             /* tile kernel: input tracks per warp per step, 1 or 2 (default when
                                   n_triplets <= 16: the extension runs two tracks per warp, 16 lanes each) */
     int32_t queue;             /* 0: pipeline of persistent stage kernels (windows, triplets, extension
-                                  with selection), each draining its own device work queue, window
-                                  hits staged per track (default);
+                                  with selection), each draining its own device work queue (default);
                                   1: one tile kernel, blocks take tiles of tracks and their warps step
                                   through the stages together; 2: the tile kernel, warps take their
-                                  own tracks; 3: the event kernel: one persistent kernel whose blocks
-                                  take events from a device work queue and follow each event's
-                                  tracks zone by zone with the zone's hits staged once in shared
-                                  memory */
-    int32_t stage_hits;        /* event kernel: largest zone (hits) staged in shared memory; a larger
-                                  zone is read from global memory (0: what blocks_per_sm leaves) */
+                                  own tracks */
+    int32_t windows_bps;       /* stage pipeline: resident blocks per SM of the windows, triplet and */
+    int32_t triplets_bps;      /* extension kernels (0: blocks_per_sm, or as many as fit; a value   */
+    int32_t extend_bps;        /* above what fits is lowered to it)                                  */
 } lf_tuning;
 
 /* Create a context: validates and copies geometry and parameters.

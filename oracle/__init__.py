@@ -73,7 +73,11 @@ def default_params(paper_K: bool = False) -> dict:
         # p >= 5 GeV or pT >= 1 GeV, whichever is tighter; 5 mm overlap of
         # the two one-sided windows; c0..c7 of Table poly_tol
         no_ut=0, p_min=5.0, pt_min=1.0, x_overlap=5.0,
-        tol_c=list(TOL_C))
+        tol_c=list(TOL_C),
+        # Sec. "Calculation of momentum and track states": 0 = linear kick;
+        # 1 = Eq. pt_kick with the polynomial field integral (coefficients
+        # from a fit on toy tracks, qop_c[i][j])
+        qop_poly=0, qop_c=[[0.0] * 10 for _ in range(5)])
 
 
 #: "Forward no-UT" column of Table tolerances with the no-UT window and
@@ -107,7 +111,8 @@ class _Par(C.Structure):
                 ("T_x", C.c_float), ("T_uv_scale", C.c_float), ("T_uv_min", C.c_float),
                 ("T_ty", C.c_float), ("T_y", C.c_float), ("T_Q", C.c_float),
                 ("C_n", C.c_float * 4), ("no_ut", C.c_int32), ("p_min", C.c_float),
-                ("pt_min", C.c_float), ("x_overlap", C.c_float), ("tol_c", C.c_float * 8)]
+                ("pt_min", C.c_float), ("x_overlap", C.c_float), ("tol_c", C.c_float * 8),
+                ("qop_poly", C.c_int32), ("qop_c", (C.c_float * 10) * 5)]
 
 
 _P = C.c_void_p
@@ -166,6 +171,12 @@ def _par(p: dict) -> _Par:
     for name, _ in _Par._fields_:
         if name in ("C_n", "tol_c"):
             getattr(s, name)[:] = [float(v) for v in p[name]]
+        elif name == "qop_c":
+            c = p.get("qop_c", [[0.0] * 10 for _ in range(5)])
+            for i in range(5):
+                s.qop_c[i][:] = [float(v) for v in c[i]]
+        elif name == "qop_poly":
+            s.qop_poly = int(p.get("qop_poly", 0))
         else:
             setattr(s, name, p[name])
     return s

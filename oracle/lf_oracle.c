@@ -347,6 +347,43 @@ static int track_triplets(const lfo_geometry* g, const lfo_params* p, const floa
     return keep;
 }
 
+/* ---------------------------------------------------- momentum (Eq. pt_kick) */
+
+/* q/p of Sec. "Calculation of momentum and track states" with the field
+ * integral as a polynomial in dSlope whose coefficients are 2-D polynomials in
+ * the VELO slopes: c_i = sum_j qop_c[i][j] t_x^k_j t_y^m_j (terms summed in
+ * coefficient order), F = c_0 + dSlope (c_1 + dSlope (c_2 + dSlope (c_3 +
+ * dSlope c_4))), q/p = (sin-like slope after - before) / (polarity F). */
+static float qop_polynomial(const lfo_geometry* g, const lfo_params* p, float tx_i, float ty_i, float tx_f,
+                            float ty_f)
+{
+    static const int KM_EVEN[10][2] = LFO_QOP_KM_EVEN;
+    static const int KM_ODD[6][2] = LFO_QOP_KM_ODD;
+    float txp[7], typ[7];
+    txp[0] = 1.0f;
+    typ[0] = 1.0f;
+    for (int e = 1; e < 7; ++e) {
+        txp[e] = txp[e - 1] * tx_i;
+        typ[e] = typ[e - 1] * ty_i;
+    }
+    float c[5];
+    for (int i = 0; i < 5; ++i) {
+        float acc = 0.0f;
+        int nt = (i % 2 == 0) ? 10 : 6;
+        for (int j = 0; j < nt; ++j) {
+            int k = (i % 2 == 0) ? KM_EVEN[j][0] : KM_ODD[j][0];
+            int m = (i % 2 == 0) ? KM_EVEN[j][1] : KM_ODD[j][1];
+            acc = acc + p->qop_c[i][j] * (txp[k] * typ[m]);
+        }
+        c[i] = acc;
+    }
+    float ds = tx_f - tx_i;
+    float F = c[0] + ds * (c[1] + ds * (c[2] + ds * (c[3] + ds * c[4])));
+    float sf = tx_f / sqrtf((1.0f + tx_f * tx_f) + ty_f * ty_f);
+    float si = tx_i / sqrtf((1.0f + tx_i * tx_i) + ty_i * ty_i);
+    return (sf - si) / ((float)g->polarity * F);
+}
+
 /* ------------------------------------------------------- extension + fit */
 
 typedef struct {
@@ -503,7 +540,10 @@ static void extend_fit(const lfo_geometry* g, const lfo_params* p, const float* 
     cd->state[2] = tx;
     cd->state[3] = ty_fit;
     cd->state[4] = C * 1e-6f;
-    cd->state[5] = (tx - s->txs) / ((float)g->polarity * g->kappa);
+    if (p->qop_poly)
+        cd->state[5] = qop_polynomial(g, p, s->txs, s->tys, tx, ty_fit);
+    else
+        cd->state[5] = (tx - s->txs) / ((float)g->polarity * g->kappa);
 }
 
 /* ------------------------------------------------------- binary64 refit */
@@ -511,7 +551,7 @@ static void extend_fit(const lfo_geometry* g, const lfo_params* p, const float* 
 /* Direct weighted least squares of Eq. trackfitmodel (unscaled dz) on the x
  * hits and of the straight y line on the stereo hits, in binary64.  Inputs
  * are indexed by layer; has[l] == 0 marks a layer without a hit. */
-static void fit64(const lfo_geometry* g, const int* has, const double* hx, const float* hz,
+static void fit64(const lfo_geometry* g, const lfo_params* p, const int* has, const double* hx, const float* hz,
                   const float* hdxdy, const float* hw, const state_t* s, double* st)
 {
     double zr = g->z_ref, dR = g->dratio;
@@ -550,7 +590,27 @@ static void fit64(const lfo_geometry* g, const int* has, const double* hx, const
     double y0 = (s2 * r0 - s1 * r1) / det;
     double ty = (s0 * r1 - s1 * r0) / det;
     st[0] = a; st[1] = y0; st[2] = t; st[3] = ty; st[4] = c;
-    st[5] = (t - (double)s->txs) / ((double)g->polarity * (double)g->kappa);
+    if (p->qop_poly) {
+        /* Eq. pt_kick with the polynomial field integral, in binary64 */
+        static const int KM_EVEN[10][2] = LFO_QOP_KM_EVEN;
+        static const int KM_ODD[6][2] = LFO_QOP_KM_ODD;
+        double txi = s->txs, tyi = s->tys, c[5];
+        for (int i = 0; i < 5; ++i) {
+            c[i] = 0.0;
+            int nt = (i % 2 == 0) ? 10 : 6;
+            for (int j = 0; j < nt; ++j) {
+                int k = (i % 2 == 0) ? KM_EVEN[j][0] : KM_ODD[j][0];
+                int m = (i % 2 == 0) ? KM_EVEN[j][1] : KM_ODD[j][1];
+                c[i] += (double)p->qop_c[i][j] * pow(txi, k) * pow(tyi, m);
+            }
+        }
+        double ds = t - txi;
+        double F = c[0] + ds * (c[1] + ds * (c[2] + ds * (c[3] + ds * c[4])));
+        double sf = t / sqrt(1.0 + t * t + ty * ty), si = txi / sqrt(1.0 + txi * txi + tyi * tyi);
+        st[5] = (sf - si) / ((double)g->polarity * F);
+    } else {
+        st[5] = (t - (double)s->txs) / ((double)g->polarity * (double)g->kappa);
+    }
 }
 
 /* ------------------------------------------------------------ per event */
@@ -631,7 +691,7 @@ static int find_event_range(const lfo_geometry* g, const lfo_params* p, int32_t 
                         hd[l] = h >= 0 ? dxdy[h] : 0.0f;
                         hw[l] = h >= 0 ? w[h] : 0.0f;
                     }
-                    fit64(g, has, hx, hz, hd, hw, &s, st);
+                    fit64(g, p, has, hx, hz, hd, hw, &s, st);
                 } else {
                     for (int k = 0; k < 6; ++k) st[k] = 0.0;
                 }

@@ -52,7 +52,21 @@ typedef struct {
     float p_min, pt_min;        /* assumed momentum: the tighter of p_min and pt_min / sin(theta) */
     float x_overlap;            /* overlap of the two one-sided windows (mm) */
     float tol_c[8];             /* c0..c7 of Eq. tol_noUT (Table poly_tol) */
+    /* Sec. "Calculation of momentum and track states": qop_poly = 0 takes q/p
+     * from the slope change in the linear kick form, (t_x,FT - t_x,VELO) /
+     * (polarity kappa); qop_poly = 1 from Eq. pt_kick with the field integral
+     * F = sum_i c_i dSlope^i (i = 0..4, dSlope = t_x,FT - t_x,VELO) whose
+     * c_i = sum c_i^km t_x^k t_y^m (k + m <= 6; m even; k even for even i,
+     * odd for odd i): q/p = (t_x,f / sqrt(1 + t_x,f^2 + t_y,f^2) - t_x,i /
+     * sqrt(1 + t_x,i^2 + t_y,i^2)) / (polarity F).  qop_c[i][j] is c_i^km of
+     * the j-th (k, m) of LFO_QOP_KM_EVEN (even i) or LFO_QOP_KM_ODD (odd i). */
+    int32_t qop_poly;
+    float qop_c[5][10];
 } lfo_params;
+
+/* (k, m) exponents of t_x^k t_y^m in each c_i, in coefficient order */
+#define LFO_QOP_KM_EVEN {{0, 0}, {0, 2}, {0, 4}, {0, 6}, {2, 0}, {2, 2}, {2, 4}, {4, 0}, {4, 2}, {6, 0}}
+#define LFO_QOP_KM_ODD  {{1, 0}, {1, 2}, {1, 4}, {3, 0}, {3, 2}, {5, 0}}
 
 /* Outputs of lfo_find_tracks.  Per input track t (global index):
  *   found[t], nhits[t], hit_idx[t*12 + layer] (packed hit index or -1),

@@ -1,12 +1,15 @@
 """Autotuner of the persistent form's launch shape.
 
-For a batch it times a small set of lf_tuning candidates (queue mode, warps
-per block, tracks per warp, resident blocks per SM) with CUDA events on the
-current stream, keeps the fastest, and caches the choice per (GPU name,
-batch bucket).  The bucket is the event-size class of the batch (mean input
-tracks per event: 1-32, 33-64, 65-128, 129-256, 257+) and its event-count
-scale (log2), the shape classes of the uneven and served workloads.  Every
-candidate gives identical results; only the launch shape differs.
+For a batch it times a small set of lf_tuning candidates with CUDA events on
+the current stream, keeps the fastest, and caches the choice per (GPU name,
+batch bucket).  The candidates are the stage pipeline's occupancy knobs (the
+resident blocks per SM of its windows, triplet and extension kernels: fewer
+blocks leave each more registers and cache, more blocks hide more latency)
+and the tile kernel.  The bucket is the event-size class of the batch (mean
+input tracks per event: 1-32, 33-64, 65-128, 129-256, 257+) and its
+event-count scale (log2), the shape classes of the uneven and served
+workloads.  Every candidate gives identical results; only the launch shape
+differs.
 """
 from __future__ import annotations
 
@@ -19,11 +22,13 @@ from typing import Dict, Optional, Tuple
 import torch
 
 CANDIDATES = [
-    dict(queue=0),                                        # persistent stage kernels
-    dict(queue=0, blocks_per_sm=2),
+    dict(queue=0),                                        # stage pipeline, every stage as many blocks as fit
+    dict(queue=0, windows_bps=4),
+    dict(queue=0, triplets_bps=4),
+    dict(queue=0, extend_bps=3),
+    dict(queue=0, triplets_bps=4, extend_bps=3),
+    dict(queue=0, windows_bps=4, triplets_bps=4, extend_bps=3),
     dict(queue=1, warps_per_block=8, grain=2),            # block-synchronous tile kernel
-    dict(queue=1, warps_per_block=16, grain=2),
-    dict(queue=1, warps_per_block=8, grain=1),
 ]
 TRACK_EDGES = (32, 64, 128, 256)
 

@@ -96,6 +96,11 @@ bool param_error(const lf_geometry* g, const lf_params* p, char* msg, size_t n) 
     if (!(p->magtol_max >= p->magtol_min)) return bad("magtol_max < magtol_min");
     if (g->kappa == 0.0f) return bad("kappa must be non-zero");
     if (p->no_ut != 0 && p->no_ut != 1) return bad("no_ut must be 0 or 1");
+    if (p->qop_poly != 0 && p->qop_poly != 1) return bad("qop_poly must be 0 or 1");
+    if (p->qop_poly)
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 10; ++j)
+                if (!finite(p->qop_c[i][j])) return bad("qop_c[%d][%d] not finite", i, j);
     if (p->no_ut) {
         if (!(p->p_min > 0.0f) || !(p->pt_min > 0.0f) || !finite(p->p_min) || !finite(p->pt_min))
             return bad("p_min and pt_min must be positive");
@@ -148,6 +153,9 @@ KParams make_kparams(const lf_geometry* g, const lf_params* p) {
     k.pt_min = p->pt_min;
     k.x_overlap = p->x_overlap;
     for (int i = 0; i < 8; ++i) k.tol_c[i] = p->tol_c[i];
+    k.qop_poly = p->qop_poly;
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 10; ++j) k.qop_c[i][j] = p->qop_c[i][j];
     volatile float pol = (float)g->polarity;  // binary32 products, as the method forms them
     k.pol_f = pol;
     k.pk = pol * g->kappa;
@@ -374,31 +382,26 @@ lf_status lf_find_tracks(lf_ctx* c, const lf_batch* b, const lf_output* o, void*
 namespace {
 
 struct Shape {
-    int wpb, bps, grain, queue, stage;
+    int wpb, bps, grain, queue;
+    int stage_bps[3];   // per-stage blocks per SM of the stage pipeline (0: bps, else as many as fit)
 };
 
 // queue modes of lf_tuning
-constexpr int Q_STAGES = 0, Q_TILE_SYNC = 1, Q_TILE = 2, Q_EVENT = 3;
+constexpr int Q_STAGES = 0, Q_TILE_SYNC = 1;
 
 lf_status resolve_shape(lf_ctx* c, const lf_tuning* tuning, Shape& sh) {
     sh.queue = tuning ? tuning->queue : Q_STAGES;
-    sh.stage = 0;
-    if (sh.queue < 0 || sh.queue > 3) return fail(c, LF_ERR_ARG, "queue mode %d outside 0..3", sh.queue);
+    if (sh.queue < 0 || sh.queue > 2) return fail(c, LF_ERR_ARG, "queue mode %d outside 0..2", sh.queue);
     sh.wpb = tuning && tuning->warps_per_block > 0 ? tuning->warps_per_block : 8;
     sh.grain = (tuning && tuning->grain > 0 ? (tuning->grain & 15) : 0) + (sh.queue == Q_TILE_SYNC ? 16 : 0);
     if (sh.wpb > 16) return fail(c, LF_ERR_ARG, "warps_per_block %d above 16", sh.wpb);
-    if (c->p.no_ut && (sh.queue == Q_TILE_SYNC || sh.queue == Q_TILE))
-        return fail(c, LF_ERR_ARG, "the no-UT variant runs on the event kernel or the stage pipeline only");
-    if (sh.queue == Q_EVENT) {
-        const int want = tuning && tuning->blocks_per_sm > 0 ? tuning->blocks_per_sm : 3;
-        if (tuning && tuning->stage_hits < 0) return fail(c, LF_ERR_ARG, "stage_hits %d negative", tuning->stage_hits);
-        sh.stage = tuning && tuning->stage_hits > 0 ? tuning->stage_hits : event_stage_cap_default(want);
-        int max_bps = 0;
-        LF_CUDA(c, event_max_blocks_per_sm(c->kp, sh.stage, &max_bps));
-        if (max_bps < 1) return fail(c, LF_ERR_ARG, "event kernel with %d staged hits does not fit on an SM", sh.stage);
-        sh.bps = want < max_bps ? want : max_bps;
-        return LF_OK;
-    }
+    if (c->p.no_ut && sh.queue != Q_STAGES)
+        return fail(c, LF_ERR_ARG, "the no-UT variant runs on the staged pipeline (queue 0) only");
+    sh.stage_bps[0] = tuning ? tuning->windows_bps : 0;
+    sh.stage_bps[1] = tuning ? tuning->triplets_bps : 0;
+    sh.stage_bps[2] = tuning ? tuning->extend_bps : 0;
+    for (int i = 0; i < 3; ++i)
+        if (sh.stage_bps[i] < 0) return fail(c, LF_ERR_ARG, "negative blocks per SM");
     if (sh.queue == Q_STAGES) {
         if (!c->stage_bps[0]) LF_CUDA(c, stage_blocks_per_sm(c->kp, c->stage_bps));
         sh.bps = tuning && tuning->blocks_per_sm > 0 ? tuning->blocks_per_sm : 0;
@@ -416,7 +419,7 @@ lf_status resolve_shape(lf_ctx* c, const lf_tuning* tuning, Shape& sh) {
 lf_status prepare_batched(lf_ctx* c, const lf_batch* b, const Shape& sh) {
     lf_status st;
     if ((st = ensure(c, c->ev_count, (size_t)b->n_events * 4)) != LF_OK) return st;
-    if (sh.queue == Q_EVENT || sh.queue == Q_STAGES) {
+    if (sh.queue == Q_STAGES) {
         const size_t nt = (size_t)b->n_tracks, NT = (size_t)(c->p.n_triplets > 0 ? c->p.n_triplets : 1);
         const size_t ns = c->p.no_ut ? 2 : 1;
         if ((st = ensure(c, c->trk_event, nt * 4)) != LF_OK) return st;
@@ -429,7 +432,8 @@ lf_status prepare_batched(lf_ctx* c, const lf_batch* b, const Shape& sh) {
 }
 
 int stage_grid(lf_ctx* c, const Shape& sh, int i) {
-    int bps = sh.bps > 0 && sh.bps < c->stage_bps[i] ? sh.bps : c->stage_bps[i];
+    const int want = sh.stage_bps[i] > 0 ? sh.stage_bps[i] : sh.bps;
+    int bps = want > 0 && want < c->stage_bps[i] ? want : c->stage_bps[i];
     return (bps > 0 ? bps : 1) * c->n_sm;
 }
 
@@ -440,10 +444,7 @@ lf_status launch_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const
     KOut ko = to_kout(o);
     LF_CUDA(c, cudaMemsetAsync(c->cursor, 0, 8 * sizeof(int), s));
     if (b->n_tracks > 0) {
-        if (sh.queue == Q_EVENT) {
-            LF_CUDA(c, launch_event(c->kp, kb, ko, (int*)c->wbeg.p, (uint8_t*)c->wcnt.p, (uint64_t*)c->keys.p,
-                                    (uint8_t*)c->ntrip.p, c->cursor, c->status, sh.stage, sh.bps * c->n_sm, s));
-        } else if (sh.queue == Q_STAGES) {
+        if (sh.queue == Q_STAGES) {
             auto* te = (int*)c->trk_event.p;
             auto* wb = (int*)c->wbeg.p;
             auto* wc = (uint8_t*)c->wcnt.p;
@@ -486,7 +487,9 @@ lf_status lf_find_tracks_batched(lf_ctx* c, const lf_batch* b, const lf_output* 
     GraphKey key;
     {
         const auto u = [](const void* q) { return (uintptr_t)q; };
-        key.v = {(uintptr_t)sh.wpb, (uintptr_t)sh.bps, (uintptr_t)(sh.grain + 64 * sh.queue + ((uintptr_t)sh.stage << 8)),
+        key.v = {(uintptr_t)sh.wpb, (uintptr_t)sh.bps,
+                 (uintptr_t)(sh.grain + 64 * sh.queue + ((uintptr_t)sh.stage_bps[0] << 8) +
+                             ((uintptr_t)sh.stage_bps[1] << 16) + ((uintptr_t)sh.stage_bps[2] << 24)),
                  (uintptr_t)b->n_events, (uintptr_t)b->n_tracks, (uintptr_t)b->n_hits, (uintptr_t)c->generation,
                  u(b->hit_offsets), u(b->x), u(b->z), u(b->dxdy), u(b->w), u(b->trk_offsets),
                  u(b->sx), u(b->sy), u(b->stx), u(b->sty), u(b->sqop),

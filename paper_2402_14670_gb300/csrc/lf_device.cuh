@@ -173,6 +173,44 @@ __device__ __forceinline__ float f2_of(float u, float D) { return (u * u) * (1.0
 __device__ __forceinline__ float model_x(float A, float T, float C, float u, float D) {
     return (A + T * u) + C * f2_of(u, D);
 }
+// ------------------------------------------------------------ momentum
+
+// q/p of Sec. "Calculation of momentum and track states" (Eq. pt_kick) with
+// the field integral as a fourth-order polynomial in dSlope whose
+// coefficients are 2-D polynomials in the input slopes (the layout of
+// lf_params.qop_c); every sum in entry order, the polynomial in dSlope by
+// Horner's rule.  Out of line: evaluated once per accepted candidate.
+static __device__ __noinline__ float qop_polynomial(const KParams& k, float tx_i, float ty_i, float tx_f, float ty_f) {
+    constexpr int KE[10] = {0, 0, 0, 0, 2, 2, 2, 4, 4, 6}, ME[10] = {0, 2, 4, 6, 0, 2, 4, 0, 2, 0};
+    constexpr int KO[6] = {1, 1, 1, 3, 3, 5}, MO[6] = {0, 2, 4, 0, 2, 0};
+    float txp[7], typ[7];
+    txp[0] = 1.0f;
+    typ[0] = 1.0f;
+#pragma unroll
+    for (int e = 1; e < 7; ++e) {
+        txp[e] = txp[e - 1] * tx_i;
+        typ[e] = typ[e - 1] * ty_i;
+    }
+    float c[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        float acc = 0.0f;
+        if (i % 2 == 0) {
+#pragma unroll
+            for (int j = 0; j < 10; ++j) acc = acc + k.qop_c[i][j] * (txp[KE[j]] * typ[ME[j]]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 6; ++j) acc = acc + k.qop_c[i][j] * (txp[KO[j]] * typ[MO[j]]);
+        }
+        c[i] = acc;
+    }
+    const float ds = tx_f - tx_i;
+    const float F = c[0] + ds * (c[1] + ds * (c[2] + ds * (c[3] + ds * c[4])));
+    const float sf = tx_f / sqrtf((1.0f + tx_f * tx_f) + ty_f * ty_f);
+    const float si = tx_i / sqrtf((1.0f + tx_i * tx_i) + ty_i * ty_i);
+    return (sf - si) / (k.pol_f * F);
+}
+
 // ---------------------------------------------------------------- selection
 
 // Lowest Q among the accepted candidates of a group of G consecutive lanes

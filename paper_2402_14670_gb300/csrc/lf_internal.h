@@ -35,6 +35,8 @@ struct KParams {
     float pg;     // pol_f * gamma
     float D;      // dratio * 1000 (model in u = dz/1000)
     float inv_T_x;  // 1/T_x when T_x is a power of two (then r^2 / T_x == r^2 * inv_T_x exactly), else 0
+    int qop_poly;   // q/p from Eq. pt_kick with the polynomial field integral
+    float qop_c[5][10];
 };
 
 // 1/t when t is a power of two whose reciprocal is a normal float (dividing by
@@ -136,14 +138,6 @@ cudaError_t stage_blocks_per_sm(const KParams& k, int* out4);
 cudaError_t launch_fused(const KParams& k, const KBatch& b, const KOut& o, int* cursor, int grain,
                          int warps_per_block, int n_blocks, cudaStream_t s);
 cudaError_t fused_max_blocks_per_sm(const KParams& k, int warps_per_block, int grain, int* out);
-// per-event persistent kernel (lf_event.cu): a block per event zone, the
-// zone's x staged in shared memory (stage_cap hits at most, else read from
-// global memory); windows, keys and counts pass through wbeg/wcnt/keys/ntrip
-cudaError_t launch_event(const KParams& k, const KBatch& b, const KOut& o, int* wbeg, uint8_t* wcnt, uint64_t* keys,
-                         uint8_t* ntrip, int* cursor, int* status, int stage_cap, int blocks, cudaStream_t s);
-cudaError_t event_max_blocks_per_sm(const KParams& k, int stage_cap, int* out);
-// staging capacity (hits) that lets blocks_per_sm blocks share an SM
-int event_stage_cap_default(int blocks_per_sm);
 cudaError_t launch_hits_to_raw(const uint8_t* found, int* hit_idx, const int* perm, int n_tracks, int base,
                               cudaStream_t s);
 cudaError_t launch_compact(const int* trk_offsets, const uint8_t* found, int n_events, int* ev_count,

@@ -81,6 +81,8 @@ struct EvShared {
     int event, next;
     unsigned flagged;        // buckets above LF_MAX_BUCKET
     int b1;                  // end bin of the current chunk
+    int n_big;               // bins above SMALL_BIN hits in the current pass
+    int big[64];             // their indices (BIG_BINS)
 };
 
 // x as an unsigned integer with the same order (-0 already turned into +0)
@@ -129,6 +131,12 @@ __device__ __forceinline__ int bucket_code(int p, bool& bad) {
     return p;
 }
 
+// bins above this population are sorted by the whole block (bitonic), the
+// others by one thread each (insertion sort), so that a skewed x distribution
+// (many hits at one x) costs O(n log^2 n), not O(n^2)
+constexpr int SMALL_BIN = 32;
+constexpr int BIG_BINS = 64;   // big bins of one sorting pass recorded (more: another pass)
+
 // insertion sort of the bin [s, e) by (x, raw index) (the hits of one bin
 // share their bucket)
 template <typename K>
@@ -148,20 +156,6 @@ __device__ __forceinline__ void sort_bin(float* xs, K* ks, int s, int e) {
         xs[j + 1] = xv;
         ks[j + 1] = kv;
     }
-}
-
-// bucket of event position j: the last q with boff[q] <= j (an empty bucket
-// shares its offset with the next one)
-__device__ __forceinline__ int bucket_at(const int* boff, int j) {
-    int lo = 0, hi = NB - 1;
-#pragma unroll
-    for (int it = 0; it < 5; ++it) {   // 2^5 >= 24 buckets
-        const int mid = (lo + hi + 1) >> 1;
-        if (lo < hi) {
-            if (boff[mid] <= j) lo = mid; else hi = mid - 1;
-        }
-    }
-    return lo;
 }
 
 // Bin counters of one event: 16-bit halves of 32-bit words (WIDE = false) or
@@ -191,6 +185,84 @@ struct Bins {
         }
     }
 };
+
+// Block-wide sort of [s, e) by (x, raw index): the bitonic network on the
+// next power of two, positions at or beyond e standing for +infinity, in
+// its form that compares every pair towards the lower index (so padded
+// positions never move).  All PACK_THREADS threads call it.
+template <typename K>
+__device__ __forceinline__ void sort_range_block(float* xs, K* ks, int s, int e, int tid) {
+    const int n = e - s;
+    int p2 = 1;
+    while (p2 < n) p2 <<= 1;
+    for (int kk = 2; kk <= p2; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < p2; i += PACK_THREADS) {
+                // the partner: mirrored inside the kk-block on its first step
+                const int pi = (j == (kk >> 1)) ? (i ^ (kk - 1)) : (i ^ j);
+                if (pi > i && pi < n) {
+                    const float xa = xs[s + i], xb = xs[s + pi];
+                    const K ka = ks[s + i], kb = ks[s + pi];
+                    if (xb < xa || (xb == xa && kb < ka)) {
+                        xs[s + i] = xb;
+                        ks[s + i] = kb;
+                        xs[s + pi] = xa;
+                        ks[s + pi] = ka;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Order every bin of [b0, b1) (starts at pos(b - 1), ends at pos(b), both
+// relative to `base`): small bins by their thread, big ones by the block.
+template <bool WIDE, typename K>
+__device__ __forceinline__ void sort_bins(const Bins<WIDE>& bins, float* xs, K* ks, int b0, int b1, int base,
+                                          EvShared& sh, int tid) {
+    // (sh.n_big was cleared before the barrier that precedes this call)
+    for (int b = b0 + tid; b < b1; b += PACK_THREADS) {
+        const int s0 = (b == b0 ? base : bins.get(b - 1)) - base, s1 = bins.get(b) - base;
+        if (s1 - s0 <= SMALL_BIN) {
+            sort_bin(xs, ks, s0, s1);
+        } else {
+            const int q = atomicAdd(&sh.n_big, 1);
+            if (q < BIG_BINS) sh.big[q] = b;
+        }
+    }
+    __syncthreads();
+    const int nbig = sh.n_big;
+    if (nbig == 0) return;
+    if (nbig <= BIG_BINS) {
+        for (int q = 0; q < nbig; ++q) {
+            const int b = sh.big[q];
+            const int s0 = (b == b0 ? base : bins.get(b - 1)) - base, s1 = bins.get(b) - base;
+            sort_range_block(xs, ks, s0, s1, tid);
+        }
+    } else {
+        // more big bins than the record holds: visit every bin in order
+        for (int b = b0; b < b1; ++b) {
+            const int s0 = (b == b0 ? base : bins.get(b - 1)) - base, s1 = bins.get(b) - base;
+            if (s1 - s0 > SMALL_BIN) sort_range_block(xs, ks, s0, s1, tid);
+        }
+    }
+    __syncthreads();
+}
+
+// bucket of event position j: the last q with boff[q] <= j (an empty bucket
+// shares its offset with the next one)
+__device__ __forceinline__ int bucket_at(const int* boff, int j) {
+    int lo = 0, hi = NB - 1;
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {   // 2^5 >= 24 buckets
+        const int mid = (lo + hi + 1) >> 1;
+        if (lo < hi) {
+            if (boff[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+    }
+    return lo;
+}
 
 struct PackIO {
     const float* __restrict__ x;
@@ -344,13 +416,14 @@ __device__ __forceinline__ void sort_event(const PackIO& io, EvShared& sh, char*
         }
         __syncthreads();
         // bins[b] now holds the end of bin b; order each bin by (x, raw index)
-        for (int b = tid; b < nbin; b += PACK_THREADS) sort_bin(xs, ks, b == 0 ? 0 : bins.get(b - 1), bins.get(b));
-        __syncthreads();
+        sort_bins(bins, xs, ks, 0, nbin, 0, sh, tid);
         // x, layer and perm straight from shared memory
         const size_t o0 = (size_t)rb;
+        int qb = 0;   // bucket of position j (j only grows: the last q with boff[q] <= j)
         for (int j = tid; j < n; j += PACK_THREADS) {
+            while (qb + 1 < NB && sh.boff[qb + 1] <= j) ++qb;
             io.ox[o0 + j] = xs[j];
-            io.ol[o0 + j] = (uint8_t)(bucket_at(sh.boff, j) % NL);
+            io.ol[o0 + j] = (uint8_t)(qb % NL);
             io.perm[o0 + j] = rb + (int)ks[j];
         }
         __syncthreads();
@@ -411,6 +484,7 @@ __device__ __forceinline__ void sort_event(const PackIO& io, EvShared& sh, char*
                 if (bins.get(m) - base <= chunk) l = m; else h = m - 1;
             }
             sh.b1 = l;
+            sh.n_big = 0;
         }
         __syncthreads();
         const int b1 = sh.b1;
@@ -446,13 +520,13 @@ __device__ __forceinline__ void sort_event(const PackIO& io, EvShared& sh, char*
         }
         __syncthreads();
         // bins[b] now holds the end of bin b for b in [b0, b1)
-        for (int b = b0 + tid; b < b1; b += PACK_THREADS)
-            sort_bin(xs, ks, (b == b0 ? base : bins.get(b - 1)) - base, bins.get(b) - base);
-        __syncthreads();
+        sort_bins(bins, xs, ks, b0, b1, base, sh, tid);
         const size_t o0 = (size_t)rb + base;
+        int qb = 0;   // bucket of position base + j (grows with j)
         for (int j = tid; j < tot; j += PACK_THREADS) {
+            while (qb + 1 < NB && sh.boff[qb + 1] <= base + j) ++qb;
             io.ox[o0 + j] = xs[j];
-            io.ol[o0 + j] = (uint8_t)(bucket_at(sh.boff, base + j) % NL);
+            io.ol[o0 + j] = (uint8_t)(qb % NL);
             io.perm[o0 + j] = rb + (int)ks[j];
         }
         for (int ib = 0; ib < n; ib += PACK_THREADS * UNROLL) {
@@ -481,11 +555,30 @@ __device__ __forceinline__ void sort_event(const PackIO& io, EvShared& sh, char*
                 if (b < b0 || b >= b1) continue;
                 const int en = bins.get(b) - base;
                 int j = (b == b0 ? base : bins.get(b - 1)) - base;
+                if (en - j > SMALL_BIN) continue;   // a big bin: gathered below
                 while (j < en && (int)ks[j] != i) ++j;
                 if (j < en) {
                     io.oz[o0 + j] = zu[u];
                     io.od[o0 + j] = du[u];
                     io.ow[o0 + j] = wu[u];
+                }
+            }
+        }
+        // hits of big bins (many hits at one x): their payload is gathered
+        // through the raw index kept beside each x, so a big bin costs no
+        // search per hit
+        if (sh.n_big > 0) {
+            const bool listed = sh.n_big <= BIG_BINS;
+            const int nb_ = listed ? sh.n_big : b1 - b0;
+            for (int q = 0; q < nb_; ++q) {
+                const int b = listed ? sh.big[q] : b0 + q;
+                const int s0 = (b == b0 ? base : bins.get(b - 1)) - base, s1 = bins.get(b) - base;
+                if (s1 - s0 <= SMALL_BIN) continue;
+                for (int j = s0 + tid; j < s1; j += PACK_THREADS) {
+                    const int i = (int)ks[j];
+                    io.oz[o0 + j] = __ldg(io.z + rb + i);
+                    io.od[o0 + j] = __ldg(io.dxdy + rb + i);
+                    io.ow[o0 + j] = __ldg(io.w + rb + i);
                 }
             }
         }
@@ -510,6 +603,7 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
             sh.event = sh.next;
             sh.next = sh.event < n_events ? atomicAdd(cursor, 1) : n_events;
             sh.flagged = 0u;
+            sh.n_big = 0;
         }
         __syncthreads();
         const int e = sh.event;

@@ -223,32 +223,22 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) 
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Copy x and z of the window hits into the slot: the (layer, hit) pairs of
-// the windows (all twelve, or the six x layers when XONLY) are flattened over
-// the lanes and every pair is one asynchronous copy per array, so all of a
-// track's copies are in flight at once (stage_issue); stage_finish waits for
-// them and flags a window whose hits do not all share one z.
+// Copy x and z of the window hits into the slot, one asynchronous copy per
+// hit and array: layer by layer, lane j copying hit j (and j + 32), so the
+// copies of all of a track's windows are in flight at once (stage_issue);
+// stage_finish waits for them and flags a window whose hits do not all
+// share one z.
 template <bool XONLY = false, bool ZTOO = true>
 __device__ __forceinline__ void stage_issue(const KParams& k, const KBatch& b, const Slot& m, int lane) {
     const int cap = k.cap;
-    int off[NL + 1];
-    off[0] = 0;
-#pragma unroll
-    for (int l = 0; l < NL; ++l) off[l + 1] = off[l] + ((XONLY && !is_x(l)) ? 0 : m.h->wcnt[l]);
-    const int total = off[NL];
-#pragma unroll 2
-    for (int q = lane; q < total; q += 32) {
-        int l = 0, lo = 0;   // the window of pair q (offsets are non-decreasing)
-#pragma unroll
-        for (int i = 1; i < NL; ++i)
-            if (q >= off[i]) {
-                l = i;
-                lo = off[i];
-            }
-        const int j = q - lo;
-        const int src = m.h->wbeg[l] + j;
-        cp_async4(m.wx + l * cap + j, b.x + src);
-        if (ZTOO) cp_async4(m.wz + l * cap + j, b.z + src);
+#pragma unroll 1
+    for (int l = 0; l < NL; ++l) {
+        if (XONLY && !is_x(l)) continue;
+        const int n = m.h->wcnt[l], src = m.h->wbeg[l];
+        for (int j = lane; j < n; j += 32) {
+            cp_async4(m.wx + l * cap + j, b.x + src + j);
+            if (ZTOO) cp_async4(m.wz + l * cap + j, b.z + src + j);
+        }
     }
 }
 
@@ -659,7 +649,7 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
     cd.st[2] = tx;
     cd.st[3] = ty_fit;
     cd.st[4] = C * 1e-6f;
-    cd.st[5] = (tx - s.txs) / k.pk;
+    cd.st[5] = k.qop_poly ? qop_polynomial(k, s.txs, s.tys, tx, ty_fit) : (tx - s.txs) / k.pk;
 }
 
 

@@ -50,7 +50,8 @@ class lf_params(C.Structure):
                 ("magtol_tx", C.c_float), ("T_triplet", C.c_float), ("T_x", C.c_float),
                 ("T_uv_scale", C.c_float), ("T_uv_min", C.c_float), ("T_ty", C.c_float), ("T_y", C.c_float),
                 ("T_Q", C.c_float), ("C_n", C.c_float * 4), ("no_ut", C.c_int32), ("p_min", C.c_float),
-                ("pt_min", C.c_float), ("x_overlap", C.c_float), ("tol_c", C.c_float * 8)]
+                ("pt_min", C.c_float), ("x_overlap", C.c_float), ("tol_c", C.c_float * 8),
+                ("qop_poly", C.c_int32), ("qop_c", (C.c_float * 10) * 5)]
 
 
 class lf_raw_hits(C.Structure):
@@ -85,7 +86,8 @@ class lf_host_output(C.Structure):
 
 class lf_tuning(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("grain", C.c_int32),
-                ("queue", C.c_int32), ("stage_hits", C.c_int32)]
+                ("queue", C.c_int32), ("windows_bps", C.c_int32), ("triplets_bps", C.c_int32),
+                ("extend_bps", C.c_int32)]
 
 
 def tuning_struct(tuning: Optional[dict]) -> Optional[lf_tuning]:
@@ -164,7 +166,17 @@ def default_params(paper_K: bool = False) -> dict:
                 p_bend=5.0, magtol_min=8.0, magtol_max=40.0, magtol_c=96.0, magtol_tx=10.0, T_triplet=8.0,
                 T_x=2.0, T_uv_scale=50.0, T_uv_min=2.0, T_ty=0.02, T_y=800.0, T_Q=0.5,
                 C_n=[5.0, 1.0, 0.8, 0.5], no_ut=0, p_min=5.0, pt_min=1.0, x_overlap=5.0,
-                tol_c=[4824.3, 426.3, 7071.1, 12080.4, 14077.8, 13909.3, 9315.3, 3209.5])
+                tol_c=[4824.3, 426.3, 7071.1, 12080.4, 14077.8, 13909.3, 9315.3, 3209.5],
+                qop_poly=0, qop_c=[[0.0] * 10 for _ in range(5)])
+
+
+def qop_poly_params(coefficients, base: Optional[dict] = None) -> dict:
+    """Parameters with q/p from Eq. pt_kick and the polynomial field integral
+    (Sec. "Calculation of momentum and track states"); coefficients[5][10]
+    as fitted by qop_fit.fit_qop_poly."""
+    p = dict(base or default_params())
+    p.update(qop_poly=1, qop_c=[[float(v) for v in row] for row in np.asarray(coefficients, np.float32)])
+    return p
 
 
 def no_ut_params() -> dict:
@@ -195,6 +207,12 @@ def _params(p: dict) -> lf_params:
     for name, _ in lf_params._fields_:
         if name in ("C_n", "tol_c"):
             getattr(s, name)[:] = [float(v) for v in p[name]]
+        elif name == "qop_c":
+            c = p.get("qop_c", [[0.0] * 10 for _ in range(5)])
+            for i in range(5):
+                s.qop_c[i][:] = [float(v) for v in c[i]]
+        elif name == "qop_poly":
+            s.qop_poly = int(p.get("qop_poly", 0))
         else:
             setattr(s, name, p[name])
     return s

@@ -150,6 +150,50 @@ def pin_closed_form_md(orc):
     pin_closed_form(orc, polarity=-1)
 
 
+def _qop_poly_params(polarity=1):
+    from paper_2402_14670_gb300 import qop_fit
+    c = qop_fit.fit_qop_poly(kappa=1.2)
+    p = oracle.default_params()
+    p.update(qop_poly=1, qop_c=c.tolist())
+    return p
+
+
+def pin_qop_polynomial(orc, polarity=1):
+    """Sec. "Calculation of momentum and track states": with q/p from Eq.
+    pt_kick and the field integral fitted on toy tracks (fourth order in
+    dSlope, 2-D polynomials in the VELO slopes), noise-free particles of the
+    exact trajectory model are found with exactly their hits and their q/p
+    is the generating one to the fit's accuracy (0.3 % over 3-50 GeV on the
+    fit grid; 0.5 % allowed); the binary64 refit agrees the same way."""
+    geo, b = closed_form_batch(polarity)
+    p = _qop_poly_params(polarity)
+    res = orc.run_batch(b, geometry=geo_dict(geo), params=p, use_x64=True)
+    lin = orc.run_batch(b, geometry=geo_dict(geo), use_x64=True)
+    trk_mcp = b.trk_mcp.numpy()
+    qop_true = b.mcp["qop"].numpy()
+    f = res["found"].astype(bool)
+    assert np.array_equal(f, lin["found"].astype(bool))
+    assert np.array_equal(res["hit_idx"][f], lin["hit_idx"][f])
+    assert np.array_equal(res["state"][f][:, :5], lin["state"][f][:, :5])   # only q/p changes
+    # tracks made of their own particle's hits (an input state whose particle
+    # left the acceptance may pick up a neighbour's)
+    hit_mcp = b.hit_mcp.numpy()[res["packed"]["perm"]]
+    own = np.array([f[t] and np.all(hit_mcp[res["hit_idx"][t][res["hit_idx"][t] >= 0]] == trk_mcp[t])
+                    for t in range(b.n_tracks)])
+    q = res["state"][own][:, 5].astype(np.float64)
+    qt = qop_true[trk_mcp[own]]
+    assert own.sum() >= 20
+    assert np.all(np.abs(q / qt - 1.0) < 5e-3), np.max(np.abs(q / qt - 1.0))
+    q64 = res["state64"][own][:, 5]
+    assert np.all(np.abs(q64 / qt - 1.0) < 5e-3)
+    # the polynomial form differs from the linear one (it is evaluated)
+    assert np.any(res["state"][f][:, 5] != lin["state"][f][:, 5])
+
+
+def pin_qop_polynomial_md(orc):
+    pin_qop_polynomial(orc, polarity=-1)
+
+
 # ------------------------------------------------------------------- windows
 
 def _golden_windows():
@@ -703,7 +747,8 @@ def pin_no_ut_qop_unused(orc):
     assert r0["found"].sum() > 10
 
 
-ALL_PINS = [pin_pack_lexsort, pin_closed_form, pin_closed_form_md, pin_window_edges,
+ALL_PINS = [pin_pack_lexsort, pin_closed_form, pin_closed_form_md, pin_qop_polynomial, pin_qop_polynomial_md,
+            pin_window_edges,
             pin_window_edges_inclusive, pin_extension_T_x, pin_extension_T_uv, pin_window_cap,
             pin_closest_tie, pin_triplet_chi2_K, pin_top_n, pin_bending_filter,
             pin_magnet_tolerance, pin_known_residual_Q, pin_T_Q, pin_ty_cut, pin_invariants,

@@ -26,6 +26,11 @@ def test_choice_table_round_trip(tmp_path):
     assert t.lookup(100_000, 8_000_000) == choice
     # another bucket is not in the table
     assert t.lookup(100, 100) is None
-    # every candidate is a valid tuning (queue 0..2; the stage pipeline first)
+    # every candidate is a valid tuning (queue 0..2; the stage pipeline first,
+    # with its per-stage occupancy knobs)
     assert autotune.CANDIDATES[0] == dict(queue=0)
     assert all(c.get("queue", 0) in (0, 1, 2) for c in autotune.CANDIDATES)
+    from paper_2402_14670_gb300 import lf
+    names = {f for f, _ in lf.lf_tuning._fields_}
+    assert all(set(c) <= names for c in autotune.CANDIDATES)
+    assert sum(1 for c in autotune.CANDIDATES if c.get("queue", 0) == 0 and len(c) > 1) >= 4

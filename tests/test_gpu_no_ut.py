@@ -1,7 +1,7 @@
 """The no-UT variant (Sec. "No-UT tuning") on the GPU against the oracle.
 
-Every form that follows it (plain stages; the persistent event kernel and
-the persistent stage pipeline) must give the oracle's two window sets per track, its pooled triplet list
+Both forms that follow it (plain stages, and the persistent staged pipeline)
+must give the oracle's two window sets per track, its pooled triplet list
 (side bit included), hit lists, states and Q bit for bit.
 """
 import numpy as np
@@ -55,11 +55,10 @@ def test_no_ut_high_occupancy_subset(lfm):
     assert info["n_found"] > 300
 
 
-@pytest.mark.parametrize("tuning", [None, dict(queue=3), dict(queue=3, stage_hits=1)])
-def test_no_ut_uneven_subset(lfm, tuning):
+def test_no_ut_uneven_subset(lfm):
     p = _p(lfm)
     b = synth.generate(2, n_events=120).to("cuda")
-    run_both(lfm.Tracker(None, p), b, mode="batched", params=p, tuning=tuning)
+    run_both(lfm.Tracker(None, p), b, mode="batched", params=p)
 
 
 def test_no_ut_magdown(lfm):

@@ -67,6 +67,15 @@ MUTANTS = [
      "double f[3] = {1.0, dz, dz * dz};", ["pin_closed_form"]),
     ("q/p ignores the polarity", "cd->state[5] = (tx - s->txs) / ((float)g->polarity * g->kappa);",
      "cd->state[5] = (tx - s->txs) / g->kappa;", ["pin_closed_form_md"]),
+    ("polynomial q/p without the slope normalisation", "float sf = tx_f / sqrtf((1.0f + tx_f * tx_f) + ty_f * ty_f);",
+     "float sf = tx_f;", ["pin_qop_polynomial"]),
+    ("polynomial q/p with dSlope reversed", "float ds = tx_f - tx_i;", "float ds = tx_i - tx_f;",
+     ["pin_qop_polynomial"]),
+    ("polynomial q/p coefficients with t_x and t_y swapped",
+     "acc = acc + p->qop_c[i][j] * (txp[k] * typ[m]);", "acc = acc + p->qop_c[i][j] * (txp[m] * typ[k]);",
+     ["pin_qop_polynomial"]),
+    ("polynomial q/p ignores the polarity", "return (sf - si) / ((float)g->polarity * F);", "return (sf - si) / F;",
+     ["pin_qop_polynomial_md"]),
     ("x refit skipped", "A = A + ((c00 * b0 + c01 * b1) + c02 * b2) / dt;", "A = A + 0.0f * dt;",
      ["pin_fit32_vs_fit64"]),
     ("stereo-hit-per-station requirement dropped",

@@ -32,8 +32,13 @@ def _np(t):
     return t.detach().cpu().numpy()
 
 
-def test_static_entry_point_matches_batched(lfm):
-    tr = lfm.Tracker()
+@pytest.mark.parametrize("cap,nt", [(32, 12), (16, 12), (64, 12), (32, 20)])
+def test_static_entry_point_matches_batched(lfm, cap, nt):
+    """Window caps 16/32/64 select different kernel instantiations; more than
+    16 kept triplets put one track instead of two on a warp."""
+    p = lfm.default_params()
+    p.update(n_hits_window=cap, n_triplets=nt)
+    tr = lfm.Tracker(None, p)
     stream = torch.cuda.current_stream()
     for config, n_ev in ((1, 300), (2, 150)):   # two calls in a row, different batches
         b = synth.generate(config, n_events=n_ev).to("cuda")
@@ -59,6 +64,34 @@ def test_static_entry_point_matches_batched(lfm):
         n_out = int(_np(out["n_out"])[0])
         assert n_out == int(_np(ref["n_out"])[0])
         assert np.array_equal(_np(out["out_trk"])[:n_out], _np(ref["out_trk"])[:n_out])
+    tr.close()
+
+
+def test_static_entry_point_events_without_tracks(lfm):
+    """Events without input tracks: no track kernel runs, the compaction
+    still writes every event's offset and n_out = 0 over the shared array
+    the previous call left behind."""
+    tr = lfm.Tracker()
+    stream = torch.cuda.current_stream()
+    b = synth.generate(1, n_events=50).to("cuda")
+    packed = tr.pack(b)
+    out = tr.alloc_output(b.n_tracks, b.n_events, "cuda")
+    lfm.lf_find_tracks_static(tr.geometry, tr.params, tr.batch_struct(packed, b, b.n_events),
+                              tr.output_struct(out), lfm._P(stream.cuda_stream))
+    torch.cuda.synchronize()
+    assert int(_np(out["n_out"])[0]) > 0
+    # the same hits with every event's track range empty
+    b.trk_offsets = torch.zeros_like(b.trk_offsets)
+    for k in ("sx", "sy", "stx", "sty", "sqop"):
+        setattr(b, k, getattr(b, k)[:0])
+    out0 = tr.alloc_output(0, b.n_events, "cuda")
+    out0["out_offsets"].fill_(-5)
+    out0["n_out"].fill_(-1)
+    lfm.lf_find_tracks_static(tr.geometry, tr.params, tr.batch_struct(packed, b, b.n_events),
+                              tr.output_struct(out0), lfm._P(stream.cuda_stream))
+    torch.cuda.synchronize()
+    assert int(_np(out0["n_out"])[0]) == 0
+    assert np.array_equal(_np(out0["out_offsets"]), np.zeros(b.n_events + 1, np.int32))
     tr.close()
 
 
