@@ -165,6 +165,44 @@ def host_copy(batch, arena_bytes_extra: int = 0):
     return synth.EventBatch(batch.n_events, **kw), arena
 
 
+def on_node(node_cpus, fn):
+    """Run fn with this process bound to the given CPUs (page-locked memory
+    it allocates is placed on their NUMA node), then restore the binding."""
+    if not node_cpus:
+        return fn()
+    old = os.sched_getaffinity(0)
+    try:
+        os.sched_setaffinity(0, node_cpus)
+        return fn()
+    finally:
+        os.sched_setaffinity(0, old)
+
+
+def numa_link(n_bytes: int = 1 << 30) -> dict:
+    """The GPU's nearest host NUMA node and the host-to-device copy rate
+    from page-locked memory placed on each node this process may use."""
+    from paper_2402_14670_gb300 import lf
+    nodes = lf.numa_node_cpus()
+    out = {"gpu_host_numa_node": lf.lf_device_host_numa(), "nodes": {}}
+    dst = torch.empty(n_bytes // 4, dtype=torch.float32, device="cuda")
+    for node, cpus in nodes.items():
+        arena = on_node(cpus, lambda: lf.HostArena(n_bytes + 256))
+        src = arena.take(n_bytes // 4, torch.float32)
+        src.fill_(1.0)
+        best = 0.0
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            best = max(best, n_bytes / (time.perf_counter() - t0) / 1e9)
+        out["nodes"][str(node)] = {"cpus": len(cpus), "h2d_gbps": best}
+        del src
+        arena.close()
+    del dst
+    return out
+
+
 def sub_batches(batch, size: int):
     """Views of consecutive `size`-event sub-batches (offsets rebased)."""
     from paper_2402_14670_gb300 import synth
@@ -473,7 +511,11 @@ def main():
     # ---------------- end to end through lf_process_host on pinned host buffers
     e2e = None
     if not args.no_e2e:
-        host, arena = host_copy(batch)
+        numa = numa_link()
+        # the page-locked host batch on the GPU's nearest NUMA node when the
+        # host reports one this process may use
+        near = lf.numa_node_cpus().get(numa["gpu_host_numa_node"])
+        host, arena = on_node(near, lambda: host_copy(batch))
         hout = tr.alloc_host_output(host.n_tracks)
         for _ in range(args.warmup):
             tr.process_host(host, out=hout, tuning=tuning)
@@ -502,52 +544,62 @@ def main():
                "api": "lf_process_host (chunked; copies in, compute and copies out on three streams)"}
         n_hits, n_trk = host.n_hits, host.n_tracks
         cpu_src = host
-        e2e["host_memory"] = "cudaHostAlloc (lf_host_alloc)"
+        e2e["host_memory"] = "cudaHostAlloc (lf_host_alloc)%s" % (
+            " on NUMA node %d (nearest to the GPU)" % numa["gpu_host_numa_node"] if near else "")
+        e2e["numa_link"] = numa
     else:
         n_hits, n_trk = batch.n_hits, batch.n_tracks
         cpu_src = None
 
-    # ---------------- served stream: continuous batching over the pinned pool
+    # ---------------- served stream (the served workload: events of the
+    # uneven distribution arriving as a Poisson process at 10 %..120 % of the
+    # batched rate; continuous batching over S slots, 16 GB budget).  Stated
+    # before measuring: with events arriving in device memory the loop holds
+    # p99 <= 5 ms up to 80 % of the batched rate.
     served = None
     if not args.no_serve and e2e is not None:
         from paper_2402_14670_gb300 import serve
-        srv = serve.Server(host, n_slots=4, max_events=2048, budget_bytes=16 << 30)
-        n_sat = min(n_ev, 60000)
-        sat = srv.run(np.zeros(n_sat))
-        points = []
-        for frac in (0.25, 0.5, 0.8):
-            rate = frac * sat.events_per_s
-            n_pt = int(min(n_ev, max(2000, rate * 1.0)))
-            st = srv.run(serve.poisson_arrivals(n_pt, rate, seed=int(frac * 100)))
-            points.append({"offered_rate": rate, "offered_frac_of_served_peak": frac,
-                           "offered_frac_of_batched": rate / value, "events_per_s": st.events_per_s,
-                           "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_batch_events": st.mean_batch_events,
-                           "events": st.n_events})
-        served = {"saturation_events_per_s": sat.events_per_s, "saturation_p50_ms": sat.p50_ms,
-                  "saturation_p99_ms": sat.p99_ms, "slots": len(srv.slots), "budget_bytes": 16 << 30,
-                  "points": points,
-                  "note": "events arrive in pinned host memory; each batch is copied in, packed, followed "
-                          "and its per-track results copied back; latency = arrival to results on host"}
-        srv.close()
-        # the same loop with the events already in device memory (arrivals
-        # written straight to HBM): no copies in, results still leave the device
+        P99_BOUND_MS = 5.0
+
+        def sweep_rates(srv, fracs, seed0):
+            pts = []
+            for frac in fracs:
+                rate = frac * value
+                n_pt = int(min(n_ev, max(2000, rate * 0.5)))
+                st = srv.run(serve.poisson_arrivals(n_pt, rate, seed=seed0 + int(frac * 1000)))
+                pts.append({"offered_frac_of_batched": frac, "offered_rate": rate, "events_per_s": st.events_per_s,
+                            "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_batch_events": st.mean_batch_events,
+                            "events": st.n_events})
+            return pts
+
+        fracs = (0.1, 0.2, 0.4, 0.6, 0.8, 1.0, 1.2)
+        # events arriving in device memory (arrivals written straight to HBM)
         srv = serve.Server(batch, n_slots=4, max_events=2048, budget_bytes=16 << 30)
+        srv.tune_buckets((256, 1024, 2048))
+        n_sat = min(n_ev, 60000)
         sat_d = srv.run(np.zeros(n_sat))
-        pts_d = []
-        for frac in (0.5, 0.65, 0.8):   # offered load as a fraction of the batched rate
-            rate = frac * value
-            if rate >= sat_d.events_per_s:
-                continue
-            n_pt = int(min(n_ev, max(2000, rate * 1.0)))
-            st_d = srv.run(serve.poisson_arrivals(n_pt, rate, seed=int(frac * 1000)))
-            pts_d.append({"offered_frac_of_batched": frac, "offered_rate": rate, "events_per_s": st_d.events_per_s,
-                          "p50_ms": st_d.p50_ms, "p99_ms": st_d.p99_ms,
-                          "mean_batch_events": st_d.mean_batch_events, "events": st_d.n_events})
-        served["device_resident"] = {
-            "saturation_events_per_s": sat_d.events_per_s, "saturation_p50_ms": sat_d.p50_ms,
-            "saturation_p99_ms": sat_d.p99_ms, "saturation_frac_of_batched": sat_d.events_per_s / value,
-            "points": pts_d,
-            "note": "events arrive in device memory; batches are views of it; per-track results copied back"}
+        pts_d = sweep_rates(srv, fracs, 100)
+        at80 = [p for p in pts_d if p["offered_frac_of_batched"] == 0.8][0]
+        served = {"p99_bound_ms": P99_BOUND_MS, "bound_load_frac_of_batched": 0.8,
+                  "bound_met": bool(at80["p99_ms"] <= P99_BOUND_MS),
+                  "slots": len(srv.slots), "budget_bytes": 16 << 30,
+                  "device_resident": {
+                      "saturation_events_per_s": sat_d.events_per_s, "saturation_p50_ms": sat_d.p50_ms,
+                      "saturation_p99_ms": sat_d.p99_ms, "saturation_frac_of_batched": sat_d.events_per_s / value,
+                      "points": pts_d,
+                      "note": "events arrive in device memory; batches are views of it; per-track results "
+                              "copied back; latency = arrival to results on host"}}
+        srv.close()
+        # events arriving in page-locked host memory: copied in per batch
+        srv = serve.Server(host, n_slots=4, max_events=2048, budget_bytes=16 << 30)
+        srv.tune_buckets((256, 1024, 2048))
+        sat = srv.run(np.zeros(n_sat))
+        served["host_fed"] = {
+            "saturation_events_per_s": sat.events_per_s, "saturation_p50_ms": sat.p50_ms,
+            "saturation_p99_ms": sat.p99_ms, "saturation_frac_of_batched": sat.events_per_s / value,
+            "points": sweep_rates(srv, (0.1, 0.2, 0.4, 0.6), 200),
+            "note": "events arrive in pinned host memory; each batch is copied in, packed, followed and its "
+                    "per-track results copied back"}
         srv.close()
 
     # ---------------- roofline of the dominant kernel (persistent find)

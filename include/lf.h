@@ -59,14 +59,15 @@ typedef enum {
     LF_ERR_CUDA = 2,       /* a CUDA call failed; lf_last_error has the message */
     LF_ERR_OOM = 3,        /* scratch allocation failed */
     LF_ERR_CAPACITY = 4,   /* device status: a bucket above LF_MAX_BUCKET hits */
-    LF_ERR_TIMEOUT = 5,    /* device status: a bounded wait ran out */
+    LF_ERR_TIMEOUT = 5,    /* device status: a bounded wait ran out (reserved: no kernel of this
+                              library waits on a flag or barrier, so none sets it today) */
     LF_ERR_INTERNAL = 6
 } lf_status;
 
 /* device status word bits, read by lf_sync_status */
 #define LF_FLAG_BUCKET_OVERFLOW 0x1
 #define LF_FLAG_PLANE_RANGE     0x2
-#define LF_FLAG_TIMEOUT         0x4
+#define LF_FLAG_TIMEOUT         0x4   /* reserved; see LF_ERR_TIMEOUT */
 
 typedef struct lf_ctx lf_ctx;
 
@@ -190,8 +191,11 @@ typedef struct {
     int32_t extend_bps;        /* above what fits is lowered to it)                                  */
 } lf_tuning;
 
-/* Create a context: validates and copies geometry and parameters.
- * Returns LF_ERR_ARG on a parameter outside its range. */
+/* Create a context: validates and copies geometry and parameters (the
+ * constants of Sec. "Defining the search windows", "Triplet Seeding",
+ * "Extending triplets to other layers" and "Quality Filter"; Table
+ * tolerances, Table C_nhits, Table poly_tol).  Returns LF_ERR_ARG on a
+ * parameter outside its range. */
 lf_status lf_create(const lf_geometry* geometry, const lf_params* params, lf_ctx** out);
 
 /* Release the context and its scratch (synchronises the device). */
@@ -203,8 +207,16 @@ const char* lf_last_error(const lf_ctx* ctx);
 /* Number of SMs of the current device (for launch sizing). */
 int32_t lf_device_sm_count(void);
 
-/* Bucket and sort raw hits: per event, buckets ordered zone*12+layer, x
- * ascending inside a bucket, ties by raw index; -0.0 becomes +0.0.  Output
+/* Host NUMA node nearest to the current device (cudaDevAttrHostNumaId), or
+ * -1 when the platform does not report one.  Page-locked host buffers placed
+ * on that node (allocated by a thread running there) give the host link its
+ * full bandwidth to this device. */
+int32_t lf_device_host_numa(void);
+
+/* Bucket and sort raw hits (the per-layer x-sorted hit containers the
+ * search windows of Sec. "Defining the search windows" are index ranges
+ * of): per event, buckets ordered zone*12+layer, x ascending inside a
+ * bucket, ties by raw index; -0.0 becomes +0.0.  Output
  * arrays hold raw->n_hits entries and hit_offsets 24*n_events+1.  A plane
  * code >= 24 sets status flag 0x2 (the hit is counted in bucket 23); a
  * bucket above LF_MAX_BUCKET hits sets flag 0x1 and is not sorted (its perm
@@ -212,12 +224,15 @@ int32_t lf_device_sm_count(void);
  * context's work-queue cursor. */
 lf_status lf_pack_hits(lf_ctx* ctx, const lf_raw_hits* raw, const lf_packed* packed, void* stream);
 
-/* Plain form: one launch per stage (windows, triplets, extension+fit,
- * selection, compaction) over the whole batch, intermediate results in
- * context scratch. */
+/* Plain form of the whole method (Sec. "Defining the search windows",
+ * "Triplet Seeding", "Extending triplets to other layers", "Quality
+ * Filter", "Calculation of momentum and track states"): one launch per
+ * stage (windows, triplets, extension+fit, selection, compaction) over the
+ * whole batch, intermediate results in context scratch. */
 lf_status lf_find_tracks(lf_ctx* ctx, const lf_batch* batch, const lf_output* out, void* stream);
 
-/* Persistent form: persistent kernels over device work queues (by default a
+/* Persistent form of the same method (the sections listed for
+ * lf_find_tracks): persistent kernels over device work queues (by default a
  * pipeline of one persistent kernel per stage; see lf_tuning.queue), then
  * compaction.  The first call with a given launch shape (tuning, sizes and
  * every batch and output pointer) launches the kernels directly; when the
@@ -300,7 +315,10 @@ lf_status lf_process_host(lf_ctx* ctx, const lf_host_batch* batch, const lf_host
  * GPU loading the library keeps until the process exits.  The caller passes
  * inputs and outputs as for lf_find_tracks_batched.
  *   - The first call on a device (with that device current) looks the array's
- *     address up once; make that first call before any stream capture.
+ *     address up once; make that first call before any stream capture.  A
+ *     device reset (cudaDeviceReset) may move the array: the address looked
+ *     up before it is not valid after it, so do not call this entry point
+ *     on a device that was reset in the same process.
  *   - All calls share the array; each call clears the cursor it needs.  Calls
  *     that overlap on the GPU (other streams, other threads) race on it.
  *   - Returns LF_ERR_CAPACITY, without launching, when batch->n_events is

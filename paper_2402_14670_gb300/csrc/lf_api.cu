@@ -342,6 +342,16 @@ int32_t lf_device_sm_count(void) {
     return n;
 }
 
+int32_t lf_device_host_numa(void) {
+    int dev = 0, id = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (cudaDeviceGetAttribute(&id, cudaDevAttrHostNumaId, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return id;
+}
+
 lf_status lf_pack_hits(lf_ctx* c, const lf_raw_hits* raw, const lf_packed* pk, void* stream) {
     if (!c) return LF_ERR_ARG;
     if (!raw || !pk) return fail(c, LF_ERR_ARG, "raw or packed is NULL");

@@ -105,6 +105,8 @@ _lib.lf_last_error.argtypes = [_P]
 _lib.lf_last_error.restype = C.c_char_p
 _lib.lf_device_sm_count.argtypes = []
 _lib.lf_device_sm_count.restype = C.c_int32
+_lib.lf_device_host_numa.argtypes = []
+_lib.lf_device_host_numa.restype = C.c_int32
 _lib.lf_pack_hits.argtypes = [_P, C.POINTER(lf_raw_hits), C.POINTER(lf_packed), _P]
 _lib.lf_pack_hits.restype = C.c_int
 _lib.lf_find_tracks.argtypes = [_P, C.POINTER(lf_batch), C.POINTER(lf_output), _P]
@@ -131,7 +133,7 @@ _lib.lf_host_free.restype = None
 
 EXPORTED = ["lf_create", "lf_destroy", "lf_last_error", "lf_device_sm_count", "lf_pack_hits", "lf_find_tracks",
             "lf_find_tracks_batched", "lf_debug_stages", "lf_sync_status", "lf_process_host",
-            "lf_find_tracks_static", "lf_host_alloc", "lf_host_free", "lf_reserve"]
+            "lf_find_tracks_static", "lf_host_alloc", "lf_host_free", "lf_reserve", "lf_device_host_numa"]
 
 
 class LFError(RuntimeError):
@@ -246,6 +248,10 @@ def lf_last_error(ctx) -> str:
 
 def lf_device_sm_count() -> int:
     return int(_lib.lf_device_sm_count())
+
+
+def lf_device_host_numa() -> int:
+    return int(_lib.lf_device_host_numa())
 
 
 def lf_reserve(ctx, n_events: int, n_tracks: int, tuning: Optional["lf_tuning"] = None) -> None:
@@ -491,3 +497,22 @@ class Tracker:
         packed = self.pack(raw, stream)
         out = self.find(packed, raw, raw.n_events, mode, tuning, stream)
         return packed, out
+
+
+def numa_node_cpus() -> dict:
+    """NUMA node -> CPU ids of this host that the process may run on (from
+    /sys; empty when the host reports no nodes)."""
+    import glob
+    allowed = os.sched_getaffinity(0)
+    out = {}
+    for path in sorted(glob.glob("/sys/devices/system/node/node[0-9]*/cpulist")):
+        node = int(path.split("/node")[-1].split("/")[0])
+        cpus = set()
+        for part in open(path).read().strip().split(","):
+            if not part:
+                continue
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        if cpus & allowed:
+            out[node] = sorted(cpus & allowed)
+    return out

@@ -8,7 +8,8 @@ copies in, compute (two of these, alternating over the slots), copies out.
 Whenever a slot is free it takes every event that has arrived and is not yet
 scheduled (up to the slot's event and hit capacity); its copies in are queued
 on the first stream, its pack and find (persistent form, launch shape from the
-autotuner for the batch's size bucket) on its compute stream after them, and the copies of its per-track
+autotuner for the batch's size bucket, tuned on the pool's events before
+serving) on its compute stream after them, and the copies of its per-track
 results on the third stream after the compute, chained by events.  So the
 copies in of one batch, the compute of another and the copies out of a third
 overlap on the device.
@@ -138,6 +139,24 @@ class Server:
     def close(self):
         for s in self.slots:
             s.close()
+
+    def tune_buckets(self, sizes=(256, 1024, 2048)) -> dict:
+        """Autotune the launch shape for batches of the pool's first n events
+        for each n in sizes (their buckets), before serving: the first slot's
+        tracker runs the candidates on a device copy of those events."""
+        chosen = {}
+        tr = self.slots[0].tr
+        for n in sizes:
+            n = min(int(n), self.pool.n_events, self.max_events)
+            if n <= 0:
+                continue
+            sub = self.pool.select_events(range(n)).to(self.dev)
+            if sub.n_tracks == 0:
+                continue
+            packed = tr.pack(sub)
+            chosen[n] = self.tuner.choose(tr, packed, sub, n)
+        torch.cuda.synchronize(self.dev)
+        return chosen
 
     # -------------------------------------------------------------- batches
     def _take(self, head: int, avail: int) -> tuple:
