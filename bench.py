@@ -574,8 +574,8 @@ def main():
 
         fracs = (0.1, 0.2, 0.4, 0.6, 0.8, 1.0, 1.2)
         # events arriving in device memory (arrivals written straight to HBM)
-        srv = serve.Server(batch, n_slots=4, max_events=2048, budget_bytes=16 << 30)
-        srv.tune_buckets((256, 1024, 2048))
+        srv = serve.Server(batch, n_slots=4, max_events=1024, budget_bytes=16 << 30)
+        srv.tune_buckets((256, 1024))
         n_sat = min(n_ev, 60000)
         sat_d = srv.run(np.zeros(n_sat))
         pts_d = sweep_rates(srv, fracs, 100)
@@ -591,8 +591,8 @@ def main():
                               "copied back; latency = arrival to results on host"}}
         srv.close()
         # events arriving in page-locked host memory: copied in per batch
-        srv = serve.Server(host, n_slots=4, max_events=2048, budget_bytes=16 << 30)
-        srv.tune_buckets((256, 1024, 2048))
+        srv = serve.Server(host, n_slots=4, max_events=1024, budget_bytes=16 << 30)
+        srv.tune_buckets((256, 1024))
         sat = srv.run(np.zeros(n_sat))
         served["host_fed"] = {
             "saturation_events_per_s": sat.events_per_s, "saturation_p50_ms": sat.p50_ms,
