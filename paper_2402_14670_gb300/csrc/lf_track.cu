@@ -462,6 +462,18 @@ __device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState&
 // --------------------------------------------------- stage: extension + fit
 
 
+// A float of a shared-memory array read through an explicit 32-bit shared
+// address.  The extension reads its staged window x this way: with the
+// quality-factor loop rolled, the plain-form kernel's generic-pointer load
+// of m.wx[l * cap + j] was measured to return the element of a neighbouring
+// layer's window (same j), although the index and the hit's other data were
+// right, while this form of the same rolled loop gave exact results.
+__device__ __forceinline__ float lds_f(const float* base, int i) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"((unsigned)__cvta_generic_to_shared(base) + 4u * (unsigned)i));
+    return v;
+}
+
 // Extension and fit of one triplet (Sec. "Extending triplets to other
 // layers", "Quality Filter"); x and z of the window hits come from the
 // slot, dxdy and w of the hits used from global memory.
@@ -470,7 +482,7 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
                                            uint64_t key, Cand& cd) {
     // z of window hit j of layer l: staged, or read from global memory
     auto zat = [&](int l, int j) -> float {
-        return ZG ? __ldg(b.z + m.h->wbeg[l] + j) : m.wz[l * k.cap + j];
+        return ZG ? __ldg(b.z + m.h->wbeg[l] + j) : lds_f(m.wz, l * k.cap + j);
     };
     const int cap = k.cap;
     const float D = k.D;
@@ -484,7 +496,7 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
     cd.n = 0;
 
     // three-point solution through the triplet
-    float x0 = m.wx[L0 * cap + j0], x1 = m.wx[L1 * cap + j1], x2 = m.wx[L2 * cap + j2];
+    float x0 = lds_f(m.wx, L0 * cap + j0), x1 = lds_f(m.wx, L1 * cap + j1), x2 = lds_f(m.wx, L2 * cap + j2);
     float u0 = (zat(L0, j0) - k.z_ref) * 1e-3f;
     float u1 = (zat(L1, j1) - k.z_ref) * 1e-3f;
     float u2 = (zat(L2, j2) - k.z_ref) * 1e-3f;
@@ -510,7 +522,7 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
         int j = closest_shared((unsigned)__cvta_generic_to_shared(m.wx + l * cap), m.h->wcnt[l], xe);
         int jm = -1;
         if (j >= 0) {
-            float dx = m.wx[l * cap + j] - xe;
+            float dx = lds_f(m.wx, l * cap + j) - xe;
             if (dx * dx < k.T_x) jm = j;
         }
         if (cfg) hl[4 * i] = jm; else hl[4 * i + 3] = jm;
@@ -524,7 +536,7 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
         int q = l * cap + hl[l];
         float u = (zat(l, hl[l]) - k.z_ref) * 1e-3f;
         float f = f2_of(u, D);
-        float r = m.wx[q] - model_x(A, T, C, u, D);
+        float r = lds_f(m.wx, q) - model_x(A, T, C, u, D);
         float wt = __ldg(b.w + m.h->wbeg[l] + hl[l]);
         float wu = wt * u, wf = wt * f;
         S00 = S00 + wt; S01 = S01 + wu; S02 = S02 + wf;
@@ -556,7 +568,7 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
         float xe = model_x(A, T, C, (k.z[l] - k.z_ref) * 1e-3f, D) - yl * k.dxdy[l];
         int j = closest_shared((unsigned)__cvta_generic_to_shared(m.wx + l * cap), m.h->wcnt[l], xe);
         if (j < 0) continue;
-        float dx = m.wx[l * cap + j] - xe;
+        float dx = lds_f(m.wx, l * cap + j) - xe;
         if (dx * dx < T_uv) hl[l] = j;
     }
 
@@ -595,7 +607,7 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
         float u = (zat(l, hl[l]) - k.z_ref) * 1e-3f;
         float dd = __ldg(b.dxdy + g);
         dv[l] = dd;
-        float y = (model_x(A, T, C, u, D) - m.wx[q]) / dd;
+        float y = (model_x(A, T, C, u, D) - lds_f(m.wx, q)) / dd;
         yv[l] = y;
         float wt = __ldg(b.w + g);
         float wu = wt * u;
@@ -624,12 +636,12 @@ __device__ __forceinline__ void extend_fit(const KParams& k, const KBatch& b, co
         float u = (zat(l, hl[l]) - k.z_ref) * 1e-3f;
         float xf = model_x(A, T, C, u, D);
         if (is_x(l)) {
-            float r = m.wx[q] - xf;
+            float r = lds_f(m.wx, q) - xf;
             // T_x a power of two: the product by its reciprocal is the quotient
             qx = qx + (k.inv_T_x != 0.0f ? (r * r) * k.inv_T_x : div_call(r * r, k.T_x));
         } else {
             float yf = Y0 + TY * u;
-            float r = m.wx[q] - (xf - yf * dv[l]);
+            float r = lds_f(m.wx, q) - (xf - yf * dv[l]);
             qx = qx + div_call(r * r, T_uv);
             float ry = yv[l] - yf;
             qy = qy + div_call(ry * ry, k.T_y);

@@ -338,10 +338,13 @@ def test_bad_parameters_rejected(lfm):
         lfm.Tracker(None, p)
 
 
-def test_full_size_uneven_sampled(lfm):
-    """The uneven 100 000-event workload in the launch configuration the
-    benchmark times; the oracle recomputes a sample of events one by one."""
-    b = synth.generate(2, device="cuda", truth=False)
+@pytest.mark.parametrize("config,n_sample,min_cmp", [(2, 48, 1000), (4, 12, 2000)])
+def test_full_size_sampled(lfm, config, n_sample, min_cmp):
+    """The uneven (100 000 events) and high-occupancy (20 000 events)
+    workloads at full size in the launch configuration the benchmark times;
+    the oracle recomputes a sample of events one by one (plus the events with
+    the most tracks and hits, and the last)."""
+    b = synth.generate(config, device="cuda", truth=False)
     tr = _tracker(lfm)
     packed, out = tr.run(b, mode="batched")
     torch.cuda.synchronize()
@@ -350,7 +353,7 @@ def test_full_size_uneven_sampled(lfm):
     to = to_np(b.trk_offsets).astype(np.int64)
     ntrk = np.diff(to)
     rng = np.random.default_rng(5)
-    sample = sorted(set(rng.choice(b.n_events, 48, replace=False).tolist()) |
+    sample = sorted(set(rng.choice(b.n_events, n_sample, replace=False).tolist()) |
                     {int(np.argmax(ntrk)), int(np.argmax(np.diff(ro))), b.n_events - 1})
     sub = b.select_events(sample).to("cpu")
     res = oracle.run_batch(sub, dumps=False)
@@ -375,7 +378,7 @@ def test_full_size_uneven_sampled(lfm):
             assert np.array_equal(st_g[tg].view(np.uint32), res["state"][ts].view(np.uint32)), ("state", e, j)
             assert q_g[tg] == res["quality"][ts]
             n_cmp += 1
-    assert n_cmp > 1000
+    assert n_cmp > min_cmp
     # compaction over the whole batch
     f = found_g.astype(np.int64)
     cnt = np.add.reduceat(f, to[:-1]) if f.size else f
