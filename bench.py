@@ -282,7 +282,7 @@ def pack_bytes(n_events, n_hits):
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("lf_track.cu", "lf_internal.h"):
+    for f in ("lf_track.cu", "lf_device.cuh", "lf_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2402_14670_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
