@@ -16,8 +16,9 @@
  *   Sec. "Quality Filter"                         y line fit, T_ty, Q_x, Q_y,
  *       Q = (Q_x/nDoF_x + Q_y/nDoF_y) C(n_hits) (Table C_nhits), Q < T_Q,
  *       best Q per input track;
- *   Sec. "Calculation of momentum and track states" q/p from the slope change
- *       in the linear kick form.
+ *   Sec. "Calculation of momentum and track states" q/p from the slope change,
+ *       in the linear kick form or (lf_params.qop_poly) through the field
+ *       integral's polynomial in dSlope (Eq. pt_kick).
  *
  * Conventions
  *   - Every pointer inside lf_raw_hits, lf_packed, lf_batch and lf_output is a
@@ -237,12 +238,61 @@ lf_status lf_find_tracks(lf_ctx* ctx, const lf_batch* batch, const lf_output* ou
  * compaction.  The first call with a given launch shape (tuning, sizes and
  * every batch and output pointer) launches the kernels directly; when the
  * same shape comes back it is captured into a CUDA graph, which later calls
- * replay (at most 64 graphs and 256 remembered shapes per context), reading
- * the buffers' current contents.  A call that changes any pointer or size is
- * a new shape.  tuning may be NULL (defaults).  Results are identical to
+ * replay (at most 64 graphs per context, the least recently used dropped
+ * first, and 256 remembered shapes), reading the buffers' current contents.
+ * A call that changes any pointer or size is a new shape (lf_process_slot
+ * replays one graph across batch sizes).  tuning may be NULL (defaults).  Results are identical to
  * lf_find_tracks. */
 lf_status lf_find_tracks_batched(lf_ctx* ctx, const lf_batch* batch, const lf_output* out,
                                  const lf_tuning* tuning, void* stream);
+
+/* Gather source of a slot batch (device pointers, caller-owned): batch event
+ * e of lf_process_slot reads its hits from the raw arrays starting at raw
+ * index hit_src[e], and its input states from sx..sqop starting at
+ * trk_src[e]; the batch's own offsets give each event's counts and its place
+ * in the slot's buffers. */
+typedef struct {
+    const int32_t* hit_src;    /* [event capacity] */
+    const int32_t* trk_src;    /* [event capacity] */
+    const float* sx; const float* sy; const float* stx; const float* sty; const float* sqop;
+} lf_gather;
+
+/* Slot form, for a serving loop: pack (as lf_pack_hits) and the persistent
+ * find (as lf_find_tracks_batched) of one batch held in a slot, the buffers
+ * of fixed capacity a server reuses from batch to batch, with the batch's
+ * event count read from device memory when the kernels run.
+ *   - raw, packed, batch and out are the slot's buffers.  raw->n_events ==
+ *     batch->n_events is the event capacity, raw->n_hits == batch->n_hits the
+ *     hit capacity, batch->n_tracks the track capacity; the batch's hit arrays
+ *     must be the packed arrays.
+ *   - *n_events_dev (device int32, written by the caller on `stream` before
+ *     this call) is the batch's event count n; raw->raw_offsets[0..n] and
+ *     batch->trk_offsets[0..n] (device data) give its hits and tracks.  They
+ *     must start at 0, not decrease and end within the capacities (the
+ *     kernels clamp n to the event capacity and the track count to the track
+ *     capacity; hit offsets are not checked on the device, as in
+ *     lf_pack_hits).
+ *   - gather == NULL: the raw arrays and the batch's state arrays hold the
+ *     batch itself.  Otherwise the raw arrays are a larger hit pool that the
+ *     pack reads event by event through gather->hit_src (no copy of the hits),
+ *     and the states are first copied from gather's arrays into the batch's
+ *     state arrays; perm then gives hit indices in the batch's own numbering
+ *     (hit k of batch event e is raw index raw_offsets[e] + k).
+ *   - Every call with the same buffers, gather arrays, count pointer and
+ *     tuning replays one CUDA graph, captured on the first such call, whatever
+ *     the batch's size (a context keeps at most 64 graphs, dropping the least
+ *     recently used).  Results are identical to lf_pack_hits followed by
+ *     lf_find_tracks_batched on the same batch.
+ *   - LF_ERR_ARG on a NULL array, capacities that differ between raw and
+ *     batch, or batch hit arrays other than the packed ones; LF_ERR_CUDA on a
+ *     launch or capture error.  Asynchronous on stream. */
+lf_status lf_process_slot(lf_ctx* ctx, const lf_raw_hits* raw, const lf_packed* packed, const lf_batch* batch,
+                          const lf_gather* gather, const int32_t* n_events_dev, const lf_output* out,
+                          const lf_tuning* tuning, void* stream);
+
+/* Number of CUDA graphs the context has captured since its creation (the
+ * batched and slot forms), or -1 for a NULL context. */
+int64_t lf_graph_count(const lf_ctx* ctx);
 
 /* Host-resident batch for lf_process_host: pointers are HOST pointers
  * (pinned memory gives full copy bandwidth; pageable memory also works). */

@@ -25,7 +25,7 @@ struct DevBuf {
 // the launch shape, the sizes, the scratch generation and every batch and
 // output pointer: a call that changes any of them is a new shape.
 struct GraphKey {
-    std::array<uintptr_t, 26> v;
+    std::array<uintptr_t, 48> v{};
     bool operator<(const GraphKey& o) const { return v < o.v; }
 };
 
@@ -45,9 +45,11 @@ struct lf_ctx {
     DevBuf trk_event, wbeg, wcnt, keys, ntrip, cands, ev_count;
     struct GraphEntry {
         cudaGraphExec_t exec = nullptr;
-        cudaStream_t stream = nullptr;
+        unsigned long long used = 0;   // last use (graph_clock), for eviction
     };
     std::map<GraphKey, GraphEntry> graphs;
+    unsigned long long graph_clock = 0;
+    unsigned long long graph_captures = 0;   // graphs captured since creation
     // launch shapes seen once: a shape is captured into a graph only when it
     // comes back (a serving loop's batch sizes rarely repeat)
     std::map<GraphKey, unsigned long long> seen;
@@ -226,6 +228,7 @@ KBatch to_kbatch(const lf_batch* b) {
     k.stx = b->stx;
     k.sty = b->sty;
     k.sqop = b->sqop;
+    k.n_dev = nullptr;
     return k;
 }
 
@@ -449,8 +452,10 @@ int stage_grid(lf_ctx* c, const Shape& sh, int i) {
 
 // persistent form, launches only (scratch prepared): queue reset, the stage
 // pipeline or the tile kernel, compaction
-lf_status launch_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const Shape& sh, cudaStream_t s) {
+lf_status launch_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const Shape& sh, cudaStream_t s,
+                         const int* n_dev = nullptr) {
     KBatch kb = to_kbatch(b);
+    kb.n_dev = n_dev;
     KOut ko = to_kout(o);
     LF_CUDA(c, cudaMemsetAsync(c->cursor, 0, 8 * sizeof(int), s));
     if (b->n_tracks > 0) {
@@ -471,7 +476,7 @@ lf_status launch_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const
         }
     }
     LF_CUDA(c, launch_compact(b->trk_offsets, o->found, b->n_events, (int*)c->ev_count.p, o->out_offsets, o->out_trk,
-                              o->n_out, s));
+                              o->n_out, s, n_dev));
     return LF_OK;
 }
 
@@ -482,6 +487,70 @@ lf_status batched_direct(lf_ctx* c, const lf_batch* b, const lf_output* o, const
 }
 
 }  // namespace
+
+extern "C++" {
+namespace {
+
+constexpr size_t MAX_GRAPHS = 64;
+
+// The graph of `key`, captured from `launch(stream)` when missing (the least
+// recently used graph is dropped when the cache is full), then replayed on s.
+template <class Launch>
+lf_status graph_replay(lf_ctx* c, const GraphKey& key, cudaStream_t s, Launch&& launch) {
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        cudaStream_t cap;
+        LF_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        lf_status ls = LF_OK;
+        if (e == cudaSuccess) ls = launch(cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = e2;
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess && ls == LF_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        if (ls != LF_OK) return ls;
+        if (e != cudaSuccess) return fail(c, LF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        if (c->graphs.size() >= MAX_GRAPHS) {
+            auto old = c->graphs.begin();
+            for (auto jt = c->graphs.begin(); jt != c->graphs.end(); ++jt)
+                if (jt->second.used < old->second.used) old = jt;
+            if (old->second.exec) cudaGraphExecDestroy(old->second.exec);
+            c->graphs.erase(old);
+        }
+        lf_ctx::GraphEntry ge;
+        ge.exec = exec;
+        it = c->graphs.emplace(key, ge).first;
+        ++c->graph_captures;
+    }
+    it->second.used = ++c->graph_clock;
+    LF_CUDA(c, cudaGraphLaunch(it->second.exec, s));
+    return LF_OK;
+}
+
+// key words: the launch shape, then the caller's sizes and pointers
+void key_shape(GraphKey& key, size_t& i, const Shape& sh, unsigned long long generation, uintptr_t form) {
+    key.v[i++] = form;
+    key.v[i++] = (uintptr_t)sh.wpb;
+    key.v[i++] = (uintptr_t)sh.bps;
+    key.v[i++] = (uintptr_t)(sh.grain + 64 * sh.queue + ((uintptr_t)sh.stage_bps[0] << 8) +
+                             ((uintptr_t)sh.stage_bps[1] << 16) + ((uintptr_t)sh.stage_bps[2] << 24));
+    key.v[i++] = (uintptr_t)generation;
+}
+void key_batch(GraphKey& key, size_t& i, const lf_batch* b, const lf_output* o) {
+    const uintptr_t w[] = {(uintptr_t)b->n_events, (uintptr_t)b->n_tracks, (uintptr_t)b->n_hits,
+                           (uintptr_t)b->hit_offsets, (uintptr_t)b->x, (uintptr_t)b->z, (uintptr_t)b->dxdy,
+                           (uintptr_t)b->w, (uintptr_t)b->trk_offsets, (uintptr_t)b->sx, (uintptr_t)b->sy,
+                           (uintptr_t)b->stx, (uintptr_t)b->sty, (uintptr_t)b->sqop, (uintptr_t)o->found,
+                           (uintptr_t)o->nhits, (uintptr_t)o->hit_idx, (uintptr_t)o->state, (uintptr_t)o->quality,
+                           (uintptr_t)o->out_offsets, (uintptr_t)o->out_trk, (uintptr_t)o->n_out};
+    for (uintptr_t x : w) key.v[i++] = x;
+}
+
+}  // namespace
+}  // extern "C++"
 
 lf_status lf_find_tracks_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const lf_tuning* tuning,
                                  void* stream) {
@@ -495,19 +564,10 @@ lf_status lf_find_tracks_batched(lf_ctx* c, const lf_batch* b, const lf_output* 
     if ((st = prepare_batched(c, b, sh)) != LF_OK) return st;
 
     GraphKey key;
-    {
-        const auto u = [](const void* q) { return (uintptr_t)q; };
-        key.v = {(uintptr_t)sh.wpb, (uintptr_t)sh.bps,
-                 (uintptr_t)(sh.grain + 64 * sh.queue + ((uintptr_t)sh.stage_bps[0] << 8) +
-                             ((uintptr_t)sh.stage_bps[1] << 16) + ((uintptr_t)sh.stage_bps[2] << 24)),
-                 (uintptr_t)b->n_events, (uintptr_t)b->n_tracks, (uintptr_t)b->n_hits, (uintptr_t)c->generation,
-                 u(b->hit_offsets), u(b->x), u(b->z), u(b->dxdy), u(b->w), u(b->trk_offsets),
-                 u(b->sx), u(b->sy), u(b->stx), u(b->sty), u(b->sqop),
-                 u(o->found), u(o->nhits), u(o->hit_idx), u(o->state), u(o->quality),
-                 u(o->out_offsets), u(o->out_trk), u(o->n_out)};
-    }
-    auto it = c->graphs.find(key);
-    if (it == c->graphs.end()) {
+    size_t i = 0;
+    key_shape(key, i, sh, c->generation, 1);
+    key_batch(key, i, b, o);
+    if (c->graphs.find(key) == c->graphs.end()) {
         // first use of this shape: launch directly and remember it (bounded)
         if (c->seen.find(key) == c->seen.end()) {
             if (c->seen.size() >= 256) {
@@ -519,33 +579,56 @@ lf_status lf_find_tracks_batched(lf_ctx* c, const lf_batch* b, const lf_output* 
             c->seen[key] = ++c->seen_clock;
             return launch_batched(c, b, o, sh, s);
         }
-        cudaStream_t cap;
-        LF_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-        cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-        lf_status ls = LF_OK;
-        if (e == cudaSuccess) ls = launch_batched(c, b, o, sh, cap);
-        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
-        if (e == cudaSuccess) e = e2;
-        cudaGraphExec_t exec = nullptr;
-        if (e == cudaSuccess && ls == LF_OK) e = cudaGraphInstantiate(&exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        cudaStreamDestroy(cap);
-        if (ls != LF_OK) return ls;
-        if (e != cudaSuccess) return fail(c, LF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-        // keep a bounded cache of shapes
-        if (c->graphs.size() >= 64) {
-            for (auto& kv : c->graphs)
-                if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-            c->graphs.clear();
-        }
-        lf_ctx::GraphEntry ge;
-        ge.exec = exec;
-        it = c->graphs.emplace(key, ge).first;
     }
-    LF_CUDA(c, cudaGraphLaunch(it->second.exec, s));
-    return LF_OK;
+    return graph_replay(c, key, s, [&](cudaStream_t cs) { return launch_batched(c, b, o, sh, cs); });
 }
+
+lf_status lf_process_slot(lf_ctx* c, const lf_raw_hits* raw, const lf_packed* pk, const lf_batch* b,
+                          const lf_gather* g, const int32_t* n_events_dev, const lf_output* o,
+                          const lf_tuning* tuning, void* stream) {
+    if (!c) return LF_ERR_ARG;
+    lf_status st;
+    if (!raw || !pk || !n_events_dev) return fail(c, LF_ERR_ARG, "raw, packed or n_events_dev is NULL");
+    if ((st = check_batch(c, b)) != LF_OK) return st;
+    if ((st = check_out(c, o, b->n_tracks)) != LF_OK) return st;
+    if (raw->n_events != b->n_events || raw->n_hits != b->n_hits)
+        return fail(c, LF_ERR_ARG, "raw and batch capacities differ");
+    if (!raw->raw_offsets || !raw->x || !raw->z || !raw->dxdy || !raw->w || !raw->plane || !pk->layer || !pk->perm)
+        return fail(c, LF_ERR_ARG, "a raw or packed array is NULL");
+    if (b->hit_offsets != pk->hit_offsets || b->x != pk->x || b->z != pk->z || b->dxdy != pk->dxdy || b->w != pk->w)
+        return fail(c, LF_ERR_ARG, "the batch's hit arrays are not the packed arrays");
+    if (g && (!g->hit_src || !g->trk_src || !g->sx || !g->sy || !g->stx || !g->sty || !g->sqop))
+        return fail(c, LF_ERR_ARG, "a gather array is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    Shape sh;
+    if ((st = resolve_shape(c, tuning, sh)) != LF_OK) return st;
+    if ((st = prepare_batched(c, b, sh)) != LF_OK) return st;
+
+    GraphKey key;
+    size_t i = 0;
+    key_shape(key, i, sh, c->generation, 2);
+    key_batch(key, i, b, o);
+    const uintptr_t w[] = {(uintptr_t)n_events_dev, (uintptr_t)raw->raw_offsets, (uintptr_t)raw->x,
+                           (uintptr_t)raw->z, (uintptr_t)raw->dxdy, (uintptr_t)raw->w, (uintptr_t)raw->plane,
+                           (uintptr_t)pk->layer, (uintptr_t)pk->perm, (uintptr_t)(g ? g->hit_src : nullptr),
+                           (uintptr_t)(g ? g->trk_src : nullptr), (uintptr_t)(g ? g->sx : nullptr),
+                           (uintptr_t)(g ? g->sy : nullptr), (uintptr_t)(g ? g->stx : nullptr),
+                           (uintptr_t)(g ? g->sty : nullptr), (uintptr_t)(g ? g->sqop : nullptr)};
+    for (uintptr_t x : w) key.v[i++] = x;
+    return graph_replay(c, key, s, [&](cudaStream_t cs) -> lf_status {
+        if (g) {
+            KBatch kb = to_kbatch(b);
+            kb.n_dev = n_events_dev;
+            LF_CUDA(c, launch_gather_states(kb, g->trk_src, g->sx, g->sy, g->stx, g->sty, g->sqop, c->n_sm, cs));
+        }
+        LF_CUDA(c, launch_pack(raw->raw_offsets, raw->x, raw->z, raw->dxdy, raw->w, raw->plane, raw->n_events,
+                               raw->n_hits, pk->hit_offsets, pk->x, pk->z, pk->dxdy, pk->w, pk->layer, pk->perm,
+                               c->cursor + 6, c->status, c->n_sm, cs, n_events_dev, g ? g->hit_src : nullptr));
+        return launch_batched(c, b, o, sh, cs, n_events_dev);
+    });
+}
+
+int64_t lf_graph_count(const lf_ctx* c) { return c ? (int64_t)c->graph_captures : -1; }
 
 lf_status lf_debug_stages(lf_ctx* c, const lf_batch* b, int32_t* win_begin, int32_t* win_count, int32_t* n_trip,
                           int32_t* trip, float* trip_chi2, void* stream) {

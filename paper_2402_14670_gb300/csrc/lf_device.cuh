@@ -1,8 +1,7 @@
-// Device helpers shared by the track-following kernels (lf_track.cu, the
-// per-track stage kernels; lf_event.cu, the per-event kernel): the method's
+// Device helpers of the track-following kernels (lf_track.cu): the method's
 // extrapolation and window arithmetic, the fit model, warp primitives and the
 // warp-vote selection.  Every helper is inline (or static), so each
-// translation unit holds its own copy.
+// translation unit that includes this header holds its own copy.
 #pragma once
 #include <cstdint>
 

@@ -56,7 +56,29 @@ struct KBatch {
     const float *x, *z, *dxdy, *w;
     const int* trk_offsets;
     const float *sx, *sy, *stx, *sty, *sqop;
+    // slot form: the batch's event count in device memory; n_events and
+    // n_tracks above are then the slot's capacities (nullptr otherwise)
+    const int* n_dev;
 };
+
+// Sizes of a slot batch, read when the kernel runs: the event count from
+// device memory, clamped to the slot's capacity, and the track count from
+// the batch's offsets, clamped likewise.  No-op outside the slot form.
+__device__ __forceinline__ void slot_sizes(KBatch& b) {
+    if (b.n_dev) {
+        int n = *b.n_dev;
+        n = n < 0 ? 0 : (n > b.n_events ? b.n_events : n);
+        const int t = b.trk_offsets[n];
+        b.n_tracks = t < 0 ? 0 : (t > b.n_tracks ? b.n_tracks : t);
+        b.n_events = n;
+    }
+}
+// the event count of a slot batch (n_dev set) or n (otherwise), clamped to n
+__device__ __forceinline__ int slot_events(const int* n_dev, int n) {
+    if (!n_dev) return n;
+    const int v = *n_dev;
+    return v < 0 ? 0 : (v > n ? n : v);
+}
 
 struct KOut {
     uint8_t* found;
@@ -112,10 +134,19 @@ KParams make_kparams(const lf_geometry* g, const lf_params* p);
 
 // ---- launchers (defined in the .cu files) ----
 // persistent per-event pack; cursor: two device ints (the work queues)
+// n_dev: slot form (event count in device memory, n_events and n_hits the
+// capacities; nullptr otherwise); hit_src: per event, the raw index of its
+// first hit (the event is read from there and written at raw_offsets[e] of
+// the output; nullptr: read at raw_offsets[e])
 cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, const float* dxdy,
                         const float* w, const uint8_t* plane, int n_events, int n_hits, int* hit_offsets,
                         float* ox, float* oz, float* odxdy, float* ow, uint8_t* olayer, int* perm, int* cursor,
-                        int* status, int n_sm, cudaStream_t s);
+                        int* status, int n_sm, cudaStream_t s, const int* n_dev = nullptr,
+                        const int* hit_src = nullptr);
+// slot form with a gather source: the states of batch event e's tracks are
+// copied from src (starting at trk_src[e]) to the batch's state arrays
+cudaError_t launch_gather_states(const KBatch& b, const int* trk_src, const float* sx, const float* sy,
+                                 const float* stx, const float* sty, const float* sqop, int n_sm, cudaStream_t s);
 
 cudaError_t launch_track_event(const KBatch& b, int* trk_event, cudaStream_t s);
 // stage kernels: cursor == nullptr launches the plain one-pass grid,
@@ -141,7 +172,7 @@ cudaError_t fused_max_blocks_per_sm(const KParams& k, int warps_per_block, int g
 cudaError_t launch_hits_to_raw(const uint8_t* found, int* hit_idx, const int* perm, int n_tracks, int base,
                               cudaStream_t s);
 cudaError_t launch_compact(const int* trk_offsets, const uint8_t* found, int n_events, int* ev_count,
-                           int* out_offsets, int* out_trk, int* n_out, cudaStream_t s);
+                           int* out_offsets, int* out_trk, int* n_out, cudaStream_t s, const int* n_dev = nullptr);
 cudaError_t launch_debug_triplets(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* wcnt,
                                   const uint64_t* keys, const uint8_t* ntrip, int* win_count_out, int* n_trip_out,
                                   int* trip_out, float* chi2_out, cudaStream_t s);

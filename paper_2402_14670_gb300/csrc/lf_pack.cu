@@ -591,10 +591,11 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
     const int* __restrict__ raw_offsets, const float* __restrict__ x, const float* __restrict__ z,
     const float* __restrict__ dxdy, const float* __restrict__ w, const uint8_t* __restrict__ plane, int n_events,
     int* hit_offsets, float* ox, float* oz, float* od, float* ow, uint8_t* ol, int* perm, int* cursor,
-    int* status) {
+    int* status, const int* __restrict__ n_dev, const int* __restrict__ hit_src) {
     extern __shared__ __align__(16) char smem[];
     __shared__ EvShared sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    n_events = slot_events(n_dev, n_events);
     if (blockIdx.x == 0 && tid == 0) hit_offsets[(size_t)n_events * NB] = raw_offsets[n_events];
     if (tid == 0) sh.next = atomicAdd(cursor, 1);
     for (;;) {
@@ -608,19 +609,23 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
         __syncthreads();
         const int e = sh.event;
         if (e >= n_events) break;
+        // the event's place in the output (rb) and in the input (ib: the
+        // same, or its gather source)
         const int rb = raw_offsets[e], n = raw_offsets[e + 1] - rb;
+        const int ib = hit_src ? hit_src[e] : rb;
         // this event's payload and the next event's keys go to L2 while the
         // event is sorted (addresses inside the events' ranges only)
         if (n > 0) {
-            prefetch_range(z + rb, (size_t)n * 4, tid);
-            prefetch_range(dxdy + rb, (size_t)n * 4, tid);
-            prefetch_range(w + rb, (size_t)n * 4, tid);
+            prefetch_range(z + ib, (size_t)n * 4, tid);
+            prefetch_range(dxdy + ib, (size_t)n * 4, tid);
+            prefetch_range(w + ib, (size_t)n * 4, tid);
         }
         if (sh.next < n_events) {
             const int nb0 = raw_offsets[sh.next], nn = raw_offsets[sh.next + 1] - nb0;
+            const int ni0 = hit_src ? hit_src[sh.next] : nb0;
             if (nn > 0) {
-                prefetch_range(plane + nb0, (size_t)nn, tid);
-                prefetch_range(x + nb0, (size_t)nn * 4, tid);
+                prefetch_range(plane + ni0, (size_t)nn, tid);
+                prefetch_range(x + ni0, (size_t)nn * 4, tid);
             }
         }
         if (n == 0) {
@@ -634,7 +639,9 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
             for (int i = tid; i < n; i += PACK_THREADS) perm[(size_t)rb + i] = -1;
             continue;
         }
-        const PackIO io{x, z, dxdy, w, plane, hit_offsets, ox, oz, od, ow, ol, perm, status};
+        // input pointers shifted so that raw index rb + i reads input ib + i
+        const ptrdiff_t d = (ptrdiff_t)ib - rb;
+        const PackIO io{x + d, z + d, dxdy + d, w + d, plane + d, hit_offsets, ox, oz, od, ow, ol, perm, status};
         if (n > 65535) sort_event<true>(io, sh, smem, e, rb, n, tid, lane, warp);
         else sort_event<false>(io, sh, smem, e, rb, n, tid, lane, warp);
     }
@@ -645,7 +652,7 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
 cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, const float* dxdy, const float* w,
                         const uint8_t* plane, int n_events, int n_hits, int* hit_offsets, float* ox, float* oz,
                         float* odxdy, float* ow, uint8_t* olayer, int* perm, int* cursor, int* status, int n_sm,
-                        cudaStream_t s) {
+                        cudaStream_t s, const int* n_dev, const int* hit_src) {
     (void)n_hits;
     cudaError_t err =
         cudaFuncSetAttribute(k_pack_event, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AREA_BYTES);
@@ -654,7 +661,8 @@ cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, 
     int grid = n_sm;
     if (grid > n_events) grid = n_events > 0 ? n_events : 1;
     k_pack_event<<<grid, PACK_THREADS, AREA_BYTES, s>>>(raw_offsets, x, z, dxdy, w, plane, n_events, hit_offsets,
-                                                        ox, oz, odxdy, ow, olayer, perm, cursor, status);
+                                                        ox, oz, odxdy, ow, olayer, perm, cursor, status, n_dev,
+                                                        hit_src);
     return cudaGetLastError();
 }
 

@@ -680,6 +680,7 @@ __device__ __forceinline__ int event_of(const int* __restrict__ trk_offsets, int
 // ================================================================ kernels
 
 __global__ void k_track_event(KBatch b, int* trk_event) {
+    slot_sizes(b);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < b.n_events; e += gridDim.x * blockDim.x) {
         int t0 = b.trk_offsets[e], t1 = b.trk_offsets[e + 1];
         for (int t = t0; t < t1; ++t) trk_event[t] = e;
@@ -768,6 +769,7 @@ template <bool P, bool NOUT>
 __global__ void k_windows(KParams k, KBatch b, const int* __restrict__ trk_event, int* wbeg, uint8_t* wcnt,
                           int* cursor) {
     const int lane = threadIdx.x & 31;
+    slot_sizes(b);
     if (!P) {
         const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         if (t < b.n_tracks) windows_track<NOUT>(k, b, trk_event, wbeg, wcnt, t, lane);
@@ -835,6 +837,7 @@ __global__ void __launch_bounds__(PLAIN_WARPS * 32, 5) k_triplets(KParams k, KBa
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Slot m = slot_at(smem, warp, k.cap);
     const Scratch sc = scratch_at(smem + PLAIN_WARPS * slot_bytes(k.cap), warp);
+    slot_sizes(b);
     if (!P) {
         const int t = blockIdx.x * PLAIN_WARPS + warp;
         if (t < b.n_tracks) triplets_track<NIT, NOUT>(k, b, wbeg, wcnt, keys, ntrip, m, sc, t, lane);
@@ -1000,6 +1003,7 @@ __global__ void __launch_bounds__(PLAIN_WARPS * 32, 4) k_extend(
     Slot sl[TPW];
 #pragma unroll
     for (int q = 0; q < TPW; ++q) sl[q] = slot_at(smem, warp * TPW + q, k.cap);
+    slot_sizes(b);
     if (!P) {
         const int t0 = (blockIdx.x * PLAIN_WARPS + warp) * TPW;
         if (t0 < b.n_tracks) {
@@ -1074,6 +1078,7 @@ __global__ void __launch_bounds__(512, 1) k_tile(KParams k, KBatch b, KOut o, in
 #pragma unroll
     for (int q = 0; q < TPW; ++q) sl[q] = slot_at(smem, warp * TPW + q, k.cap);
     const Scratch sc = scratch_at(smem + (size_t)nw * TPW * slot_bytes(k.cap), warp);
+    slot_sizes(b);
     for (;;) {
         int first, e;
         if (SYNC) {
@@ -1206,9 +1211,10 @@ __global__ void k_hits_to_raw(const uint8_t* __restrict__ found, int* hit_idx, c
 
 // per-event count of found tracks (warp per event)
 __global__ void k_compact_count(const int* __restrict__ trk_offsets, const uint8_t* __restrict__ found, int n_events,
-                                int* ev_count) {
+                                int* ev_count, const int* n_dev) {
     int lane = threadIdx.x & 31;
     int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    n_events = slot_events(n_dev, n_events);
     if (e >= n_events) return;
     int t0 = trk_offsets[e], t1 = trk_offsets[e + 1];
     int c = 0;
@@ -1219,10 +1225,12 @@ __global__ void k_compact_count(const int* __restrict__ trk_offsets, const uint8
 }
 
 // exclusive scan of the per-event counts by one block
-__global__ void k_compact_scan(const int* __restrict__ ev_count, int n_events, int* out_offsets, int* n_out) {
+__global__ void k_compact_scan(const int* __restrict__ ev_count, int n_events, int* out_offsets, int* n_out,
+                               const int* n_dev) {
     __shared__ int warp_tot[32];
     __shared__ int carry;
     int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    n_events = slot_events(n_dev, n_events);
     if (tid == 0) carry = 0;
     __syncthreads();
     for (int base = 0; base < n_events; base += blockDim.x) {
@@ -1251,9 +1259,10 @@ __global__ void k_compact_scan(const int* __restrict__ ev_count, int n_events, i
 
 // scatter of found track indices (warp per event, ballot positions)
 __global__ void k_compact_scatter(const int* __restrict__ trk_offsets, const uint8_t* __restrict__ found, int n_events,
-                                  const int* __restrict__ out_offsets, int* out_trk) {
+                                  const int* __restrict__ out_offsets, int* out_trk, const int* n_dev) {
     int lane = threadIdx.x & 31;
     int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    n_events = slot_events(n_dev, n_events);
     if (e >= n_events) return;
     int t0 = trk_offsets[e], t1 = trk_offsets[e + 1];
     int pos = out_offsets[e];
@@ -1263,6 +1272,29 @@ __global__ void k_compact_scatter(const int* __restrict__ trk_offsets, const uin
         unsigned msk = __ballot_sync(FULL, f);
         if (f) out_trk[pos + __popc(msk & ((1u << lane) - 1u))] = t;
         pos += __popc(msk);
+    }
+}
+
+// Slot form with a gather source: the input states of batch event e's
+// tracks are copied from the source arrays, starting at trk_src[e], to the
+// batch's own state arrays (warp per event, lanes over its tracks).
+__global__ void k_gather_states(KBatch b, const int* __restrict__ trk_src, const float* __restrict__ sx,
+                                const float* __restrict__ sy, const float* __restrict__ stx,
+                                const float* __restrict__ sty, const float* __restrict__ sqop, float* dx, float* dy,
+                                float* dtx, float* dty, float* dqop) {
+    slot_sizes(b);
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < b.n_events; e += nw) {
+        const int t0 = b.trk_offsets[e], t1 = min(b.trk_offsets[e + 1], b.n_tracks);
+        const long d = (long)trk_src[e] - t0;
+        for (int t = t0 + lane; t < t1; t += 32) {
+            dx[t] = sx[d + t];
+            dy[t] = sy[d + t];
+            dtx[t] = stx[d + t];
+            dty[t] = sty[d + t];
+            dqop[t] = sqop[d + t];
+        }
     }
 }
 
@@ -1442,15 +1474,27 @@ cudaError_t launch_hits_to_raw(const uint8_t* found, int* hit_idx, const int* pe
 }
 
 cudaError_t launch_compact(const int* trk_offsets, const uint8_t* found, int n_events, int* ev_count,
-                           int* out_offsets, int* out_trk, int* n_out, cudaStream_t s) {
+                           int* out_offsets, int* out_trk, int* n_out, cudaStream_t s, const int* n_dev) {
     if (n_events > 0) {
-        k_compact_count<<<cdiv((long)n_events * 32, 256), 256, 0, s>>>(trk_offsets, found, n_events, ev_count);
+        k_compact_count<<<cdiv((long)n_events * 32, 256), 256, 0, s>>>(trk_offsets, found, n_events, ev_count,
+                                                                       n_dev);
     }
-    k_compact_scan<<<1, 1024, 0, s>>>(ev_count, n_events, out_offsets, n_out);
+    k_compact_scan<<<1, 1024, 0, s>>>(ev_count, n_events, out_offsets, n_out, n_dev);
     if (n_events > 0) {
         k_compact_scatter<<<cdiv((long)n_events * 32, 256), 256, 0, s>>>(trk_offsets, found, n_events, out_offsets,
-                                                                         out_trk);
+                                                                         out_trk, n_dev);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_states(const KBatch& b, const int* trk_src, const float* sx, const float* sy,
+                                 const float* stx, const float* sty, const float* sqop, int n_sm, cudaStream_t s) {
+    if (b.n_events <= 0 || b.n_tracks <= 0) return cudaSuccess;
+    const int want = cdiv((long)b.n_events * 32, 256);
+    const int grid = want < 8 * n_sm ? want : 8 * n_sm;
+    k_gather_states<<<grid, 256, 0, s>>>(b, trk_src, sx, sy, stx, sty, sqop, const_cast<float*>(b.sx),
+                                         const_cast<float*>(b.sy), const_cast<float*>(b.stx),
+                                         const_cast<float*>(b.sty), const_cast<float*>(b.sqop));
     return cudaGetLastError();
 }
 

@@ -74,6 +74,10 @@ class lf_output(C.Structure):
                 ("out_offsets", _P), ("out_trk", _P), ("n_out", _P)]
 
 
+class lf_gather(C.Structure):
+    _fields_ = [("hit_src", _P), ("trk_src", _P), ("sx", _P), ("sy", _P), ("stx", _P), ("sty", _P), ("sqop", _P)]
+
+
 class lf_host_batch(C.Structure):
     _fields_ = [("n_events", C.c_int32), ("n_hits", C.c_int32), ("n_tracks", C.c_int32), ("raw_offsets", _P),
                 ("x", _P), ("z", _P), ("dxdy", _P), ("w", _P), ("plane", _P), ("trk_offsets", _P), ("sx", _P),
@@ -121,6 +125,11 @@ _lib.lf_process_host.argtypes = [_P, C.POINTER(lf_host_batch), C.POINTER(lf_host
                                  C.c_int64]
 _lib.lf_process_host.restype = C.c_int
 
+_lib.lf_process_slot.argtypes = [_P, C.POINTER(lf_raw_hits), C.POINTER(lf_packed), C.POINTER(lf_batch),
+                                 C.POINTER(lf_gather), _P, C.POINTER(lf_output), C.POINTER(lf_tuning), _P]
+_lib.lf_process_slot.restype = C.c_int
+_lib.lf_graph_count.argtypes = [_P]
+_lib.lf_graph_count.restype = C.c_int64
 _lib.lf_find_tracks_static.argtypes = [C.POINTER(lf_geometry), C.POINTER(lf_params), C.POINTER(lf_batch),
                                        C.POINTER(lf_output), _P]
 _lib.lf_find_tracks_static.restype = C.c_int
@@ -133,7 +142,8 @@ _lib.lf_host_free.restype = None
 
 EXPORTED = ["lf_create", "lf_destroy", "lf_last_error", "lf_device_sm_count", "lf_pack_hits", "lf_find_tracks",
             "lf_find_tracks_batched", "lf_debug_stages", "lf_sync_status", "lf_process_host",
-            "lf_find_tracks_static", "lf_host_alloc", "lf_host_free", "lf_reserve", "lf_device_host_numa"]
+            "lf_find_tracks_static", "lf_host_alloc", "lf_host_free", "lf_reserve", "lf_device_host_numa",
+            "lf_process_slot", "lf_graph_count"]
 
 
 class LFError(RuntimeError):
@@ -319,6 +329,18 @@ def lf_find_tracks_batched(ctx, batch: lf_batch, out: lf_output, tuning: Optiona
     _check(ctx, _lib.lf_find_tracks_batched(ctx, C.byref(batch), C.byref(out), tp, stream))
 
 
+def lf_process_slot(ctx, raw: lf_raw_hits, packed: lf_packed, batch: lf_batch, gather: Optional[lf_gather],
+                    n_events_dev: int, out: lf_output, tuning: Optional[lf_tuning], stream) -> None:
+    gp = C.byref(gather) if gather is not None else None
+    tp = C.byref(tuning) if tuning is not None else None
+    _check(ctx, _lib.lf_process_slot(ctx, C.byref(raw), C.byref(packed), C.byref(batch), gp, _P(n_events_dev),
+                                     C.byref(out), tp, stream))
+
+
+def lf_graph_count(ctx) -> int:
+    return int(_lib.lf_graph_count(ctx))
+
+
 def lf_debug_stages(ctx, batch: lf_batch, win_begin, win_count, n_trip, trip, trip_chi2, stream) -> None:
     _check(ctx, _lib.lf_debug_stages(ctx, C.byref(batch), win_begin, win_count, n_trip, trip, trip_chi2, stream))
 
@@ -497,6 +519,79 @@ class Tracker:
         packed = self.pack(raw, stream)
         out = self.find(packed, raw, raw.n_events, mode, tuning, stream)
         return packed, out
+
+    def process_slot(self, slot: "SlotBuffers", pool=None, tuning: Optional[dict] = None, stream=None) -> None:
+        """lf_process_slot on a slot's buffers: the batch whose event count is
+        in slot.n_dev (and offsets in slot.raw_offsets / slot.trk_offsets);
+        pool (an object with device x, z, dxdy, w, plane, sx, sy, stx, sty,
+        sqop) is the gather source, read through slot.hit_src / slot.trk_src."""
+        raw, pk, b, o = slot.structs(pool)
+        g = None
+        if pool is not None:
+            g = lf_gather(_ptr(slot.hit_src), _ptr(slot.trk_src), _ptr(pool.sx), _ptr(pool.sy), _ptr(pool.stx),
+                          _ptr(pool.sty), _ptr(pool.sqop))
+        lf_process_slot(self.ctx, raw, pk, b, g, slot.n_dev.data_ptr(), o, tuning_struct(tuning), _stream(stream))
+
+    def graph_count(self) -> int:
+        return lf_graph_count(self.ctx)
+
+
+class SlotBuffers:
+    """Device buffers of one slot of lf_process_slot, of fixed capacity:
+    offsets, states, packed hits, outputs, the event count (n_dev) and the
+    gather indices; raw hit arrays too unless the slot gathers from a pool."""
+
+    def __init__(self, max_events: int, max_hits: int, max_tracks: int, device, own_raw: bool = True):
+        e = lambda n, dt: torch.empty(max(int(n), 1), dtype=dt, device=device)
+        self.max_events, self.max_hits, self.max_tracks = int(max_events), int(max_hits), int(max_tracks)
+        # the per-batch values in one int32 block (one copy from the host per
+        # batch): event count, raw and track offsets, gather sources
+        self.meta = torch.zeros(self.meta_size(self.max_events), dtype=torch.int32, device=device)
+        self.n_dev, self.raw_offsets, self.trk_offsets, self.hit_src, self.trk_src = self.meta_views(self.meta)
+        self.raw = None
+        if own_raw:
+            self.raw = dict(x=e(max_hits, torch.float32), z=e(max_hits, torch.float32),
+                            dxdy=e(max_hits, torch.float32), w=e(max_hits, torch.float32),
+                            plane=e(max_hits, torch.uint8))
+        self.states = dict(sx=e(max_tracks, torch.float32), sy=e(max_tracks, torch.float32),
+                           stx=e(max_tracks, torch.float32), sty=e(max_tracks, torch.float32),
+                           sqop=e(max_tracks, torch.float32))
+        self.packed = dict(hit_offsets=e(NB * max_events + 1, torch.int32), x=e(max_hits, torch.float32),
+                           z=e(max_hits, torch.float32), dxdy=e(max_hits, torch.float32),
+                           w=e(max_hits, torch.float32), layer=e(max_hits, torch.uint8),
+                           perm=e(max_hits, torch.int32))
+        self.out = Tracker.alloc_output(self.max_tracks, self.max_events, device)
+
+    @staticmethod
+    def meta_size(max_events: int) -> int:
+        return 1 + 2 * (max_events + 1) + 2 * max(max_events, 1)
+
+    def meta_views(self, meta: torch.Tensor):
+        """(n_dev, raw_offsets, trk_offsets, hit_src, trk_src) views of a
+        block of meta_size int32 values (device, or a host staging copy)."""
+        c = self.max_events
+        a, b, d = 1 + (c + 1), 1 + 2 * (c + 1), 1 + 2 * (c + 1) + max(c, 1)
+        return meta[0:1], meta[1:a], meta[a:b], meta[b:d], meta[d:d + max(c, 1)]
+
+    def structs(self, pool=None):
+        src = pool if pool is not None else SimpleRaw(self.raw)
+        raw = lf_raw_hits(self.max_events, self.max_hits, _ptr(self.raw_offsets), _ptr(src.x), _ptr(src.z),
+                          _ptr(src.dxdy), _ptr(src.w), _ptr(src.plane))
+        pk = self.packed
+        packed = lf_packed(_ptr(pk["hit_offsets"]), _ptr(pk["x"]), _ptr(pk["z"]), _ptr(pk["dxdy"]), _ptr(pk["w"]),
+                           _ptr(pk["layer"]), _ptr(pk["perm"]))
+        st = self.states
+        b = lf_batch(self.max_events, self.max_hits, self.max_tracks, _ptr(pk["hit_offsets"]), _ptr(pk["x"]),
+                     _ptr(pk["z"]), _ptr(pk["dxdy"]), _ptr(pk["w"]), _ptr(self.trk_offsets), _ptr(st["sx"]),
+                     _ptr(st["sy"]), _ptr(st["stx"]), _ptr(st["sty"]), _ptr(st["sqop"]))
+        return raw, packed, b, Tracker.output_struct(self.out)
+
+
+class SimpleRaw:
+    """Attribute view of a dict of raw hit arrays."""
+
+    def __init__(self, d: dict):
+        self.__dict__.update(d)
 
 
 def numa_node_cpus() -> dict:
