@@ -315,12 +315,13 @@ typedef struct {
 } lf_host_output;
 
 /* Size the context's scratch for persistent-form batches of up to n_events
- * events and n_tracks input tracks (with this tuning; NULL for the defaults),
+ * events, n_hits hits and n_tracks input tracks (with this tuning; NULL for
+ * the defaults),
  * so that later calls within those sizes allocate nothing.  Growing scratch
  * inside a call frees and reallocates device memory, and cudaFree
  * synchronises the whole device, so a serving loop reserves once at start.
  * LF_ERR_OOM when the allocation fails. */
-lf_status lf_reserve(lf_ctx* ctx, int32_t n_events, int32_t n_tracks, const lf_tuning* tuning);
+lf_status lf_reserve(lf_ctx* ctx, int32_t n_events, int32_t n_hits, int32_t n_tracks, const lf_tuning* tuning);
 
 /* Page-locked host memory of exactly `bytes` bytes (cudaHostAlloc, portable
  * across devices) for the host-side buffers of lf_process_host and of a

@@ -42,7 +42,7 @@ struct lf_ctx {
     int* cursor = nullptr;   // device work-queue cursors (8 ints)
     unsigned long long generation = 0;  // bumped whenever scratch is reallocated
     int stage_bps[4] = {0, 0, 0, 0};
-    DevBuf trk_event, wbeg, wcnt, keys, ntrip, cands, ev_count;
+    DevBuf trk_event, wbeg, wcnt, keys, ntrip, cands, ev_count, coarse;
     struct GraphEntry {
         cudaGraphExec_t exec = nullptr;
         unsigned long long used = 0;   // last use (graph_clock), for eviction
@@ -229,6 +229,7 @@ KBatch to_kbatch(const lf_batch* b) {
     k.sty = b->sty;
     k.sqop = b->sqop;
     k.n_dev = nullptr;
+    k.x_coarse = nullptr;
     return k;
 }
 
@@ -269,11 +270,14 @@ lf_status plain_stages(lf_ctx* c, const lf_batch* b, cudaStream_t s) {
     if ((st = ensure(c, c->wcnt, nt * ns * NL)) != LF_OK) return st;
     if ((st = ensure(c, c->keys, nt * NT * 8)) != LF_OK) return st;
     if ((st = ensure(c, c->ntrip, nt)) != LF_OK) return st;
+    if ((st = ensure(c, c->coarse, coarse_count(b->n_hits) * 4)) != LF_OK) return st;
     KBatch kb = to_kbatch(b);
+    kb.x_coarse = (const float*)c->coarse.p;
     auto* te = (int*)c->trk_event.p;
     auto* wb = (int*)c->wbeg.p;
     auto* wc = (uint8_t*)c->wcnt.p;
     LF_CUDA(c, launch_track_event(kb, te, s));
+    LF_CUDA(c, launch_coarse(kb, (float*)c->coarse.p, c->n_sm, s));
     LF_CUDA(c, launch_windows(c->kp, kb, te, wb, wc, s));
     LF_CUDA(c, launch_triplets(c->kp, kb, te, wb, wc, (uint64_t*)c->keys.p, (uint8_t*)c->ntrip.p, s));
     return LF_OK;
@@ -327,7 +331,7 @@ void lf_destroy(lf_ctx* c) {
     if (c->host_pin) cudaFreeHost(c->host_pin);
     for (auto& kv : c->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-    DevBuf* bufs[] = {&c->trk_event, &c->wbeg, &c->wcnt, &c->keys, &c->ntrip,
+    DevBuf* bufs[] = {&c->trk_event, &c->wbeg, &c->wcnt, &c->keys, &c->ntrip, &c->coarse,
                       &c->cands, &c->ev_count};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
@@ -432,6 +436,7 @@ lf_status resolve_shape(lf_ctx* c, const lf_tuning* tuning, Shape& sh) {
 lf_status prepare_batched(lf_ctx* c, const lf_batch* b, const Shape& sh) {
     lf_status st;
     if ((st = ensure(c, c->ev_count, (size_t)b->n_events * 4)) != LF_OK) return st;
+    if ((st = ensure(c, c->coarse, coarse_count(b->n_hits) * 4)) != LF_OK) return st;
     if (sh.queue == Q_STAGES) {
         const size_t nt = (size_t)b->n_tracks, NT = (size_t)(c->p.n_triplets > 0 ? c->p.n_triplets : 1);
         const size_t ns = c->p.no_ut ? 2 : 1;
@@ -456,9 +461,11 @@ lf_status launch_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const
                          const int* n_dev = nullptr) {
     KBatch kb = to_kbatch(b);
     kb.n_dev = n_dev;
+    kb.x_coarse = (const float*)c->coarse.p;
     KOut ko = to_kout(o);
     LF_CUDA(c, cudaMemsetAsync(c->cursor, 0, 8 * sizeof(int), s));
     if (b->n_tracks > 0) {
+        LF_CUDA(c, launch_coarse(kb, (float*)c->coarse.p, c->n_sm, s));
         if (sh.queue == Q_STAGES) {
             auto* te = (int*)c->trk_event.p;
             auto* wb = (int*)c->wbeg.p;
@@ -662,13 +669,13 @@ lf_status lf_sync_status(lf_ctx* c, void* stream, int32_t* flags) {
     return LF_OK;
 }
 
-lf_status lf_reserve(lf_ctx* c, int32_t n_events, int32_t n_tracks, const lf_tuning* tuning) {
+lf_status lf_reserve(lf_ctx* c, int32_t n_events, int32_t n_hits, int32_t n_tracks, const lf_tuning* tuning) {
     if (!c) return LF_ERR_ARG;
-    if (n_events < 0 || n_tracks < 0) return fail(c, LF_ERR_ARG, "negative size");
+    if (n_events < 0 || n_hits < 0 || n_tracks < 0) return fail(c, LF_ERR_ARG, "negative size");
     Shape sh;
     lf_status st;
     if ((st = resolve_shape(c, tuning, sh)) != LF_OK) return st;
-    lf_batch big{n_events, 0, n_tracks, nullptr, nullptr, nullptr, nullptr, nullptr,
+    lf_batch big{n_events, n_hits, n_tracks, nullptr, nullptr, nullptr, nullptr, nullptr,
                  nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     return prepare_batched(c, &big, sh);
 }

@@ -59,6 +59,9 @@ struct KBatch {
     // slot form: the batch's event count in device memory; n_events and
     // n_tracks above are then the slot's capacities (nullptr otherwise)
     const int* n_dev;
+    // every 32nd packed x (x_coarse[i] = x[32 i]), written by k_coarse for
+    // the window searches (nullptr: plain binary searches)
+    const float* x_coarse;
 };
 
 // Sizes of a slot batch, read when the kernel runs: the event count from
@@ -149,6 +152,9 @@ cudaError_t launch_gather_states(const KBatch& b, const int* trk_src, const floa
                                  const float* stx, const float* sty, const float* sqop, int n_sm, cudaStream_t s);
 
 cudaError_t launch_track_event(const KBatch& b, int* trk_event, cudaStream_t s);
+// x_coarse[i] = x[32 i] for 32 i < n_hits (slot form: up to the batch's hits)
+cudaError_t launch_coarse(const KBatch& b, float* x_coarse, int n_sm, cudaStream_t s);
+inline size_t coarse_count(int n_hits) { return ((size_t)n_hits + 31) / 32 + 1; }
 // stage kernels: cursor == nullptr launches the plain one-pass grid,
 // otherwise a persistent grid of `blocks` blocks draining the stage's queue
 cudaError_t launch_windows(const KParams& k, const KBatch& b, const int* trk_event, int* wbeg, uint8_t* wcnt,

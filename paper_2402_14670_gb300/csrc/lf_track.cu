@@ -79,6 +79,36 @@ __device__ __forceinline__ void bound2_global(const float* __restrict__ x, int& 
         }
     }
 }
+// The same two searches through the coarse index c (c[i] = x[32 i]): first
+// over the coarse entries inside each range (a few neighbouring words, so
+// after the first load mostly L1 hits), which leaves at most 32 candidates,
+// then over those (one or two cache lines).  Same results as bound2_global:
+// the first coarse entry not left of v brackets the answer from above and
+// the entry before it from below.
+__device__ __forceinline__ void bound2_coarse(const float* __restrict__ x, const float* __restrict__ c, int& lo0,
+                                              int hi0, float v0, int& lo1, int hi1, float v1, bool upper) {
+    // coarse entries with lo <= 32 i < hi
+    int a0 = (lo0 + 31) >> 5, b0 = (hi0 + 31) >> 5, a1 = (lo1 + 31) >> 5, b1 = (hi1 + 31) >> 5;
+    const int s0 = a0, s1 = a1;
+    if (lo0 >= hi0) b0 = a0;
+    if (lo1 >= hi1) b1 = a1;
+    bound2_global(c, a0, b0, v0, a1, b1, v1, upper);
+    // a = first coarse index (in range) not left of v: the answer is in
+    // (32 (a - 1), 32 a] within [lo, hi)
+    int h0 = hi0, h1 = hi1;
+    if (a0 > s0) lo0 = 32 * (a0 - 1) + 1;
+    if (32 * a0 < hi0 && a0 < ((hi0 + 31) >> 5)) h0 = 32 * a0;
+    if (a1 > s1) lo1 = 32 * (a1 - 1) + 1;
+    if (32 * a1 < hi1 && a1 < ((hi1 + 31) >> 5)) h1 = 32 * a1;
+    bound2_global(x, lo0, h0, v0, lo1, h1, v1, upper);
+}
+// one search through the coarse index
+__device__ __forceinline__ int bound_coarse(const float* __restrict__ x, const float* __restrict__ c, int lo, int hi,
+                                            float v, bool upper) {
+    int lo1 = 0;
+    bound2_coarse(x, c, lo, hi, v, lo1, 0, 0.0f, upper);
+    return lo;
+}
 // first index in [0, n) of a window in shared memory with x >= v
 __device__ __forceinline__ int lb_smem(const float* x, int n, float v) {
     int lo = 0, hi = n;
@@ -164,7 +194,9 @@ __device__ __forceinline__ void warp_windows(const KParams& k, const KBatch& b, 
     const int* off = b.hit_offsets + (size_t)e * NB + zone * NL + l;
     const int bb = __ldg(off), be = __ldg(off + 1);
     int v = 0;
-    if (lane < 2 * NL) v = bound_global(b.x, bb, be, lane < NL ? xmin : xmax, lane >= NL);
+    if (lane < 2 * NL)
+        v = b.x_coarse ? bound_coarse(b.x, b.x_coarse, bb, be, lane < NL ? xmin : xmax, lane >= NL)
+                       : bound_global(b.x, bb, be, lane < NL ? xmin : xmax, lane >= NL);
     int hi = __shfl_sync(FULL, v, (lane + NL) & 31);
     begin = 0;
     count = 0;
@@ -173,7 +205,8 @@ __device__ __forceinline__ void warp_windows(const KParams& k, const KBatch& b, 
         if (hi < lo) hi = lo;
         int cnt = hi - lo, start = lo;
         if (cnt > k.cap) {
-            int c = bound_global(b.x, lo, hi, centre, false);
+            int c = b.x_coarse ? bound_coarse(b.x, b.x_coarse, lo, hi, centre, false)
+                               : bound_global(b.x, lo, hi, centre, false);
             start = c - k.cap / 2;
             if (start > hi - k.cap) start = hi - k.cap;
             if (start < lo) start = lo;
@@ -731,7 +764,8 @@ __device__ __forceinline__ void windows_track2(const KParams& k, const KBatch& b
         v1 = has1 ? __ldg(off1) : 0;
         const int h0 = __ldg(off0 + 1), h1 = has1 ? __ldg(off1 + 1) : 0;
         const bool up = lane >= NL;
-        bound2_global(b.x, v0, h0, up ? xmax0 : xmin0, v1, h1, up ? xmax1 : xmin1, up);
+        if (b.x_coarse) bound2_coarse(b.x, b.x_coarse, v0, h0, up ? xmax0 : xmin0, v1, h1, up ? xmax1 : xmin1, up);
+        else bound2_global(b.x, v0, h0, up ? xmax0 : xmin0, v1, h1, up ? xmax1 : xmin1, up);
     }
     int hi0 = __shfl_sync(FULL, v0, (lane + NL) & 31), hi1 = __shfl_sync(FULL, v1, (lane + NL) & 31);
     if (lane < NL) {
@@ -741,7 +775,8 @@ __device__ __forceinline__ void windows_track2(const KParams& k, const KBatch& b
         // the capped windows' centre searches, together
         int cc0 = lo0, cc1 = lo1;
         const bool cap0 = hi0 - lo0 > k.cap, cap1 = has1 && hi1 - lo1 > k.cap;
-        bound2_global(b.x, cc0, cap0 ? hi0 : lo0, c0, cc1, cap1 ? hi1 : lo1, c1, false);
+        if (b.x_coarse) bound2_coarse(b.x, b.x_coarse, cc0, cap0 ? hi0 : lo0, c0, cc1, cap1 ? hi1 : lo1, c1, false);
+        else bound2_global(b.x, cc0, cap0 ? hi0 : lo0, c0, cc1, cap1 ? hi1 : lo1, c1, false);
         int st0 = lo0, n0 = hi0 - lo0, st1 = lo1, n1 = hi1 - lo1;
         if (cap0) {
             st0 = cc0 - k.cap / 2;
@@ -1275,6 +1310,19 @@ __global__ void k_compact_scatter(const int* __restrict__ trk_offsets, const uin
     }
 }
 
+// Coarse index of the packed x: every 32nd value (slot form: up to the
+// batch's last hit).
+__global__ void k_coarse(KBatch b, float* __restrict__ c) {
+    int n_hits = b.n_hits;
+    if (b.n_dev) {
+        slot_sizes(b);
+        const int h = b.hit_offsets[(size_t)b.n_events * NB];
+        n_hits = h < 0 ? 0 : (h < n_hits ? h : n_hits);
+    }
+    const int n = (n_hits + 31) >> 5;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) c[i] = __ldg(b.x + 32 * (size_t)i);
+}
+
 // Slot form with a gather source: the input states of batch event e's
 // tracks are copied from the source arrays, starting at trk_src[e], to the
 // batch's own state arrays (warp per event, lanes over its tracks).
@@ -1484,6 +1532,14 @@ cudaError_t launch_compact(const int* trk_offsets, const uint8_t* found, int n_e
         k_compact_scatter<<<cdiv((long)n_events * 32, 256), 256, 0, s>>>(trk_offsets, found, n_events, out_offsets,
                                                                          out_trk, n_dev);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse(const KBatch& b, float* x_coarse, int n_sm, cudaStream_t s) {
+    if (b.n_hits <= 0) return cudaSuccess;
+    const int want = cdiv(((long)b.n_hits + 31) / 32, 256);
+    const int grid = want < 16 * n_sm ? want : 16 * n_sm;
+    k_coarse<<<grid, 256, 0, s>>>(b, x_coarse);
     return cudaGetLastError();
 }
 

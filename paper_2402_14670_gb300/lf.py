@@ -133,7 +133,7 @@ _lib.lf_graph_count.restype = C.c_int64
 _lib.lf_find_tracks_static.argtypes = [C.POINTER(lf_geometry), C.POINTER(lf_params), C.POINTER(lf_batch),
                                        C.POINTER(lf_output), _P]
 _lib.lf_find_tracks_static.restype = C.c_int
-_lib.lf_reserve.argtypes = [_P, C.c_int32, C.c_int32, C.POINTER(lf_tuning)]
+_lib.lf_reserve.argtypes = [_P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(lf_tuning)]
 _lib.lf_reserve.restype = C.c_int
 _lib.lf_host_alloc.argtypes = [C.c_size_t, C.POINTER(_P)]
 _lib.lf_host_alloc.restype = C.c_int
@@ -264,8 +264,9 @@ def lf_device_host_numa() -> int:
     return int(_lib.lf_device_host_numa())
 
 
-def lf_reserve(ctx, n_events: int, n_tracks: int, tuning: Optional["lf_tuning"] = None) -> None:
-    _check(ctx, _lib.lf_reserve(ctx, int(n_events), int(n_tracks), C.byref(tuning) if tuning else None))
+def lf_reserve(ctx, n_events: int, n_hits: int, n_tracks: int, tuning: Optional["lf_tuning"] = None) -> None:
+    _check(ctx, _lib.lf_reserve(ctx, int(n_events), int(n_hits), int(n_tracks),
+                                C.byref(tuning) if tuning else None))
 
 
 def lf_host_alloc(nbytes: int) -> int:
@@ -477,10 +478,10 @@ class Tracker:
     def status(self, stream=None) -> int:
         return lf_sync_status(self.ctx, _stream(stream))
 
-    def reserve(self, n_events: int, n_tracks: int, tuning: Optional[dict] = None) -> None:
+    def reserve(self, n_events: int, n_hits: int, n_tracks: int, tuning: Optional[dict] = None) -> None:
         """Size the persistent form's scratch for batches up to these sizes."""
         tu = tuning_struct(tuning)
-        lf_reserve(self.ctx, n_events, n_tracks, tu)
+        lf_reserve(self.ctx, n_events, n_hits, n_tracks, tu)
 
     @staticmethod
     def _hptr(t: torch.Tensor):

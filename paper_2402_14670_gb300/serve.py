@@ -90,7 +90,7 @@ class _Slot:
         self.tr = lf.Tracker(geometry, params)
         # scratch sized once: growing it mid-stream would free device memory,
         # which synchronises the device
-        self.tr.reserve(max_events, max_tracks)
+        self.tr.reserve(max_events, max_hits, max_tracks)
         self.buf = lf.SlotBuffers(max_events, max_hits, max_tracks, dev, own_raw=False)
         p = lambda n, dt: torch.empty(n, dtype=dt, pin_memory=True)
         self.h_meta = p(self.buf.meta.numel(), torch.int32)
