@@ -672,9 +672,10 @@ def main():
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "error": str(e)}
 
     # pack: one persistent kernel (k_pack_event); find (default queue mode):
-    # track->event map, three persistent stage kernels (windows, triplets,
-    # extension with the selection), three compaction kernels
-    launches_per_step = 1 + (1 + 3) + 3
+    # track->event map, the coarse index of x, three persistent stage kernels
+    # (windows, triplets, extension with the selection), three compaction
+    # kernels
+    launches_per_step = 1 + (1 + 1 + 3) + 3
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
