@@ -223,12 +223,14 @@ def sub_batches(batch, size: int):
 def per_batch_plain(tr, batch, packed, out, size: int):
     """Closure running the plain form per `size`-event batch (pack + one
     launch per stage per batch) over the whole workload."""
+    from paper_2402_14670_gb300 import lf
     subs = sub_batches(batch, size)
     dev = batch.x.device
     plans = []
     for sub, h0, h1, t0, t1 in subs:
         pk = {k: packed[k][h0:h1] for k in ("x", "z", "dxdy", "w", "layer", "perm")}
         pk["hit_offsets"] = torch.empty(24 * sub.n_events + 1, dtype=torch.int32, device=dev)
+        pk["x_coarse"] = torch.empty(lf.coarse_count(h1 - h0), dtype=torch.float32, device=dev)
         ot = {k: out[k][t0:t1] for k in ("found", "nhits", "hit_idx", "state", "quality")}
         ot["out_offsets"] = torch.empty(sub.n_events + 1, dtype=torch.int32, device=dev)
         ot["out_trk"] = out["out_trk"][t0:t1] if t1 > t0 else out["out_trk"][:1]
@@ -671,11 +673,11 @@ def main():
         except Exception as e:  # the oracle is test infrastructure; report why it did not run
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "error": str(e)}
 
-    # pack: one persistent kernel (k_pack_event); find (default queue mode):
-    # track->event map, the coarse index of x, three persistent stage kernels
-    # (windows, triplets, extension with the selection), three compaction
-    # kernels
-    launches_per_step = 1 + (1 + 1 + 3) + 3
+    # pack: one persistent kernel (k_pack_event, which also writes the coarse
+    # index of x); find (default queue mode): track->event map, three
+    # persistent stage kernels (windows, triplets, extension with the
+    # selection), three compaction kernels
+    launches_per_step = 1 + (1 + 3) + 3
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

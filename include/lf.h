@@ -150,6 +150,8 @@ typedef struct {
     float* x; float* z; float* dxdy; float* w;   /* [n_hits] */
     uint8_t* layer;            /* [n_hits] */
     int32_t* perm;             /* [n_hits] packed index -> raw index */
+    float* x_coarse;           /* optional [(n_hits+31)/32]: x_coarse[i] = x[32 i], the index the
+                                  window searches use (NULL: not written) */
 } lf_packed;
 
 /* Input of the track finding: packed hits plus input states (device). */
@@ -161,6 +163,8 @@ typedef struct {
     const float* x; const float* z; const float* dxdy; const float* w;
     const int32_t* trk_offsets;/* [n_events+1] */
     const float* sx; const float* sy; const float* stx; const float* sty; const float* sqop;
+    const float* x_coarse;     /* optional: the packed x_coarse (NULL: the find computes it in
+                                  context scratch, reading x once more) */
 } lf_batch;
 
 /* Output per input track t (device, caller-allocated).

@@ -229,7 +229,7 @@ KBatch to_kbatch(const lf_batch* b) {
     k.sty = b->sty;
     k.sqop = b->sqop;
     k.n_dev = nullptr;
-    k.x_coarse = nullptr;
+    k.x_coarse = b->x_coarse;
     return k;
 }
 
@@ -270,14 +270,16 @@ lf_status plain_stages(lf_ctx* c, const lf_batch* b, cudaStream_t s) {
     if ((st = ensure(c, c->wcnt, nt * ns * NL)) != LF_OK) return st;
     if ((st = ensure(c, c->keys, nt * NT * 8)) != LF_OK) return st;
     if ((st = ensure(c, c->ntrip, nt)) != LF_OK) return st;
-    if ((st = ensure(c, c->coarse, coarse_count(b->n_hits) * 4)) != LF_OK) return st;
+    if (!b->x_coarse && (st = ensure(c, c->coarse, coarse_count(b->n_hits) * 4)) != LF_OK) return st;
     KBatch kb = to_kbatch(b);
-    kb.x_coarse = (const float*)c->coarse.p;
     auto* te = (int*)c->trk_event.p;
     auto* wb = (int*)c->wbeg.p;
     auto* wc = (uint8_t*)c->wcnt.p;
     LF_CUDA(c, launch_track_event(kb, te, s));
-    LF_CUDA(c, launch_coarse(kb, (float*)c->coarse.p, c->n_sm, s));
+    if (!b->x_coarse) {
+        kb.x_coarse = (const float*)c->coarse.p;
+        LF_CUDA(c, launch_coarse(kb, (float*)c->coarse.p, c->n_sm, s));
+    }
     LF_CUDA(c, launch_windows(c->kp, kb, te, wb, wc, s));
     LF_CUDA(c, launch_triplets(c->kp, kb, te, wb, wc, (uint64_t*)c->keys.p, (uint8_t*)c->ntrip.p, s));
     return LF_OK;
@@ -372,7 +374,7 @@ lf_status lf_pack_hits(lf_ctx* c, const lf_raw_hits* raw, const lf_packed* pk, v
     // stages use the first ones; calls of one context are stream-ordered)
     LF_CUDA(c, launch_pack(raw->raw_offsets, raw->x, raw->z, raw->dxdy, raw->w, raw->plane, raw->n_events,
                            raw->n_hits, pk->hit_offsets, pk->x, pk->z, pk->dxdy, pk->w, pk->layer, pk->perm, c->cursor + 6,
-                           c->status, c->n_sm, s));
+                           c->status, c->n_sm, s, nullptr, nullptr, pk->x_coarse));
     return LF_OK;
 }
 
@@ -436,7 +438,7 @@ lf_status resolve_shape(lf_ctx* c, const lf_tuning* tuning, Shape& sh) {
 lf_status prepare_batched(lf_ctx* c, const lf_batch* b, const Shape& sh) {
     lf_status st;
     if ((st = ensure(c, c->ev_count, (size_t)b->n_events * 4)) != LF_OK) return st;
-    if ((st = ensure(c, c->coarse, coarse_count(b->n_hits) * 4)) != LF_OK) return st;
+    if (!b->x_coarse && (st = ensure(c, c->coarse, coarse_count(b->n_hits) * 4)) != LF_OK) return st;
     if (sh.queue == Q_STAGES) {
         const size_t nt = (size_t)b->n_tracks, NT = (size_t)(c->p.n_triplets > 0 ? c->p.n_triplets : 1);
         const size_t ns = c->p.no_ut ? 2 : 1;
@@ -461,11 +463,13 @@ lf_status launch_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const
                          const int* n_dev = nullptr) {
     KBatch kb = to_kbatch(b);
     kb.n_dev = n_dev;
-    kb.x_coarse = (const float*)c->coarse.p;
     KOut ko = to_kout(o);
     LF_CUDA(c, cudaMemsetAsync(c->cursor, 0, 8 * sizeof(int), s));
     if (b->n_tracks > 0) {
-        LF_CUDA(c, launch_coarse(kb, (float*)c->coarse.p, c->n_sm, s));
+        if (!b->x_coarse) {
+            kb.x_coarse = (const float*)c->coarse.p;
+            LF_CUDA(c, launch_coarse(kb, (float*)c->coarse.p, c->n_sm, s));
+        }
         if (sh.queue == Q_STAGES) {
             auto* te = (int*)c->trk_event.p;
             auto* wb = (int*)c->wbeg.p;
@@ -552,7 +556,8 @@ void key_batch(GraphKey& key, size_t& i, const lf_batch* b, const lf_output* o) 
                            (uintptr_t)b->w, (uintptr_t)b->trk_offsets, (uintptr_t)b->sx, (uintptr_t)b->sy,
                            (uintptr_t)b->stx, (uintptr_t)b->sty, (uintptr_t)b->sqop, (uintptr_t)o->found,
                            (uintptr_t)o->nhits, (uintptr_t)o->hit_idx, (uintptr_t)o->state, (uintptr_t)o->quality,
-                           (uintptr_t)o->out_offsets, (uintptr_t)o->out_trk, (uintptr_t)o->n_out};
+                           (uintptr_t)o->out_offsets, (uintptr_t)o->out_trk, (uintptr_t)o->n_out,
+                           (uintptr_t)b->x_coarse};
     for (uintptr_t x : w) key.v[i++] = x;
 }
 
@@ -602,7 +607,8 @@ lf_status lf_process_slot(lf_ctx* c, const lf_raw_hits* raw, const lf_packed* pk
         return fail(c, LF_ERR_ARG, "raw and batch capacities differ");
     if (!raw->raw_offsets || !raw->x || !raw->z || !raw->dxdy || !raw->w || !raw->plane || !pk->layer || !pk->perm)
         return fail(c, LF_ERR_ARG, "a raw or packed array is NULL");
-    if (b->hit_offsets != pk->hit_offsets || b->x != pk->x || b->z != pk->z || b->dxdy != pk->dxdy || b->w != pk->w)
+    if (b->hit_offsets != pk->hit_offsets || b->x != pk->x || b->z != pk->z || b->dxdy != pk->dxdy || b->w != pk->w ||
+        b->x_coarse != pk->x_coarse)
         return fail(c, LF_ERR_ARG, "the batch's hit arrays are not the packed arrays");
     if (g && (!g->hit_src || !g->trk_src || !g->sx || !g->sy || !g->stx || !g->sty || !g->sqop))
         return fail(c, LF_ERR_ARG, "a gather array is NULL");
@@ -630,7 +636,8 @@ lf_status lf_process_slot(lf_ctx* c, const lf_raw_hits* raw, const lf_packed* pk
         }
         LF_CUDA(c, launch_pack(raw->raw_offsets, raw->x, raw->z, raw->dxdy, raw->w, raw->plane, raw->n_events,
                                raw->n_hits, pk->hit_offsets, pk->x, pk->z, pk->dxdy, pk->w, pk->layer, pk->perm,
-                               c->cursor + 6, c->status, c->n_sm, cs, n_events_dev, g ? g->hit_src : nullptr));
+                               c->cursor + 6, c->status, c->n_sm, cs, n_events_dev, g ? g->hit_src : nullptr,
+                               pk->x_coarse));
         return launch_batched(c, b, o, sh, cs, n_events_dev);
     });
 }
@@ -790,6 +797,7 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
     size_t o_pw = sz; sz += al(4 * H);
     size_t o_pl2 = sz; sz += al(H);
     size_t o_pm = sz; sz += al(4 * H);
+    size_t o_pc = sz; sz += al(4 * coarse_count((int)H));
     size_t o_fd = sz; sz += al(T);
     size_t o_nh = sz; sz += al(T);
     size_t o_hi = sz; sz += al(4 * NL * T);
@@ -835,11 +843,11 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
         lf_raw_hits raw{ne, nh, (const int32_t*)(A + o_ro), (const float*)(A + o_x), (const float*)(A + o_z),
                         (const float*)(A + o_d), (const float*)(A + o_w), (const uint8_t*)(A + o_pl)};
         lf_packed pk{(int32_t*)(A + o_ho), (float*)(A + o_px), (float*)(A + o_pz), (float*)(A + o_pd),
-                     (float*)(A + o_pw), (uint8_t*)(A + o_pl2), (int32_t*)(A + o_pm)};
+                     (float*)(A + o_pw), (uint8_t*)(A + o_pl2), (int32_t*)(A + o_pm), (float*)(A + o_pc)};
         if ((rc = lf_pack_hits(sc, &raw, &pk, s_comp)) != LF_OK) break;
         lf_batch bt{ne, nh, nt, pk.hit_offsets, pk.x, pk.z, pk.dxdy, pk.w, (const int32_t*)(A + o_to),
                     (const float*)(A + o_st), (const float*)(A + o_st + 4 * T), (const float*)(A + o_st + 8 * T),
-                    (const float*)(A + o_st + 12 * T), (const float*)(A + o_st + 16 * T)};
+                    (const float*)(A + o_st + 12 * T), (const float*)(A + o_st + 16 * T), pk.x_coarse};
         lf_output out{(uint8_t*)(A + o_fd), (uint8_t*)(A + o_nh), (int32_t*)(A + o_hi), (float*)(A + o_sv),
                       (float*)(A + o_q), (int32_t*)(A + o_oo), (int32_t*)(A + o_ot), (int32_t*)(A + o_no)};
         if ((rc = batched_direct(sc, &bt, &out, sh, s_comp)) != LF_OK) break;

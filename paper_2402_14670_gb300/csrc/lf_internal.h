@@ -145,7 +145,7 @@ cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, 
                         const float* w, const uint8_t* plane, int n_events, int n_hits, int* hit_offsets,
                         float* ox, float* oz, float* odxdy, float* ow, uint8_t* olayer, int* perm, int* cursor,
                         int* status, int n_sm, cudaStream_t s, const int* n_dev = nullptr,
-                        const int* hit_src = nullptr);
+                        const int* hit_src = nullptr, float* ocoarse = nullptr);
 // slot form with a gather source: the states of batch event e's tracks are
 // copied from src (starting at trk_src[e]) to the batch's state arrays
 cudaError_t launch_gather_states(const KBatch& b, const int* trk_src, const float* sx, const float* sy,

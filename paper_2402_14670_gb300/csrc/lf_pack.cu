@@ -20,7 +20,8 @@
 //   order    each bin is ordered by (x, raw index) with an insertion sort, so
 //            the result is the exact (bucket, x, raw index) order whatever
 //            the data (a skewed x distribution costs time, never exactness);
-//   write    x, layer and perm leave coalesced.
+//   write    x, layer and perm leave coalesced (and, when asked for, every
+//            32nd x into the coarse index of the window searches).
 // An event of at most CHUNK_N hits is placed straight into shared memory as
 // (x, 16-bit raw index), 6 bytes per hit; its z, dxdy and w are then copied
 // from the raw arrays (prefetched into L2 when the event was taken) into
@@ -275,6 +276,7 @@ struct PackIO {
     uint8_t* ol;
     int* perm;
     int* status;
+    float* oc;   // coarse index: oc[p / 32] = x of output position p, p a multiple of 32 (or nullptr)
 };
 
 // Sort one event of n >= 1 hits starting at raw index rb (event e).
@@ -423,6 +425,7 @@ __device__ __forceinline__ void sort_event(const PackIO& io, EvShared& sh, char*
         for (int j = tid; j < n; j += PACK_THREADS) {
             while (qb + 1 < NB && sh.boff[qb + 1] <= j) ++qb;
             io.ox[o0 + j] = xs[j];
+            if (io.oc && ((o0 + j) & 31) == 0) io.oc[(o0 + j) >> 5] = xs[j];
             io.ol[o0 + j] = (uint8_t)(qb % NL);
             io.perm[o0 + j] = rb + (int)ks[j];
         }
@@ -461,6 +464,7 @@ __device__ __forceinline__ void sort_event(const PackIO& io, EvShared& sh, char*
                 const size_t o = (size_t)rb + j;
                 io.perm[o] = -1;
                 io.ox[o] = 0.0f;
+                if (io.oc && (o & 31) == 0) io.oc[o >> 5] = 0.0f;
                 io.oz[o] = 0.0f;
                 io.od[o] = 0.0f;
                 io.ow[o] = 0.0f;
@@ -526,6 +530,7 @@ __device__ __forceinline__ void sort_event(const PackIO& io, EvShared& sh, char*
         for (int j = tid; j < tot; j += PACK_THREADS) {
             while (qb + 1 < NB && sh.boff[qb + 1] <= base + j) ++qb;
             io.ox[o0 + j] = xs[j];
+            if (io.oc && ((o0 + j) & 31) == 0) io.oc[(o0 + j) >> 5] = xs[j];
             io.ol[o0 + j] = (uint8_t)(qb % NL);
             io.perm[o0 + j] = rb + (int)ks[j];
         }
@@ -591,7 +596,7 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
     const int* __restrict__ raw_offsets, const float* __restrict__ x, const float* __restrict__ z,
     const float* __restrict__ dxdy, const float* __restrict__ w, const uint8_t* __restrict__ plane, int n_events,
     int* hit_offsets, float* ox, float* oz, float* od, float* ow, uint8_t* ol, int* perm, int* cursor,
-    int* status, const int* __restrict__ n_dev, const int* __restrict__ hit_src) {
+    int* status, const int* __restrict__ n_dev, const int* __restrict__ hit_src, float* ocoarse) {
     extern __shared__ __align__(16) char smem[];
     __shared__ EvShared sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -641,7 +646,8 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
         }
         // input pointers shifted so that raw index rb + i reads input ib + i
         const ptrdiff_t d = (ptrdiff_t)ib - rb;
-        const PackIO io{x + d, z + d, dxdy + d, w + d, plane + d, hit_offsets, ox, oz, od, ow, ol, perm, status};
+        const PackIO io{x + d, z + d, dxdy + d, w + d, plane + d, hit_offsets, ox, oz, od, ow, ol, perm, status,
+                        ocoarse};
         if (n > 65535) sort_event<true>(io, sh, smem, e, rb, n, tid, lane, warp);
         else sort_event<false>(io, sh, smem, e, rb, n, tid, lane, warp);
     }
@@ -652,7 +658,7 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) k_pack_event(
 cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, const float* dxdy, const float* w,
                         const uint8_t* plane, int n_events, int n_hits, int* hit_offsets, float* ox, float* oz,
                         float* odxdy, float* ow, uint8_t* olayer, int* perm, int* cursor, int* status, int n_sm,
-                        cudaStream_t s, const int* n_dev, const int* hit_src) {
+                        cudaStream_t s, const int* n_dev, const int* hit_src, float* ocoarse) {
     (void)n_hits;
     cudaError_t err =
         cudaFuncSetAttribute(k_pack_event, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AREA_BYTES);
@@ -662,7 +668,7 @@ cudaError_t launch_pack(const int* raw_offsets, const float* x, const float* z, 
     if (grid > n_events) grid = n_events > 0 ? n_events : 1;
     k_pack_event<<<grid, PACK_THREADS, AREA_BYTES, s>>>(raw_offsets, x, z, dxdy, w, plane, n_events, hit_offsets,
                                                         ox, oz, odxdy, ow, olayer, perm, cursor, status, n_dev,
-                                                        hit_src);
+                                                        hit_src, ocoarse);
     return cudaGetLastError();
 }
 

@@ -86,7 +86,7 @@ extern "C" lf_status lf_find_tracks_static(const lf_geometry* geometry, const lf
     int* ev_count = scratch + kScratchHead;
     if (cudaMemsetAsync(cursor, 0, sizeof(int), s) != cudaSuccess) return LF_ERR_CUDA;
     lfk::KBatch kb{b->n_events, b->n_hits, b->n_tracks, b->hit_offsets, b->x, b->z, b->dxdy, b->w,
-                   b->trk_offsets, b->sx, b->sy, b->stx, b->sty, b->sqop, nullptr, nullptr};
+                   b->trk_offsets, b->sx, b->sy, b->stx, b->sty, b->sqop, nullptr, b->x_coarse};
     lfk::KOut ko{o->found, o->nhits, o->hit_idx, o->state, o->quality};
     if (b->n_tracks > 0 && lfk::launch_fused(k, kb, ko, cursor, grain, wpb, bps * n_sm, s) != cudaSuccess)
         return LF_ERR_CUDA;

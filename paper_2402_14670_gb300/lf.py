@@ -60,13 +60,14 @@ class lf_raw_hits(C.Structure):
 
 
 class lf_packed(C.Structure):
-    _fields_ = [("hit_offsets", _P), ("x", _P), ("z", _P), ("dxdy", _P), ("w", _P), ("layer", _P), ("perm", _P)]
+    _fields_ = [("hit_offsets", _P), ("x", _P), ("z", _P), ("dxdy", _P), ("w", _P), ("layer", _P), ("perm", _P),
+                ("x_coarse", _P)]
 
 
 class lf_batch(C.Structure):
     _fields_ = [("n_events", C.c_int32), ("n_hits", C.c_int32), ("n_tracks", C.c_int32), ("hit_offsets", _P),
                 ("x", _P), ("z", _P), ("dxdy", _P), ("w", _P), ("trk_offsets", _P), ("sx", _P), ("sy", _P),
-                ("stx", _P), ("sty", _P), ("sqop", _P)]
+                ("stx", _P), ("sty", _P), ("sqop", _P), ("x_coarse", _P)]
 
 
 class lf_output(C.Structure):
@@ -92,6 +93,11 @@ class lf_tuning(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("grain", C.c_int32),
                 ("queue", C.c_int32), ("windows_bps", C.c_int32), ("triplets_bps", C.c_int32),
                 ("extend_bps", C.c_int32)]
+
+
+def coarse_count(n_hits: int) -> int:
+    """Length of the coarse index of n_hits packed hits (every 32nd x)."""
+    return (int(n_hits) + 31) // 32 + 1
 
 
 def tuning_struct(tuning: Optional[dict]) -> Optional[lf_tuning]:
@@ -414,11 +420,12 @@ class Tracker:
                        dxdy=torch.empty(n_h, dtype=torch.float32, device=dev),
                        w=torch.empty(n_h, dtype=torch.float32, device=dev),
                        layer=torch.empty(n_h, dtype=torch.uint8, device=dev),
-                       perm=torch.empty(n_h, dtype=torch.int32, device=dev))
+                       perm=torch.empty(n_h, dtype=torch.int32, device=dev),
+                       x_coarse=torch.empty(coarse_count(n_h), dtype=torch.float32, device=dev))
         r = lf_raw_hits(n_ev, n_h, _ptr(raw.raw_offsets), _ptr(raw.x), _ptr(raw.z), _ptr(raw.dxdy), _ptr(raw.w),
                         _ptr(raw.plane))
         p = lf_packed(_ptr(out["hit_offsets"]), _ptr(out["x"]), _ptr(out["z"]), _ptr(out["dxdy"]), _ptr(out["w"]),
-                      _ptr(out["layer"]), _ptr(out["perm"]))
+                      _ptr(out["layer"]), _ptr(out["perm"]), _ptr(out.get("x_coarse")))
         lf_pack_hits(self.ctx, r, p, _stream(stream))
         return out
 
@@ -427,7 +434,7 @@ class Tracker:
         return lf_batch(int(n_events), int(packed["x"].numel()), int(states.sx.numel()), _ptr(packed["hit_offsets"]),
                         _ptr(packed["x"]), _ptr(packed["z"]), _ptr(packed["dxdy"]), _ptr(packed["w"]),
                         _ptr(states.trk_offsets), _ptr(states.sx), _ptr(states.sy), _ptr(states.stx),
-                        _ptr(states.sty), _ptr(states.sqop))
+                        _ptr(states.sty), _ptr(states.sqop), _ptr(packed.get("x_coarse")))
 
     @staticmethod
     def alloc_output(n_tracks: int, n_events: int, device) -> dict:
@@ -560,7 +567,7 @@ class SlotBuffers:
         self.packed = dict(hit_offsets=e(NB * max_events + 1, torch.int32), x=e(max_hits, torch.float32),
                            z=e(max_hits, torch.float32), dxdy=e(max_hits, torch.float32),
                            w=e(max_hits, torch.float32), layer=e(max_hits, torch.uint8),
-                           perm=e(max_hits, torch.int32))
+                           perm=e(max_hits, torch.int32), x_coarse=e(coarse_count(max_hits), torch.float32))
         self.out = Tracker.alloc_output(self.max_tracks, self.max_events, device)
 
     @staticmethod
@@ -580,11 +587,11 @@ class SlotBuffers:
                           _ptr(src.dxdy), _ptr(src.w), _ptr(src.plane))
         pk = self.packed
         packed = lf_packed(_ptr(pk["hit_offsets"]), _ptr(pk["x"]), _ptr(pk["z"]), _ptr(pk["dxdy"]), _ptr(pk["w"]),
-                           _ptr(pk["layer"]), _ptr(pk["perm"]))
+                           _ptr(pk["layer"]), _ptr(pk["perm"]), _ptr(pk["x_coarse"]))
         st = self.states
         b = lf_batch(self.max_events, self.max_hits, self.max_tracks, _ptr(pk["hit_offsets"]), _ptr(pk["x"]),
                      _ptr(pk["z"]), _ptr(pk["dxdy"]), _ptr(pk["w"]), _ptr(self.trk_offsets), _ptr(st["sx"]),
-                     _ptr(st["sy"]), _ptr(st["stx"]), _ptr(st["sty"]), _ptr(st["sqop"]))
+                     _ptr(st["sy"]), _ptr(st["stx"]), _ptr(st["sty"]), _ptr(st["sqop"]), _ptr(pk["x_coarse"]))
         return raw, packed, b, Tracker.output_struct(self.out)
 
 

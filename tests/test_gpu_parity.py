@@ -267,6 +267,10 @@ def test_pack_paths_exact(lfm):
     assert tr.status() == 0
     ref = oracle.pack(*(t.cpu().numpy() for t in (b.raw_offsets, b.x, b.z, b.dxdy, b.w, b.plane)))
     compare_pack(packed, ref)
+    # the coarse index the pack writes for the window searches: every 32nd x
+    xs = packed["x"].cpu().numpy()
+    assert np.array_equal(packed["x_coarse"].cpu().numpy()[:(len(xs) + 31) // 32].view(np.uint32),
+                          xs[::32].view(np.uint32))
 
 
 def test_pack_single_x_bucket_bounded_time(lfm):
@@ -443,3 +447,23 @@ def test_host_arena_is_page_locked(lfm):
             ar.take(1 << 20, torch.float32)
     finally:
         ar.close()
+
+
+@pytest.mark.parametrize("mode,tuning", [("plain", None), ("batched", None), ("batched", dict(queue=1, grain=2))])
+def test_coarse_index_from_the_pack_or_the_find(lfm, mode, tuning):
+    """The window searches give the same results whether the coarse index
+    comes from the pack (lf_packed.x_coarse) or is computed by the find
+    (a batch without it), and both agree with the oracle."""
+    b = synth.generate(2, n_events=300, seed=17).to("cuda")
+    tr = _tracker(lfm)
+    packed = tr.pack(b)
+    with_idx = tr.find(packed, b, b.n_events, mode, tuning)
+    bare = {k: v for k, v in packed.items() if k != "x_coarse"}
+    without = tr.find(bare, b, b.n_events, mode, tuning)
+    torch.cuda.synchronize()
+    assert tr.status() == 0
+    for k in ("found", "nhits", "hit_idx", "quality", "out_offsets"):
+        assert torch.equal(with_idx[k], without[k]), k
+    f = with_idx["found"].bool()
+    assert torch.equal(with_idx["state"][f].view(torch.int32), without["state"][f].view(torch.int32))
+    run_both(tr, b, mode=mode, tuning=tuning)
