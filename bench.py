@@ -529,13 +529,16 @@ def main():
             tr.process_host(host, out=hout, tuning=tuning)
             steps_ms.append((time.perf_counter() - ta) * 1e3)
         e2e_s = max_over_ranks(ws, time.perf_counter() - t0) / args.steps
-        # the host link alone: one copy of the x array to the device
+        # the host link alone: copies of the x array to the device (the best
+        # of two, so that the first touch of the destination is not timed)
         dx = torch.empty(host.x.numel(), dtype=torch.float32, device="cuda")
-        torch.cuda.synchronize()
-        ta = time.perf_counter()
-        dx.copy_(host.x, non_blocking=True)
-        torch.cuda.synchronize()
-        h2d_gbps = host.x.numel() * 4 / (time.perf_counter() - ta) / 1e9
+        h2d_gbps = 0.0
+        for _ in range(2):
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            dx.copy_(host.x, non_blocking=True)
+            torch.cuda.synchronize()
+            h2d_gbps = max(h2d_gbps, host.x.numel() * 4 / (time.perf_counter() - ta) / 1e9)
         del dx
         h2d = sum(int(t.numel() * t.element_size()) for t in
                   (host.raw_offsets, host.x, host.z, host.dxdy, host.w, host.plane, host.trk_offsets,
