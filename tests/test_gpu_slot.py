@@ -154,3 +154,50 @@ def test_slot_count_clamped_to_capacity(mods, pool):
     _compare(slot, cap_ev, nh, nt, packed, out)
     tr.close()
     ref_tr.close()
+
+
+def test_slot_rejects_batch_arrays_other_than_the_packed_ones(mods, pool):
+    lf = mods
+    tr = lf.Tracker()
+    slot = lf.SlotBuffers(8, 200000, 2000, "cuda", own_raw=True)
+    raw, pk, b, o = slot.structs()
+    other = torch.empty(200000, dtype=torch.float32, device="cuda")
+    b.x = other.data_ptr()
+    with pytest.raises(lf.LFError) as ei:
+        lf.lf_process_slot(tr.ctx, raw, pk, b, None, slot.n_dev.data_ptr(), o, None, None)
+    assert ei.value.status == lf.LF_ERR_ARG
+    raw, pk, b, o = slot.structs()
+    b.n_hits = slot.max_hits - 1          # capacities of raw and batch differ
+    with pytest.raises(lf.LFError) as ei:
+        lf.lf_process_slot(tr.ctx, raw, pk, b, None, slot.n_dev.data_ptr(), o, None, None)
+    assert ei.value.status == lf.LF_ERR_ARG
+    tr.close()
+
+
+def test_graph_cache_keeps_the_most_recent_shapes(mods, pool):
+    """More launch shapes than the cache holds (64): the least recently used
+    graphs are dropped and recaptured when they come back; every replay gives
+    the direct launch's results."""
+    lf = mods
+    b = pool.select_events(range(40)).to("cuda")
+    tr = lf.Tracker()
+    packed = tr.pack(b)
+    ref = tr.find(packed, b, b.n_events, "batched")
+    torch.cuda.synchronize()
+    outs = [lf.Tracker.alloc_output(b.n_tracks, b.n_events, "cuda") for _ in range(70)]
+    g0 = tr.graph_count()
+    for rep in range(3):
+        for o in outs:                      # each output set is a launch shape of its own
+            for k in ("found", "nhits"):
+                o[k].fill_(7)
+            tr.find(packed, b, b.n_events, "batched", out=o)
+        torch.cuda.synchronize()
+        m = int(ref["n_out"].item())
+        for o in outs:
+            assert torch.equal(o["found"], ref["found"]) and int(o["n_out"].item()) == m
+            assert torch.equal(o["out_trk"][:m], ref["out_trk"][:m])
+    # first pass: launched directly (first sight); second: 70 captures, the
+    # oldest 6 dropped; third: the 6 oldest (and those they push out) again
+    n = tr.graph_count() - g0
+    assert n >= 70 and n <= 140
+    tr.close()
