@@ -194,6 +194,13 @@ typedef struct {
     int32_t windows_bps;       /* stage pipeline: resident blocks per SM of the windows, triplet and */
     int32_t triplets_bps;      /* extension kernels (0: blocks_per_sm, or as many as fit; a value   */
     int32_t extend_bps;        /* above what fits is lowered to it)                                  */
+    int32_t triplet_prefilter; /* stage pipeline, VELO-UT input: 0 (default) none; 1 the half-precision
+                                  pre-filter of the triplet pairs (Sec. "Performance", the triplet
+                                  seeding's chi2 in half2 arithmetic): every (h0, h2) pair is first
+                                  tested against all hits of its h1 window in binary16, with a margin
+                                  above binary16 rounding, and only the pairs that pass get the exact
+                                  binary32 filters, closest-hit search and chi2.  Same results as 0;
+                                  LF_ERR_ARG with queue != 0 or the no-UT variant. */
 } lf_tuning;
 
 /* Create a context: validates and copies geometry and parameters (the
@@ -388,6 +395,14 @@ lf_status lf_find_tracks_static(const lf_geometry* geometry, const lf_params* pa
  * trip_chi2 [n_tracks*n_triplets] (float).  Device pointers. */
 lf_status lf_debug_stages(lf_ctx* ctx, const lf_batch* batch, int32_t* win_begin, int32_t* win_count,
                           int32_t* n_trip, int32_t* trip, float* trip_chi2, void* stream);
+
+/* The same triplet dumps (win_count, n_trip, trip, trip_chi2 as above)
+ * decoded from what the last lf_find_tracks_batched call on the stage
+ * pipeline (lf_tuning.queue 0) left in the context's scratch, for that call's
+ * batch: no stage runs again.  For parity tests of the persistent triplet
+ * kernel's launch options.  LF_ERR_ARG when the scratch holds fewer tracks. */
+lf_status lf_debug_triplets(lf_ctx* ctx, const lf_batch* batch, int32_t* win_count, int32_t* n_trip,
+                            int32_t* trip, float* trip_chi2, void* stream);
 
 /* Synchronise the stream, read and clear the device status word.
  * Returns LF_OK, LF_ERR_CAPACITY or LF_ERR_TIMEOUT; *flags gets the bits. */

@@ -4,8 +4,8 @@ For a batch it times a small set of lf_tuning candidates with CUDA events on
 the current stream, keeps the fastest, and caches the choice per (GPU name,
 batch bucket).  The candidates are the stage pipeline's occupancy knobs (the
 resident blocks per SM of its windows, triplet and extension kernels: fewer
-blocks leave each more registers and cache, more blocks hide more latency)
-and the tile kernel.  The bucket is the event-size class of the batch (mean
+blocks leave each more registers and cache, more blocks hide more latency),
+the half-precision pre-filter of the triplet pairs and the tile kernel.  The bucket is the event-size class of the batch (mean
 input tracks per event: 1-32, 33-64, 65-128, 129-256, 257+) and its
 event-count scale (log2), the shape classes of the uneven and served
 workloads.  Every candidate gives identical results; only the launch shape
@@ -28,11 +28,20 @@ CANDIDATES = [
     dict(queue=0, extend_bps=3),
     dict(queue=0, triplets_bps=4, extend_bps=3),
     dict(queue=0, windows_bps=4, triplets_bps=4, extend_bps=3),
+    dict(queue=0, triplet_prefilter=1),                   # half-precision pre-filter of the triplet pairs
     dict(queue=1, warps_per_block=8, grain=2),            # block-synchronous tile kernel
 ]
 TRACK_EDGES = (32, 64, 128, 256)
 
 _lock = threading.Lock()
+
+
+def applicable(cand: dict, params: dict) -> bool:
+    """Whether the library accepts a candidate for these parameters: the
+    no-UT variant runs on the stage pipeline without the triplet pre-filter."""
+    if params.get("no_ut", 0):
+        return cand.get("queue", 0) == 0 and not cand.get("triplet_prefilter", 0)
+    return True
 
 
 def bucket_of(n_events: int, n_tracks: int) -> Tuple[int, int]:
@@ -68,6 +77,8 @@ class Autotuner:
             out = tracker.alloc_output(int(batch.sx.numel()), n_events, packed["x"].device)
         times = {}
         for cand in CANDIDATES:
+            if not applicable(cand, tracker.params):
+                continue
             # warm-up: a first-seen launch shape runs directly; the first timed
             # call captures its graph and the later ones replay it, so the
             # minimum over the repetitions is a replay

@@ -163,6 +163,7 @@ KParams make_kparams(const lf_geometry* g, const lf_params* p) {
     k.pk = pol * g->kappa;
     k.pg = pol * g->gamma;
     k.D = g->dratio * 1000.0f;
+    k.pf_bound = std::nextafter((float)(std::sqrt((double)p->T_triplet) + (double)PF_MARGIN), INFINITY);
     return k;
 }
 
@@ -403,6 +404,7 @@ namespace {
 struct Shape {
     int wpb, bps, grain, queue;
     int stage_bps[3];   // per-stage blocks per SM of the stage pipeline (0: bps, else as many as fit)
+    int prefilter;      // triplet pre-filter (stage pipeline)
 };
 
 // queue modes of lf_tuning
@@ -421,6 +423,10 @@ lf_status resolve_shape(lf_ctx* c, const lf_tuning* tuning, Shape& sh) {
     sh.stage_bps[2] = tuning ? tuning->extend_bps : 0;
     for (int i = 0; i < 3; ++i)
         if (sh.stage_bps[i] < 0) return fail(c, LF_ERR_ARG, "negative blocks per SM");
+    sh.prefilter = tuning ? tuning->triplet_prefilter : 0;
+    if (sh.prefilter < 0 || sh.prefilter > 1) return fail(c, LF_ERR_ARG, "triplet_prefilter %d outside 0..1", sh.prefilter);
+    if (sh.prefilter && (sh.queue != Q_STAGES || c->p.no_ut))
+        return fail(c, LF_ERR_ARG, "the triplet pre-filter runs on the stage pipeline (queue 0) with VELO-UT input");
     if (sh.queue == Q_STAGES) {
         if (!c->stage_bps[0]) LF_CUDA(c, stage_blocks_per_sm(c->kp, c->stage_bps));
         sh.bps = tuning && tuning->blocks_per_sm > 0 ? tuning->blocks_per_sm : 0;
@@ -479,7 +485,8 @@ lf_status launch_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const
             auto* cd = (CandRec*)c->cands.p;
             LF_CUDA(c, launch_track_event(kb, te, s));
             LF_CUDA(c, launch_windows(c->kp, kb, te, wb, wc, s, c->cursor + 0, stage_grid(c, sh, 0)));
-            LF_CUDA(c, launch_triplets(c->kp, kb, te, wb, wc, ky, nt, s, c->cursor + 1, stage_grid(c, sh, 1)));
+            LF_CUDA(c, launch_triplets(c->kp, kb, te, wb, wc, ky, nt, s, c->cursor + 1, stage_grid(c, sh, 1),
+                                       sh.prefilter));
             // the persistent extension selects and writes the output itself
             LF_CUDA(c, launch_extend(c->kp, kb, te, wb, wc, ky, nt, cd, ko, s, c->cursor + 2, stage_grid(c, sh, 2)));
         } else {
@@ -547,7 +554,8 @@ void key_shape(GraphKey& key, size_t& i, const Shape& sh, unsigned long long gen
     key.v[i++] = (uintptr_t)sh.wpb;
     key.v[i++] = (uintptr_t)sh.bps;
     key.v[i++] = (uintptr_t)(sh.grain + 64 * sh.queue + ((uintptr_t)sh.stage_bps[0] << 8) +
-                             ((uintptr_t)sh.stage_bps[1] << 16) + ((uintptr_t)sh.stage_bps[2] << 24));
+                             ((uintptr_t)sh.stage_bps[1] << 16) + ((uintptr_t)sh.stage_bps[2] << 24) +
+                             ((uintptr_t)sh.prefilter << 32));
     key.v[i++] = (uintptr_t)generation;
 }
 void key_batch(GraphKey& key, size_t& i, const lf_batch* b, const lf_output* o) {
@@ -659,6 +667,23 @@ lf_status lf_debug_stages(lf_ctx* c, const lf_batch* b, int32_t* win_begin, int3
     LF_CUDA(c, launch_debug_triplets(c->kp, to_kbatch(b), (int*)c->wbeg.p, (uint8_t*)c->wcnt.p,
                                      (uint64_t*)c->keys.p, (uint8_t*)c->ntrip.p, win_count, n_trip, trip, trip_chi2,
                                      s));
+    return LF_OK;
+}
+
+lf_status lf_debug_triplets(lf_ctx* c, const lf_batch* b, int32_t* win_count, int32_t* n_trip, int32_t* trip,
+                            float* trip_chi2, void* stream) {
+    if (!c) return LF_ERR_ARG;
+    lf_status st;
+    if ((st = check_batch(c, b)) != LF_OK) return st;
+    if (!win_count || !n_trip || !trip || !trip_chi2) return fail(c, LF_ERR_ARG, "dump array is NULL");
+    const size_t nt = (size_t)b->n_tracks;
+    if (nt == 0) return LF_OK;
+    const size_t ns = c->p.no_ut ? 2 : 1, NT = (size_t)(c->p.n_triplets > 0 ? c->p.n_triplets : 1);
+    if (c->wbeg.cap < nt * ns * NL * 4 || c->wcnt.cap < nt * ns * NL || c->keys.cap < nt * NT * 8 || c->ntrip.cap < nt)
+        return fail(c, LF_ERR_ARG, "no stage-pipeline results of this size in the context");
+    LF_CUDA(c, launch_debug_triplets(c->kp, to_kbatch(b), (int*)c->wbeg.p, (uint8_t*)c->wcnt.p,
+                                     (uint64_t*)c->keys.p, (uint8_t*)c->ntrip.p, win_count, n_trip, trip, trip_chi2,
+                                     (cudaStream_t)stream));
     return LF_OK;
 }
 

@@ -37,7 +37,20 @@ struct KParams {
     float inv_T_x;  // 1/T_x when T_x is a power of two (then r^2 / T_x == r^2 * inv_T_x exactly), else 0
     int qop_poly;   // q/p from Eq. pt_kick with the polynomial field integral
     float qop_c[5][10];
+    float pf_bound; // half-precision triplet pre-filter: sqrt(T_triplet) + PF_MARGIN, rounded up
 };
+
+// Half-precision pre-filter of the triplet pairs (lf_tuning.triplet_prefilter).
+// It applies to a configuration whose h1 window spans at most PF_SPAN mm
+// (its x relative to the window's first hit then stay below 2048, where a
+// binary16 ulp is at most 1 mm) and whose h0 and h2 windows each share one z.
+// PF_MARGIN bounds the difference between the binary16 distance of a hit to
+// the approximate x1_expected and its exact distance to the binary32
+// x1_expected: 0.5 mm for each of the two roundings to binary16, about
+// 1e-3 mm for the binary16 subtraction near the cut, and the slope taken as a
+// product by 1/(z2 - z0) instead of a quotient (below 0.05 mm).
+constexpr float PF_SPAN = 2000.0f;
+constexpr float PF_MARGIN = 1.1f;
 
 // 1/t when t is a power of two whose reciprocal is a normal float (dividing by
 // t and multiplying by 1/t then give the same correctly rounded result for any
@@ -120,13 +133,17 @@ __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(
 __host__ __device__ inline size_t slot_bytes(int cap) {
     return align16(sizeof(SlotHead)) + size_t(2) * NL * cap * sizeof(float);
 }
-// per-warp scratch of the triplet stage: key buffer and materialised pairs
-__host__ __device__ inline size_t scratch_bytes() {
-    return align16(CAND_CAP * sizeof(unsigned long long) + PAIR_CAP * sizeof(unsigned short));
+// per-warp scratch of the triplet stage: key buffer and materialised pairs;
+// with the half-precision pre-filter (hp) also the two configurations' h1
+// windows as binary16 pairs and their constants
+constexpr size_t PF_BYTES = 2 * (MAX_CAP / 2) * 4 + 2 * 4 * sizeof(float);
+__host__ __device__ inline size_t scratch_bytes(bool hp = false) {
+    return align16(CAND_CAP * sizeof(unsigned long long) + PAIR_CAP * sizeof(unsigned short)) +
+           (hp ? align16(PF_BYTES) : 0);
 }
 // shared memory of a block of nw warps holding tpw tracks per warp
-__host__ __device__ inline size_t block_smem_bytes(int cap, int nw, int tpw) {
-    return size_t(nw) * tpw * slot_bytes(cap) + size_t(nw) * scratch_bytes();
+__host__ __device__ inline size_t block_smem_bytes(int cap, int nw, int tpw, bool hp = false) {
+    return size_t(nw) * tpw * slot_bytes(cap) + size_t(nw) * scratch_bytes(hp);
 }
 
 // ---- parameters (lf_api.cu), shared by every entry point ----
@@ -159,9 +176,11 @@ inline size_t coarse_count(int n_hits) { return ((size_t)n_hits + 31) / 32 + 1; 
 // otherwise a persistent grid of `blocks` blocks draining the stage's queue
 cudaError_t launch_windows(const KParams& k, const KBatch& b, const int* trk_event, int* wbeg, uint8_t* wcnt,
                            cudaStream_t s, int* cursor = nullptr, int blocks = 0);
+// prefilter 1: the half-precision pre-filter of the pairs (persistent form,
+// VELO-UT input only; same results)
 cudaError_t launch_triplets(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
                             const uint8_t* wcnt, uint64_t* keys, uint8_t* ntrip, cudaStream_t s,
-                            int* cursor = nullptr, int blocks = 0);
+                            int* cursor = nullptr, int blocks = 0, int prefilter = 0);
 // with a cursor (persistent) the extension also selects and writes `o`
 cudaError_t launch_extend(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
                           const uint8_t* wcnt, const uint64_t* keys, const uint8_t* ntrip, CandRec* cands,

@@ -46,6 +46,8 @@
 #include <climits>
 #include <cstdint>
 
+#include <cuda_fp16.h>
+
 #include "lf_device.cuh"
 #include "lf_internal.h"
 
@@ -229,6 +231,11 @@ struct Slot {
 struct Scratch {
     unsigned long long* cand;
     unsigned short* pairs;
+    // half-precision pre-filter: per configuration the h1 window's x
+    // relative to its first hit as binary16 pairs (MAX_CAP / 2 words each),
+    // then per configuration {reference x, 1/(z2 - z0), z0, applies}
+    __half2* hw;
+    float* pf;
 };
 
 __device__ __forceinline__ Slot slot_at(char* base, int i, int cap) {
@@ -240,11 +247,13 @@ __device__ __forceinline__ Slot slot_at(char* base, int i, int cap) {
     return s;
 }
 
-__device__ __forceinline__ Scratch scratch_at(char* base, int i) {
-    char* p = base + (size_t)i * scratch_bytes();
+__device__ __forceinline__ Scratch scratch_at(char* base, int i, bool hp = false) {
+    char* p = base + (size_t)i * scratch_bytes(hp);
     Scratch s;
     s.cand = reinterpret_cast<unsigned long long*>(p);
     s.pairs = reinterpret_cast<unsigned short*>(p + CAND_CAP * sizeof(unsigned long long));
+    s.hw = reinterpret_cast<__half2*>(p + scratch_bytes(false));
+    s.pf = reinterpret_cast<float*>(s.hw + MAX_CAP);
     return s;
 }
 
@@ -335,7 +344,96 @@ __device__ __forceinline__ int select_buffer(const Scratch& sc, int nb, int NT, 
 // threshold thr, this lane's kept key `mine`; see select_buffer).
 // key = chi2 bits << 32 | side << 19 | cfg << 18 | j0 << 12 | j2 << 6 | j1
 // (window-local indices), which orders by (chi2, side, cfg, h0, h2).
-template <int NIT, bool NOUT>
+// Half-precision pre-filter, set-up for one track: the h1 windows of both
+// configurations as binary16 pairs relative to their first hit (padded with
+// +inf) and each configuration's constants.  The pre-filter applies to a
+// configuration only if its h1 window spans at most PF_SPAN and its h0 and
+// h2 windows each share one z (the exact path then divides by the same
+// z2 - z0 for every pair of the configuration).
+__device__ __forceinline__ void prefilter_setup(const KParams& k, const Slot& m, const Scratch& sc, int lane) {
+    const int cap = k.cap, hc = (cap + 1) >> 1;
+    const __half inf = __ushort_as_half((unsigned short)0x7c00u);
+    for (int wd = lane; wd < 2 * hc; wd += 32) {
+        const int cfg = wd >= hc ? 1 : 0, i = wd - cfg * hc;
+        const int L1 = cfg ? 7 : 4, n1 = m.h->wcnt[L1];
+        const float* x1 = m.wx + L1 * cap;
+        __half a = inf, b = inf;
+        if (2 * i < n1) a = __float2half_rn(x1[2 * i] - x1[0]);
+        if (2 * i + 1 < n1) b = __float2half_rn(x1[2 * i + 1] - x1[0]);
+        sc.hw[cfg * (MAX_CAP / 2) + i] = __halves2half2(a, b);
+    }
+    if (lane < 2) {
+        const int cfg = lane;
+        const int L0 = cfg ? 3 : 0, L1 = cfg ? 7 : 4, L2 = cfg ? 11 : 8;
+        const int n0 = m.h->wcnt[L0], n1 = m.h->wcnt[L1], n2 = m.h->wcnt[L2];
+        float xr = 0.0f, rdz = 0.0f, z0 = 0.0f, ok = 0.0f;
+        if (n0 > 0 && n1 > 0 && n2 > 0 && m.h->zuni[L0] && m.h->zuni[L2]) {
+            const float* x1 = m.wx + L1 * cap;
+            z0 = m.wz[L0 * cap];
+            const float dz = m.wz[L2 * cap] - z0;
+            xr = x1[0];
+            // x1_expected of a pair the exact path accepts then lies within
+            // PF_SPAN + pf_bound < 2048 of xr, where the binary16 ulp is <= 1
+            if (dz > 0.0f && x1[n1 - 1] - xr <= PF_SPAN && k.pf_bound < 2048.0f - PF_SPAN) {
+                rdz = 1.0f / dz;
+                ok = 1.0f;
+            }
+        }
+        sc.pf[4 * cfg + 0] = xr;
+        sc.pf[4 * cfg + 1] = rdz;
+        sc.pf[4 * cfg + 2] = z0;
+        sc.pf[4 * cfg + 3] = ok;
+    }
+    __syncwarp();
+}
+
+// Half-precision pre-filter of np materialised pairs (Sec. "Performance",
+// the triplet seeding's chi2 in half2): a pair is kept if some hit of its h1
+// window lies within pf_bound of x1_expected computed with the slope as a
+// product by 1/(z2 - z0), the distances taken in binary16 two hits at a time.
+// A pair the exact path accepts has a hit within sqrt(T_triplet) of the
+// exact x1_expected, so within pf_bound in binary16 (PF_MARGIN covers the
+// roundings): the exact results are those without the pre-filter.  The kept
+// pairs are compacted in place (a kept pair never moves to a later index);
+// returns their number.
+__device__ __forceinline__ int prefilter_pairs(const KParams& k, const Slot& m, const Scratch& sc, int np,
+                                               int lane) {
+    const int cap = k.cap, hc = (cap + 1) >> 1;
+    const __half2 inf2 = __half2half2(__ushort_as_half((unsigned short)0x7c00u));
+    int ns = 0;
+#pragma unroll 1
+    for (int base = 0; base < np; base += 32) {
+        const int q = base + lane;
+        bool keep = false;
+        unsigned code = 0;
+        if (q < np) {
+            code = sc.pairs[q];
+            const int cfg = (int)(code >> 12), j0 = (int)((code >> 6) & 63), j2 = (int)(code & 63);
+            keep = true;
+            if (sc.pf[4 * cfg + 3] != 0.0f) {
+                const int L0 = cfg ? 3 : 0, L2 = cfg ? 11 : 8;
+                const float x0 = m.wx[L0 * cap + j0], x2 = m.wx[L2 * cap + j2];
+                const float t = (x2 - x0) * sc.pf[4 * cfg + 1];
+                const float K = cfg ? k.K_last : k.K_first;
+                const float z1 = cfg ? k.z[7] : k.z[4];
+                const float e = z1 * t + (x0 - t * sc.pf[4 * cfg + 2]) * K;
+                const __half2 e2 = __half2half2(__float2half_rn(e - sc.pf[4 * cfg + 0]));
+                const __half2* w = sc.hw + cfg * (MAX_CAP / 2);
+                __half2 mn = inf2;
+                for (int i = 0; i < hc; ++i) mn = __hmin2(mn, __habs2(__hsub2(w[i], e2)));
+                keep = fminf(__low2float(mn), __high2float(mn)) < k.pf_bound;
+            }
+        }
+        const unsigned msk = __ballot_sync(FULL, keep);
+        __syncwarp();
+        if (keep) sc.pairs[ns + __popc(msk & ((1u << lane) - 1u))] = (unsigned short)code;
+        ns += __popc(msk);
+    }
+    __syncwarp();
+    return ns;
+}
+
+template <int NIT, bool NOUT, bool HP = false>
 __device__ __forceinline__ void triplet_pass(const KParams& k, const TState& s, const Slot& m, const Scratch& sc,
                                              int lane, int side, int& nb, uint64_t& thr, uint64_t& mine) {
     const int cap = k.cap;
@@ -408,6 +506,7 @@ __device__ __forceinline__ void triplet_pass(const KParams& k, const TState& s, 
         pre_it[part] = P + inc - n_it[part];
         P += __shfl_sync(FULL, inc, 31);
     }
+    if (HP && P > 0) prefilter_setup(k, m, sc, lane);
 
 #pragma unroll 1
     for (int seg = 0; seg < P; seg += PAIR_CAP) {
@@ -419,7 +518,8 @@ __device__ __forceinline__ void triplet_pass(const KParams& k, const TState& s, 
                 sc.pairs[q - seg] = (unsigned short)(code_it[part] | (a_it[part] + (q - pre_it[part])));
         }
         __syncwarp();
-        const int np = min(P - seg, PAIR_CAP);
+        int np = min(P - seg, PAIR_CAP);
+        if (HP) np = prefilter_pairs(k, m, sc, np, lane);
 #pragma unroll 1
         for (int base = 0; base < np; base += 32) {
             int q = base + lane;
@@ -478,7 +578,7 @@ __device__ __forceinline__ void triplet_pass(const KParams& k, const TState& s, 
 // Triplet stage of one window set: returns this lane's entry of the sorted
 // list of kept triplet keys (lane r holds rank r; NOKEY past the end) and
 // the list length.
-template <int NIT>
+template <int NIT, bool HP = false>
 __device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState& s, const Slot& m, const Scratch& sc,
                                                  int lane, int& n_trip) {
     n_trip = 0;
@@ -486,7 +586,7 @@ __device__ __forceinline__ uint64_t triplet_scan(const KParams& k, const TState&
     int nb = 0;            // keys in the buffer
     uint64_t thr = NOKEY;  // keys at or above thr cannot be kept
     uint64_t mine = NOKEY;
-    triplet_pass<NIT, false>(k, s, m, sc, lane, 0, nb, thr, mine);
+    triplet_pass<NIT, false, HP>(k, s, m, sc, lane, 0, nb, thr, mine);
     nb = select_buffer(sc, nb, k.n_trip, thr, lane, mine);
     n_trip = nb;
     return mine;
@@ -836,7 +936,7 @@ __device__ __forceinline__ void load_windows(const int* wbeg, const uint8_t* wcn
 
 constexpr int PLAIN_WARPS = 8;
 
-template <int NIT, bool NOUT>
+template <int NIT, bool NOUT, bool HP = false>
 __device__ __forceinline__ void triplets_track(const KParams& k, const KBatch& b, const int* __restrict__ wbeg,
                                                const uint8_t* __restrict__ wcnt, uint64_t* keys, uint8_t* ntrip,
                                                const Slot& m, const Scratch& sc, int t, int lane) {
@@ -846,7 +946,7 @@ __device__ __forceinline__ void triplets_track(const KParams& k, const KBatch& b
     if (!NOUT) {
         load_windows(wbeg, wcnt, t, m, lane);
         stage_windows<true>(k, b, m, lane);
-        top = triplet_scan<NIT>(k, s, m, sc, lane, nt);
+        top = triplet_scan<NIT, HP>(k, s, m, sc, lane, nt);
     } else if (k.n_trip > 0) {
         // both charge assumptions into one list: stage and scan each set
         int nb = 0;
@@ -864,24 +964,26 @@ __device__ __forceinline__ void triplets_track(const KParams& k, const KBatch& b
     __syncwarp();
 }
 
-// stage 2: triplet seeding (warp per track)
-template <int NIT, bool P, bool NOUT>
+// stage 2: triplet seeding (warp per track); HP: the half-precision
+// pre-filter of the pairs
+template <int NIT, bool P, bool NOUT, bool HP = false>
 __global__ void __launch_bounds__(PLAIN_WARPS * 32, 5) k_triplets(KParams k, KBatch b, const int* __restrict__ wbeg, const uint8_t* __restrict__ wcnt,
                            uint64_t* keys, uint8_t* ntrip, int* cursor) {
+    static_assert(!HP || !NOUT, "the pre-filter follows VELO-UT input only");
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Slot m = slot_at(smem, warp, k.cap);
-    const Scratch sc = scratch_at(smem + PLAIN_WARPS * slot_bytes(k.cap), warp);
+    const Scratch sc = scratch_at(smem + PLAIN_WARPS * slot_bytes(k.cap), warp, HP);
     slot_sizes(b);
     if (!P) {
         const int t = blockIdx.x * PLAIN_WARPS + warp;
-        if (t < b.n_tracks) triplets_track<NIT, NOUT>(k, b, wbeg, wcnt, keys, ntrip, m, sc, t, lane);
+        if (t < b.n_tracks) triplets_track<NIT, NOUT, HP>(k, b, wbeg, wcnt, keys, ntrip, m, sc, t, lane);
         return;
     }
     for (;;) {
         const int t = queue_take(cursor, 1, lane);
         if (t >= b.n_tracks) break;
-        triplets_track<NIT, NOUT>(k, b, wbeg, wcnt, keys, ntrip, m, sc, t, lane);
+        triplets_track<NIT, NOUT, HP>(k, b, wbeg, wcnt, keys, ntrip, m, sc, t, lane);
     }
 }
 
@@ -1376,14 +1478,14 @@ cudaError_t launch_windows(const KParams& k, const KBatch& b, const int* trk_eve
     return cudaGetLastError();
 }
 
-template <int NIT, bool P, bool NOUT>
+template <int NIT, bool P, bool NOUT, bool HP = false>
 static cudaError_t launch_triplets_t(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* wcnt,
                                      uint64_t* keys, uint8_t* ntrip, cudaStream_t s, int* cursor, int blocks) {
-    size_t sm = block_smem_bytes(k.cap, PLAIN_WARPS, 1);
-    cudaError_t err = set_smem((const void*)k_triplets<NIT, P, NOUT>, sm);
+    size_t sm = block_smem_bytes(k.cap, PLAIN_WARPS, 1, HP);
+    cudaError_t err = set_smem((const void*)k_triplets<NIT, P, NOUT, HP>, sm);
     if (err != cudaSuccess) return err;
     const int grid = P ? blocks : cdiv(b.n_tracks, PLAIN_WARPS);
-    k_triplets<NIT, P, NOUT><<<grid, PLAIN_WARPS * 32, sm, s>>>(k, b, wbeg, wcnt, keys, ntrip, cursor);
+    k_triplets<NIT, P, NOUT, HP><<<grid, PLAIN_WARPS * 32, sm, s>>>(k, b, wbeg, wcnt, keys, ntrip, cursor);
     return cudaGetLastError();
 }
 
@@ -1399,9 +1501,16 @@ static cudaError_t launch_triplets_p(const KParams& k, const KBatch& b, const in
 
 cudaError_t launch_triplets(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
                             const uint8_t* wcnt, uint64_t* keys, uint8_t* ntrip, cudaStream_t s, int* cursor,
-                            int blocks) {
+                            int blocks, int prefilter) {
     (void)trk_event;
     if (b.n_tracks <= 0) return cudaSuccess;
+    if (prefilter) {
+        // persistent form, VELO-UT input (the entry points refuse the rest)
+        if (!cursor || k.no_ut) return cudaErrorInvalidValue;
+        if (k.cap <= 16) return launch_triplets_t<1, true, false, true>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
+        if (k.cap <= 32) return launch_triplets_t<2, true, false, true>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
+        return launch_triplets_t<4, true, false, true>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
+    }
     if (cursor) return launch_triplets_p<true>(k, b, wbeg, wcnt, keys, ntrip, s, cursor, blocks);
     return launch_triplets_p<false>(k, b, wbeg, wcnt, keys, ntrip, s, nullptr, 0);
 }

@@ -92,7 +92,7 @@ class lf_host_output(C.Structure):
 class lf_tuning(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("grain", C.c_int32),
                 ("queue", C.c_int32), ("windows_bps", C.c_int32), ("triplets_bps", C.c_int32),
-                ("extend_bps", C.c_int32)]
+                ("extend_bps", C.c_int32), ("triplet_prefilter", C.c_int32)]
 
 
 def coarse_count(n_hits: int) -> int:
@@ -125,6 +125,8 @@ _lib.lf_find_tracks_batched.argtypes = [_P, C.POINTER(lf_batch), C.POINTER(lf_ou
 _lib.lf_find_tracks_batched.restype = C.c_int
 _lib.lf_debug_stages.argtypes = [_P, C.POINTER(lf_batch), _P, _P, _P, _P, _P, _P]
 _lib.lf_debug_stages.restype = C.c_int
+_lib.lf_debug_triplets.argtypes = [_P, C.POINTER(lf_batch), _P, _P, _P, _P, _P]
+_lib.lf_debug_triplets.restype = C.c_int
 _lib.lf_sync_status.argtypes = [_P, _P, C.POINTER(C.c_int32)]
 _lib.lf_sync_status.restype = C.c_int
 _lib.lf_process_host.argtypes = [_P, C.POINTER(lf_host_batch), C.POINTER(lf_host_output), C.POINTER(lf_tuning),
@@ -147,7 +149,7 @@ _lib.lf_host_free.argtypes = [_P]
 _lib.lf_host_free.restype = None
 
 EXPORTED = ["lf_create", "lf_destroy", "lf_last_error", "lf_device_sm_count", "lf_pack_hits", "lf_find_tracks",
-            "lf_find_tracks_batched", "lf_debug_stages", "lf_sync_status", "lf_process_host",
+            "lf_find_tracks_batched", "lf_debug_stages", "lf_debug_triplets", "lf_sync_status", "lf_process_host",
             "lf_find_tracks_static", "lf_host_alloc", "lf_host_free", "lf_reserve", "lf_device_host_numa",
             "lf_process_slot", "lf_graph_count"]
 
@@ -352,6 +354,10 @@ def lf_debug_stages(ctx, batch: lf_batch, win_begin, win_count, n_trip, trip, tr
     _check(ctx, _lib.lf_debug_stages(ctx, C.byref(batch), win_begin, win_count, n_trip, trip, trip_chi2, stream))
 
 
+def lf_debug_triplets(ctx, batch: lf_batch, win_count, n_trip, trip, trip_chi2, stream) -> None:
+    _check(ctx, _lib.lf_debug_triplets(ctx, C.byref(batch), win_count, n_trip, trip, trip_chi2, stream))
+
+
 def lf_process_host(ctx, batch: lf_host_batch, out: lf_host_output, tuning: Optional[lf_tuning],
                     chunk_hits: int = 0) -> None:
     tp = C.byref(tuning) if tuning is not None else None
@@ -480,6 +486,22 @@ class Tracker:
         b = self.batch_struct(packed, states, n_events)
         lf_debug_stages(self.ctx, b, _ptr(d["win_begin"]), _ptr(d["win_count"]), _ptr(d["n_trip"]),
                         _ptr(d["trip"]), _ptr(d["trip_chi2"]), _stream(stream))
+        return d
+
+    def last_triplets(self, packed: dict, states, n_events: int, stream=None) -> dict:
+        """Triplet lists the last batched call (stage pipeline) left in the
+        context's scratch, decoded without running any stage again."""
+        n_t = int(states.sx.numel())
+        nt = max(int(self.params["n_triplets"]), 1)
+        dev = packed["x"].device
+        ns = 2 if self.params.get("no_ut", 0) else 1
+        d = dict(win_count=torch.empty((n_t, ns * NL), dtype=torch.int32, device=dev),
+                 n_trip=torch.empty(n_t, dtype=torch.int32, device=dev),
+                 trip=torch.full((n_t, nt, 4), -1, dtype=torch.int32, device=dev),
+                 trip_chi2=torch.zeros((n_t, nt), dtype=torch.float32, device=dev))
+        b = self.batch_struct(packed, states, n_events)
+        lf_debug_triplets(self.ctx, b, _ptr(d["win_count"]), _ptr(d["n_trip"]), _ptr(d["trip"]),
+                          _ptr(d["trip_chi2"]), _stream(stream))
         return d
 
     def status(self, stream=None) -> int:

@@ -34,3 +34,15 @@ def test_choice_table_round_trip(tmp_path):
     names = {f for f, _ in lf.lf_tuning._fields_}
     assert all(set(c) <= names for c in autotune.CANDIDATES)
     assert sum(1 for c in autotune.CANDIDATES if c.get("queue", 0) == 0 and len(c) > 1) >= 4
+
+
+def test_candidates_applicable_to_the_no_ut_variant():
+    """The no-UT variant runs on the stage pipeline without the triplet
+    pre-filter; the tuner skips the rest for it, and keeps every candidate
+    for VELO-UT input."""
+    from paper_2402_14670_gb300 import autotune
+    velo_ut = [c for c in autotune.CANDIDATES if autotune.applicable(c, dict(no_ut=0))]
+    assert velo_ut == autotune.CANDIDATES
+    no_ut = [c for c in autotune.CANDIDATES if autotune.applicable(c, dict(no_ut=1))]
+    assert no_ut and all(c.get("queue", 0) == 0 and not c.get("triplet_prefilter", 0) for c in no_ut)
+    assert any(c.get("triplet_prefilter", 0) for c in autotune.CANDIDATES)
