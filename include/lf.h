@@ -201,6 +201,12 @@ typedef struct {
                                   above binary16 rounding, and only the pairs that pass get the exact
                                   binary32 filters, closest-hit search and chi2.  Same results as 0;
                                   LF_ERR_ARG with queue != 0 or the no-UT variant. */
+    int32_t extend_form;       /* stage pipeline's extension: 0 default (1 for VELO-UT input, 2 for
+                                  the no-UT variant); 1 block form: a block of 256 threads takes
+                                  min(256 / n_triplets, 32) tracks and runs one candidate per thread
+                                  (VELO-UT input only, else LF_ERR_ARG); 2 warp form: a track per 16
+                                  lanes (two per warp when n_triplets <= 16), else per warp.  Same
+                                  results; LF_ERR_ARG with a nonzero value and queue != 0. */
 } lf_tuning;
 
 /* Create a context: validates and copies geometry and parameters (the

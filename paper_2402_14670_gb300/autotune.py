@@ -29,6 +29,7 @@ CANDIDATES = [
     dict(queue=0, triplets_bps=4, extend_bps=3),
     dict(queue=0, windows_bps=4, triplets_bps=4, extend_bps=3),
     dict(queue=0, triplet_prefilter=1),                   # half-precision pre-filter of the triplet pairs
+    dict(queue=0, extend_form=2),                         # extension: a track per 16 lanes (warp form)
     dict(queue=1, warps_per_block=8, grain=2),            # block-synchronous tile kernel
 ]
 TRACK_EDGES = (32, 64, 128, 256)
@@ -40,7 +41,7 @@ def applicable(cand: dict, params: dict) -> bool:
     """Whether the library accepts a candidate for these parameters: the
     no-UT variant runs on the stage pipeline without the triplet pre-filter."""
     if params.get("no_ut", 0):
-        return cand.get("queue", 0) == 0 and not cand.get("triplet_prefilter", 0)
+        return cand.get("queue", 0) == 0 and not cand.get("triplet_prefilter", 0) and cand.get("extend_form", 0) != 1
     return True
 
 

@@ -405,6 +405,7 @@ struct Shape {
     int wpb, bps, grain, queue;
     int stage_bps[3];   // per-stage blocks per SM of the stage pipeline (0: bps, else as many as fit)
     int prefilter;      // triplet pre-filter (stage pipeline)
+    int extend_form;    // extension of the stage pipeline: 1 block form, 2 warp form
 };
 
 // queue modes of lf_tuning
@@ -427,6 +428,14 @@ lf_status resolve_shape(lf_ctx* c, const lf_tuning* tuning, Shape& sh) {
     if (sh.prefilter < 0 || sh.prefilter > 1) return fail(c, LF_ERR_ARG, "triplet_prefilter %d outside 0..1", sh.prefilter);
     if (sh.prefilter && (sh.queue != Q_STAGES || c->p.no_ut))
         return fail(c, LF_ERR_ARG, "the triplet pre-filter runs on the stage pipeline (queue 0) with VELO-UT input");
+    sh.extend_form = tuning ? tuning->extend_form : 0;
+    if (sh.extend_form < 0 || sh.extend_form > 2)
+        return fail(c, LF_ERR_ARG, "extend_form %d outside 0..2", sh.extend_form);
+    if (sh.extend_form && sh.queue != Q_STAGES)
+        return fail(c, LF_ERR_ARG, "extend_form applies to the stage pipeline (queue 0)");
+    if (sh.extend_form == 1 && c->p.no_ut)
+        return fail(c, LF_ERR_ARG, "the block form of the extension follows VELO-UT input only");
+    if (sh.extend_form == 0) sh.extend_form = c->p.no_ut ? 2 : 1;
     if (sh.queue == Q_STAGES) {
         if (!c->stage_bps[0]) LF_CUDA(c, stage_blocks_per_sm(c->kp, c->stage_bps));
         sh.bps = tuning && tuning->blocks_per_sm > 0 ? tuning->blocks_per_sm : 0;
@@ -488,7 +497,8 @@ lf_status launch_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const
             LF_CUDA(c, launch_triplets(c->kp, kb, te, wb, wc, ky, nt, s, c->cursor + 1, stage_grid(c, sh, 1),
                                        sh.prefilter));
             // the persistent extension selects and writes the output itself
-            LF_CUDA(c, launch_extend(c->kp, kb, te, wb, wc, ky, nt, cd, ko, s, c->cursor + 2, stage_grid(c, sh, 2)));
+            LF_CUDA(c, launch_extend(c->kp, kb, te, wb, wc, ky, nt, cd, ko, s, c->cursor + 2, stage_grid(c, sh, 2),
+                                     sh.extend_form == 1 ? 1 : 0));
         } else {
             LF_CUDA(c, launch_fused(c->kp, kb, ko, c->cursor, sh.grain, sh.wpb, sh.bps * c->n_sm, s));
         }
@@ -555,7 +565,7 @@ void key_shape(GraphKey& key, size_t& i, const Shape& sh, unsigned long long gen
     key.v[i++] = (uintptr_t)sh.bps;
     key.v[i++] = (uintptr_t)(sh.grain + 64 * sh.queue + ((uintptr_t)sh.stage_bps[0] << 8) +
                              ((uintptr_t)sh.stage_bps[1] << 16) + ((uintptr_t)sh.stage_bps[2] << 24) +
-                             ((uintptr_t)sh.prefilter << 32));
+                             ((uintptr_t)sh.prefilter << 32) + ((uintptr_t)sh.extend_form << 33));
     key.v[i++] = (uintptr_t)generation;
 }
 void key_batch(GraphKey& key, size_t& i, const lf_batch* b, const lf_output* o) {

@@ -182,9 +182,11 @@ cudaError_t launch_triplets(const KParams& k, const KBatch& b, const int* trk_ev
                             const uint8_t* wcnt, uint64_t* keys, uint8_t* ntrip, cudaStream_t s,
                             int* cursor = nullptr, int blocks = 0, int prefilter = 0);
 // with a cursor (persistent) the extension also selects and writes `o`
+// form 1 (persistent, VELO-UT input): the block form, one candidate per
+// thread over a tile of tracks
 cudaError_t launch_extend(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
                           const uint8_t* wcnt, const uint64_t* keys, const uint8_t* ntrip, CandRec* cands,
-                          const KOut& o, cudaStream_t s, int* cursor = nullptr, int blocks = 0);
+                          const KOut& o, cudaStream_t s, int* cursor = nullptr, int blocks = 0, int form = 0);
 cudaError_t launch_select(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* ntrip,
                           const CandRec* cands, const KOut& o, cudaStream_t s, int* cursor = nullptr,
                           int blocks = 0);

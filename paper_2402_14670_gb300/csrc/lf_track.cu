@@ -1157,6 +1157,131 @@ __global__ void __launch_bounds__(PLAIN_WARPS * 32, 4) k_extend(
     }
 }
 
+// Block form of the persistent extension (VELO-UT input): a block takes a
+// tile of TT = min(256 / n_triplets, 32) consecutive input tracks and runs one
+// candidate per thread, thread c extending triplet c % n_triplets of track
+// c / n_triplets, so that the candidates of about 21 tracks (n_triplets 12)
+// fill all of the block's lanes instead of 24 of every warp's 32.  The
+// tile's x windows are staged once per track (warp w stages tracks w, w + 8,
+// ...); the lowest (Q bits, rank) key of a track is found with a
+// shared-memory minimum, and its candidate's thread writes the output.
+constexpr int XB_THREADS = 256;
+constexpr int XB_MAX_TRACKS = 32;   // tracks of a tile, most (shared memory of their windows)
+
+__host__ __device__ inline size_t xslot_bytes(int cap) { return align16(sizeof(SlotHead)) + size_t(NL) * cap * sizeof(float); }
+__host__ __device__ inline int xtile_tracks(int n_trip) {
+    const int tt = XB_THREADS / (n_trip > 0 ? n_trip : 1);
+    return tt < XB_MAX_TRACKS ? tt : XB_MAX_TRACKS;
+}
+__host__ __device__ inline size_t xblock_smem_bytes(int cap, int n_trip) {
+    return align16((size_t)xtile_tracks(n_trip) * sizeof(unsigned long long)) + (size_t)xtile_tracks(n_trip) * xslot_bytes(cap);
+}
+
+__device__ __forceinline__ Slot xslot_at(char* base, int i, int cap) {
+    char* p = base + (size_t)i * xslot_bytes(cap);
+    Slot s;
+    s.h = reinterpret_cast<SlotHead*>(p);
+    s.wx = reinterpret_cast<float*>(p + align16(sizeof(SlotHead)));
+    s.wz = nullptr;
+    return s;
+}
+
+// L2 prefetch of the z, dxdy and w lines of window lw of a staged slot
+__device__ __forceinline__ void prefetch_window_lines(const KBatch& b, const Slot& m, int lw) {
+    const int wb = m.h->wbeg[lw], wc = m.h->wcnt[lw];
+    if (wc <= 0) return;
+    const uintptr_t lines[3] = {reinterpret_cast<uintptr_t>(b.z + wb), reinterpret_cast<uintptr_t>(b.dxdy + wb),
+                                reinterpret_cast<uintptr_t>(b.w + wb)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const uintptr_t p0 = lines[a] & ~uintptr_t(127), p1 = lines[a] + (uintptr_t)wc * 4;
+        for (uintptr_t q = p0; q < p1; q += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+    }
+}
+
+__global__ void __launch_bounds__(XB_THREADS, 4) k_extend_block(KParams k, KBatch b, const int* __restrict__ wbeg,
+                                                              const uint8_t* __restrict__ wcnt,
+                                                              const uint64_t* __restrict__ keys,
+                                                              const uint8_t* __restrict__ ntrip, KOut o, int* cursor) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ int s_t0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int NT = k.n_trip > 0 ? k.n_trip : 1;
+    const int TT = xtile_tracks(k.n_trip);
+    unsigned long long* sel = reinterpret_cast<unsigned long long*>(smem);
+    char* slots = smem + align16((size_t)TT * sizeof(unsigned long long));
+    slot_sizes(b);
+    const int q = tid / NT, r = tid - q * NT;   // this thread's track in the tile and triplet rank
+    for (;;) {
+        if (tid == 0) s_t0 = atomicAdd(cursor, TT);
+        __syncthreads();
+        const int t0 = s_t0;
+        if (t0 >= b.n_tracks) break;
+        // stage the tile's windows: warp w stages tracks w, w + 8, ...
+        for (int qq = warp; qq < TT; qq += XB_THREADS / 32) {
+            const Slot m = xslot_at(slots, qq, k.cap);
+            const int t = t0 + qq;
+            if (lane < NL) {
+                int wb = 0, wc = 0;
+                if (t < b.n_tracks) {
+                    wb = wbeg[(size_t)t * NL + lane];
+                    wc = wcnt[(size_t)t * NL + lane];
+                }
+                m.h->wbeg[lane] = wb;
+                m.h->wcnt[lane] = wc;
+            }
+            __syncwarp();
+            stage_issue<false, false>(k, b, m, lane);
+            if (lane < NL) prefetch_window_lines(b, m, lane);
+        }
+        if (tid < TT) sel[tid] = NOKEY;
+        // this thread's candidate inputs load while the copies are in flight
+        const int t = t0 + q;
+        const bool live = q < TT && t < b.n_tracks;
+        const bool act = live && r < ntrip[t];
+        const uint64_t key = act ? keys[(size_t)t * k.n_trip + r] : NOKEY;
+        TState s = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (act) s = load_state(b, t);
+        cp_async_wait_all();
+        __syncthreads();
+        Cand cd;
+        cd.status = 9;
+        cd.Q = 0.0f;
+        cd.n = 0;
+        Slot m;
+        m.h = nullptr;
+        m.wx = nullptr;
+        m.wz = nullptr;
+        if (act) {
+            m = xslot_at(slots, q, k.cap);
+            extend_fit<true>(k, b, s, m, key, cd);
+        }
+        const bool have = act && cd.status == 0;
+        const unsigned long long mine = have ? (((unsigned long long)__float_as_uint(cd.Q) << 32) | (unsigned)r) : NOKEY;
+        if (have) atomicMin(&sel[q], mine);
+        __syncthreads();
+        if (live) {
+            const unsigned long long best = sel[q];
+            if (best == NOKEY) {
+                if (r == 0) {
+                    o.found[t] = 0;
+                    o.nhits[t] = 0;
+                }
+            } else if (have && mine == best) {
+#pragma unroll
+                for (int l = 0; l < NL; ++l)
+                    o.hit_idx[(size_t)t * NL + l] = cd.hl[l] >= 0 ? m.h->wbeg[l] + cd.hl[l] : -1;
+#pragma unroll
+                for (int p = 0; p < 6; ++p) o.state[(size_t)t * 6 + p] = cd.st[p];
+                o.quality[t] = cd.Q;
+                o.nhits[t] = (uint8_t)cd.n;
+                o.found[t] = 1;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __device__ __forceinline__ void select_track(const KParams& k, const int* __restrict__ wbeg,
                                              const uint8_t* __restrict__ ntrip, const CandRec* __restrict__ cands,
                                              const KOut& o, int t, int lane) {
@@ -1529,12 +1654,19 @@ static cudaError_t launch_extend_t(const KParams& k, const KBatch& b, const int*
 
 cudaError_t launch_extend(const KParams& k, const KBatch& b, const int* trk_event, const int* wbeg,
                           const uint8_t* wcnt, const uint64_t* keys, const uint8_t* ntrip, CandRec* cands,
-                          const KOut& o, cudaStream_t s, int* cursor, int blocks) {
+                          const KOut& o, cudaStream_t s, int* cursor, int blocks, int form) {
     (void)trk_event;
     if (b.n_tracks <= 0) return cudaSuccess;
     if (k.no_ut) {
         if (cursor) return launch_extend_t<1, true, true>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, cursor, blocks);
         return launch_extend_t<1, false, true>(k, b, wbeg, wcnt, keys, ntrip, cands, o, s, nullptr, 0);
+    }
+    if (cursor && form == 1) {
+        const size_t sm = xblock_smem_bytes(k.cap, k.n_trip);
+        cudaError_t err = set_smem((const void*)k_extend_block, sm);
+        if (err != cudaSuccess) return err;
+        k_extend_block<<<blocks, XB_THREADS, sm, s>>>(k, b, wbeg, wcnt, keys, ntrip, o, cursor);
+        return cudaGetLastError();
     }
     if (k.n_trip <= 16) {
         if (cursor)

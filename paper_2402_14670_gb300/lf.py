@@ -92,7 +92,8 @@ class lf_host_output(C.Structure):
 class lf_tuning(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("grain", C.c_int32),
                 ("queue", C.c_int32), ("windows_bps", C.c_int32), ("triplets_bps", C.c_int32),
-                ("extend_bps", C.c_int32), ("triplet_prefilter", C.c_int32)]
+                ("extend_bps", C.c_int32), ("triplet_prefilter", C.c_int32),
+                ("extend_form", C.c_int32)]
 
 
 def coarse_count(n_hits: int) -> int:

@@ -104,6 +104,8 @@ def test_parameter_edges(lfm, cap, nt):
 
 @pytest.mark.parametrize("tuning", [dict(queue=0, blocks_per_sm=1),
                                     dict(queue=0),
+                                    dict(queue=0, extend_form=1),
+                                    dict(queue=0, extend_form=2, extend_bps=1, triplet_prefilter=1),
                                     dict(queue=2, warps_per_block=1, grain=1, blocks_per_sm=1),
                                     dict(queue=2, warps_per_block=4, grain=2),
                                     dict(queue=1, warps_per_block=16, grain=2),
@@ -113,6 +115,18 @@ def test_launch_shapes_identical(lfm, tuning):
     b = synth.generate(1, n_events=120).to("cuda")
     tr = _tracker(lfm)
     run_both(tr, b, mode="batched", tuning=tuning)
+
+
+@pytest.mark.parametrize("cap,nt", [(32, 1), (5, 3), (32, 12), (64, 20), (17, 32), (32, 0)])
+def test_extension_block_form_parameters(lfm, cap, nt):
+    """The block form of the extension (a tile of min(256 / n_triplets, 32)
+    tracks, one candidate per thread) at tile sizes 32, 32, 21, 12, 8 and 32
+    tracks, against the oracle."""
+    p = lfm.default_params()
+    p.update(n_hits_window=cap, n_triplets=nt)
+    b = synth.generate(1, n_events=40).to("cuda")
+    tr = _tracker(lfm, None, p)
+    run_both(tr, b, mode="batched", params=p, tuning=dict(queue=0, extend_form=1))
 
 
 def _jitter_z(b, frac_events=0.5, seed=5):
@@ -133,7 +147,8 @@ def _jitter_z(b, frac_events=0.5, seed=5):
 
 
 @pytest.mark.parametrize("mode,tuning", [("plain", None), ("batched", None), ("batched", dict(queue=1, grain=2)),
-                                         ("batched", dict(queue=2, grain=1))])
+                                         ("batched", dict(queue=2, grain=1)),
+                                         ("batched", dict(queue=0, extend_form=1))])
 def test_hits_with_their_own_z(lfm, mode, tuning):
     """Hits of a layer at different z (one in a few hundred moved by up to
     0.5 mm): every kernel takes each hit's own z, as the oracle does, instead

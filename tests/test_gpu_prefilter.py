@@ -104,4 +104,8 @@ def test_prefilter_refused_where_it_does_not_run(lfm):
     with pytest.raises(lfm.LFError) as ei:
         tn.find(packed, b, b.n_events, "batched", HP)
     assert ei.value.status == lfm.LF_ERR_ARG
+    # the block form of the extension likewise
+    with pytest.raises(lfm.LFError) as ei:
+        tn.find(packed, b, b.n_events, "batched", dict(queue=0, extend_form=1))
+    assert ei.value.status == lfm.LF_ERR_ARG
     tn.close()
