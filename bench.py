@@ -647,7 +647,7 @@ def main():
         inst = float(fp["warp_instructions_per_launch"]) * n_trk / float(fp["tracks"])
         ach = inst / (find_avg / 1e3)
         pk_issue = n_sm * 4 * mhz * 1e6
-        roof_issue = {"kernel": "k_windows + k_triplets + k_extend (persistent)", "bound": "issue",
+        roof_issue = {"kernel": "k_windows + k_triplets + k_extend_block (persistent)", "bound": "issue",
                       "achieved": ach, "peak": pk_issue, "unit": "warp-instructions/s", "frac": ach / pk_issue,
                       "warp_instructions_per_launch": inst,
                       "peak_kind": "%d SMs x 4 schedulers x %.0f MHz (median SM clock, timed region)" % (n_sm, mhz)}
