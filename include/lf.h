@@ -410,6 +410,16 @@ lf_status lf_debug_stages(lf_ctx* ctx, const lf_batch* batch, int32_t* win_begin
 lf_status lf_debug_triplets(lf_ctx* ctx, const lf_batch* batch, int32_t* win_count, int32_t* n_trip,
                             int32_t* trip, float* trip_chi2, void* stream);
 
+/* Debug check of a batch, outside the hot path (the find kernels assume
+ * these conventions and do not check them): hit_offsets within 0..n_hits and
+ * non-decreasing; trk_offsets within 0..n_tracks, non-decreasing and ending
+ * at n_tracks; then x ascending inside every (event, zone, layer) bucket of
+ * Sec. "Defining the search windows" (ties allowed, NaN refused) and, if
+ * given, x_coarse[i] == x[32 i] bit for bit.  Synchronises the stream.
+ * Returns LF_OK, or LF_ERR_ARG with the first violation in lf_last_error
+ * (the buckets are checked only once the offsets pass). */
+lf_status lf_validate_batch(lf_ctx* ctx, const lf_batch* batch, void* stream);
+
 /* Synchronise the stream, read and clear the device status word.
  * Returns LF_OK, LF_ERR_CAPACITY or LF_ERR_TIMEOUT; *flags gets the bits. */
 lf_status lf_sync_status(lf_ctx* ctx, void* stream, int32_t* flags);

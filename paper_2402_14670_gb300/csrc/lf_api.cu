@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/lf.h: context, scratch memory,
 // argument checks, launches, and the CUDA graphs of the persistent form.
+#include <climits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -42,7 +43,7 @@ struct lf_ctx {
     int* cursor = nullptr;   // device work-queue cursors (8 ints)
     unsigned long long generation = 0;  // bumped whenever scratch is reallocated
     int stage_bps[4] = {0, 0, 0, 0};
-    DevBuf trk_event, wbeg, wcnt, keys, ntrip, cands, ev_count, coarse;
+    DevBuf trk_event, wbeg, wcnt, keys, ntrip, cands, ev_count, coarse, valid;
     struct GraphEntry {
         cudaGraphExec_t exec = nullptr;
         unsigned long long used = 0;   // last use (graph_clock), for eviction
@@ -335,7 +336,7 @@ void lf_destroy(lf_ctx* c) {
     for (auto& kv : c->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     DevBuf* bufs[] = {&c->trk_event, &c->wbeg, &c->wcnt, &c->keys, &c->ntrip, &c->coarse,
-                      &c->cands, &c->ev_count};
+                      &c->cands, &c->ev_count, &c->valid};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     cudaFree(c->status);
@@ -694,6 +695,39 @@ lf_status lf_debug_triplets(lf_ctx* c, const lf_batch* b, int32_t* win_count, in
     LF_CUDA(c, launch_debug_triplets(c->kp, to_kbatch(b), (int*)c->wbeg.p, (uint8_t*)c->wcnt.p,
                                      (uint64_t*)c->keys.p, (uint8_t*)c->ntrip.p, win_count, n_trip, trip, trip_chi2,
                                      (cudaStream_t)stream));
+    return LF_OK;
+}
+
+lf_status lf_validate_batch(lf_ctx* c, const lf_batch* b, void* stream) {
+    if (!c) return LF_ERR_ARG;
+    lf_status st;
+    if ((st = check_batch(c, b)) != LF_OK) return st;
+    if ((st = ensure(c, c->valid, 2 * sizeof(int))) != LF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    int* bad = (int*)c->valid.p;
+    const int none = INT_MAX;
+    int h[2];
+    const KBatch kb = to_kbatch(b);
+    // offsets first: the bucket checks index with them
+    LF_CUDA(c, cudaMemcpyAsync(bad, &none, sizeof(int), cudaMemcpyHostToDevice, s));
+    LF_CUDA(c, cudaMemcpyAsync(bad + 1, &none, sizeof(int), cudaMemcpyHostToDevice, s));
+    LF_CUDA(c, launch_validate_offsets(kb, bad, c->n_sm, s));
+    LF_CUDA(c, cudaMemcpyAsync(h, bad, sizeof h, cudaMemcpyDeviceToHost, s));
+    LF_CUDA(c, cudaStreamSynchronize(s));
+    if (h[0] != none)
+        return fail(c, LF_ERR_ARG, "hit_offsets[%d] is outside 0..n_hits (%d) or decreases to the next entry", h[0],
+                    b->n_hits);
+    if (h[1] != none)
+        return fail(c, LF_ERR_ARG, "trk_offsets[%d] is outside 0..n_tracks (%d), decreases, or the last entry is not "
+                    "n_tracks", h[1], b->n_tracks);
+    LF_CUDA(c, cudaMemcpyAsync(bad, &none, sizeof(int), cudaMemcpyHostToDevice, s));
+    LF_CUDA(c, cudaMemcpyAsync(bad + 1, &none, sizeof(int), cudaMemcpyHostToDevice, s));
+    LF_CUDA(c, launch_validate_hits(kb, bad, c->n_sm, s));
+    LF_CUDA(c, cudaMemcpyAsync(h, bad, sizeof h, cudaMemcpyDeviceToHost, s));
+    LF_CUDA(c, cudaStreamSynchronize(s));
+    if (h[0] != none)
+        return fail(c, LF_ERR_ARG, "x is not ascending inside a bucket: packed hits %d and %d", h[0], h[0] + 1);
+    if (h[1] != none) return fail(c, LF_ERR_ARG, "x_coarse[%d] differs from x[%d]", h[1], 32 * h[1]);
     return LF_OK;
 }
 

@@ -200,6 +200,12 @@ cudaError_t launch_hits_to_raw(const uint8_t* found, int* hit_idx, const int* pe
                               cudaStream_t s);
 cudaError_t launch_compact(const int* trk_offsets, const uint8_t* found, int n_events, int* ev_count,
                            int* out_offsets, int* out_trk, int* n_out, cudaStream_t s, const int* n_dev = nullptr);
+// batch validation (lf_validate.cu): bad2[0] <- first bad hit_offsets entry,
+// bad2[1] <- first bad trk_offsets entry; then, with valid offsets,
+// bad2[0] <- first packed hit out of x order inside its bucket, bad2[1] <-
+// first x_coarse entry that differs from x[32 i].  bad2 preset to INT_MAX.
+cudaError_t launch_validate_offsets(const KBatch& b, int* bad2, int n_sm, cudaStream_t s);
+cudaError_t launch_validate_hits(const KBatch& b, int* bad2, int n_sm, cudaStream_t s);
 cudaError_t launch_debug_triplets(const KParams& k, const KBatch& b, const int* wbeg, const uint8_t* wcnt,
                                   const uint64_t* keys, const uint8_t* ntrip, int* win_count_out, int* n_trip_out,
                                   int* trip_out, float* chi2_out, cudaStream_t s);

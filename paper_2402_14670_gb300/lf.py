@@ -126,6 +126,8 @@ _lib.lf_find_tracks_batched.argtypes = [_P, C.POINTER(lf_batch), C.POINTER(lf_ou
 _lib.lf_find_tracks_batched.restype = C.c_int
 _lib.lf_debug_stages.argtypes = [_P, C.POINTER(lf_batch), _P, _P, _P, _P, _P, _P]
 _lib.lf_debug_stages.restype = C.c_int
+_lib.lf_validate_batch.argtypes = [_P, C.POINTER(lf_batch), _P]
+_lib.lf_validate_batch.restype = C.c_int
 _lib.lf_debug_triplets.argtypes = [_P, C.POINTER(lf_batch), _P, _P, _P, _P, _P]
 _lib.lf_debug_triplets.restype = C.c_int
 _lib.lf_sync_status.argtypes = [_P, _P, C.POINTER(C.c_int32)]
@@ -150,7 +152,8 @@ _lib.lf_host_free.argtypes = [_P]
 _lib.lf_host_free.restype = None
 
 EXPORTED = ["lf_create", "lf_destroy", "lf_last_error", "lf_device_sm_count", "lf_pack_hits", "lf_find_tracks",
-            "lf_find_tracks_batched", "lf_debug_stages", "lf_debug_triplets", "lf_sync_status", "lf_process_host",
+            "lf_find_tracks_batched", "lf_debug_stages", "lf_debug_triplets", "lf_validate_batch", "lf_sync_status",
+            "lf_process_host",
             "lf_find_tracks_static", "lf_host_alloc", "lf_host_free", "lf_reserve", "lf_device_host_numa",
             "lf_process_slot", "lf_graph_count"]
 
@@ -355,6 +358,10 @@ def lf_debug_stages(ctx, batch: lf_batch, win_begin, win_count, n_trip, trip, tr
     _check(ctx, _lib.lf_debug_stages(ctx, C.byref(batch), win_begin, win_count, n_trip, trip, trip_chi2, stream))
 
 
+def lf_validate_batch(ctx, batch: lf_batch, stream) -> None:
+    _check(ctx, _lib.lf_validate_batch(ctx, C.byref(batch), stream))
+
+
 def lf_debug_triplets(ctx, batch: lf_batch, win_count, n_trip, trip, trip_chi2, stream) -> None:
     _check(ctx, _lib.lf_debug_triplets(ctx, C.byref(batch), win_count, n_trip, trip, trip_chi2, stream))
 
@@ -504,6 +511,11 @@ class Tracker:
         lf_debug_triplets(self.ctx, b, _ptr(d["win_count"]), _ptr(d["n_trip"]), _ptr(d["trip"]),
                           _ptr(d["trip_chi2"]), _stream(stream))
         return d
+
+    def validate(self, packed: dict, states, n_events: int, stream=None) -> None:
+        """lf_validate_batch: raises LFError naming the first broken input
+        convention (offsets, x order inside a bucket, coarse index)."""
+        lf_validate_batch(self.ctx, self.batch_struct(packed, states, n_events), _stream(stream))
 
     def status(self, stream=None) -> int:
         return lf_sync_status(self.ctx, _stream(stream))

@@ -485,3 +485,48 @@ def test_coarse_index_from_the_pack_or_the_find(lfm, mode, tuning):
     for k in ("state", "quality"):
         assert torch.equal(with_idx[k][f].view(torch.int32), without[k][f].view(torch.int32)), k
     run_both(tr, b, mode=mode, tuning=tuning)
+
+
+def test_validate_batch(lfm):
+    """lf_validate_batch (debug mode, outside the hot path) passes a packed
+    batch and names the first broken convention: a decreasing or
+    out-of-range hit offset, track offsets that do not end at n_tracks, x out
+    of order inside a bucket (also NaN), a coarse index that differs from x."""
+    import copy
+    b = synth.generate(1, n_events=50).to("cuda")
+    tr = _tracker(lfm)
+    packed = tr.pack(b)
+    torch.cuda.synchronize()
+    tr.validate(packed, b, b.n_events)
+
+    def fails(pk, st, pattern):
+        with pytest.raises(lfm.LFError, match=pattern) as ei:
+            tr.validate(pk, st, b.n_events)
+        assert ei.value.status == lfm.LF_ERR_ARG
+
+    ho = packed["hit_offsets"]
+    bad = dict(packed, hit_offsets=ho.clone())
+    bad["hit_offsets"][30] = ho[31] + 1
+    fails(bad, b, r"hit_offsets\[30\]")
+    bad = dict(packed, hit_offsets=ho.clone())
+    bad["hit_offsets"][-1] = b.n_hits + 5
+    fails(bad, b, r"hit_offsets\[%d\]" % (24 * b.n_events))
+    st = copy.copy(b)
+    st.trk_offsets = b.trk_offsets.clone()
+    st.trk_offsets[-1] -= 1
+    fails(packed, st, r"trk_offsets\[%d\]" % b.n_events)
+    # two hits of one bucket swapped (the first bucket with two distinct x)
+    hoh = to_np(ho)
+    xs = to_np(packed["x"])
+    q = next(q for q in range(24 * b.n_events) if hoh[q + 1] - hoh[q] >= 2 and xs[hoh[q]] < xs[hoh[q] + 1])
+    s0 = int(hoh[q])
+    x2 = packed["x"].clone()
+    x2[s0], x2[s0 + 1] = packed["x"][s0 + 1], packed["x"][s0]
+    fails(dict(packed, x=x2, x_coarse=None), b, r"packed hits %d and %d" % (s0, s0 + 1))
+    x3 = packed["x"].clone()
+    x3[s0 + 1] = float("nan")
+    fails(dict(packed, x=x3, x_coarse=None), b, r"packed hits %d and %d" % (s0, s0 + 1))
+    xc = packed["x_coarse"].clone()
+    xc[3] += 1.0
+    fails(dict(packed, x_coarse=xc), b, r"x_coarse\[3\]")
+    tr.validate(packed, b, b.n_events)      # the packed batch itself still passes
