@@ -27,6 +27,14 @@ What pins what:
   invariants      unique hits, >= 9 hits, >= 1 stereo hit per station, Q < T_Q,
                   hits inside windows, true hits inside pre-cap windows
   binary32 fit    the binary32 fit agrees with the binary64 refit
+  strict cuts     the oracle's own chi2, Q and |dty| as thresholds are refused,
+                  one binary32 step above accepted (reading R12)
+  bending at 0    a doublet with exactly the input slope fails below p_bend
+  zone at ty = 0  the upper zone
+  window centre   x-layer centres equal the generator's true x with a far
+                  reference plane (the curvature and dRatio terms of the model)
+  missing x layer the x refit over five x hits stays exact
+  selection       the lowest accepted Q wins, whatever the triplet rank
   compact         exclusive scan of per-event counts
   no-UT (Sec. No-UT tuning, Eq. tol_noUT, Eq. noUT_size_window, Table poly_tol):
     window edges  hand-worked x_tol of the polynomial at the assumed momentum,
@@ -297,12 +305,12 @@ def pin_extension_T_uv(orc):
     kept just inside, dropped just outside; once with slopes that put T_uv on
     its floor (2 mm^2) and once above it."""
     p = oracle.default_params()
-    for tx, ty in ((0.008, 0.006), (0.09, 0.06)):
+    for tx, ty in ((0.008, 0.006), (0.09, 0.06), (-0.09, 0.06), (0.09, -0.06), (-0.09, -0.06)):
         st = synth.state_of(tx, ty, 0.1)
         t_uv = np.float32(p["T_uv_scale"]) * (np.float32(abs(np.float32(st[2]))) +
                                               np.float32(abs(np.float32(st[3]))))
         t_uv = max(np.float32(p["T_uv_min"]), np.float32(t_uv))
-        if tx < 0.05:
+        if abs(tx) < 0.05:
             assert t_uv == np.float32(p["T_uv_min"])
         else:
             assert t_uv > 2.5 * p["T_uv_min"]
@@ -417,26 +425,29 @@ def pin_bending_filter(orc):
 
 
 def pin_magnet_tolerance(orc):
-    # p = 20 GeV, slope 0.3 after the kick, x = 100 mm at the magnet centre
+    # p = 20 GeV, slope 0.3 after the kick, x = 100 mm at the magnet centre;
+    # then the mirror image (negative slope and charge: the tolerance grows
+    # with |t_x^doublet|)
     p, T0 = 20.0, 0.3
-    qop = 1.0 / p
-    txs = T0 - 1.2 * qop
-    st = (100.0 - txs * 2500.0, 270.0, txs, 0.1, qop)
     g = synth.Geometry()
-    line = lambda z: 100.0 + T0 * (z - g.z_magnet)
     dz = g.z[8] - g.z[0]
     r = (g.z[0] - g.z_magnet) / dz          # x offset at the magnet per unit x2 offset
     # decoy h2 shifted by s: |dx_mag| = r*s against tol = 8 + 96/p + 10*(T0 + s/dz)
     s_star = (8.0 + 96.0 / p + 10.0 * T0) / (r - 10.0 / dz)
-    for s, inside in ((s_star - 0.05, True), (s_star + 0.05, False)):
-        x1 = line(g.z[4]) + s * (g.z[4] - g.z[0]) / dz
-        hits = [(0, 1, line(g.z[0])), (8, 1, line(g.z[8])), (4, 1, line(g.z[4])),
-                (8, 1, line(g.z[8]) + s), (4, 1, x1)]
-        res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]))
-        perm = res["packed"]["perm"]
-        h2s = {int(perm[res["trip"][0, k, 3]]) for k in range(res["n_trip"][0])}
-        assert 1 in h2s, "true doublet lost"
-        assert (3 in h2s) == inside, ("magnet tolerance", s, h2s)
+    for sg in (1.0, -1.0):
+        qop = sg / p
+        txs = sg * T0 - 1.2 * qop
+        st = (sg * 100.0 - txs * 2500.0, 270.0, txs, 0.1, qop)
+        line = lambda z: sg * (100.0 + T0 * (z - g.z_magnet))
+        for s, inside in ((s_star - 0.05, True), (s_star + 0.05, False)):
+            x1 = line(g.z[4]) + sg * s * (g.z[4] - g.z[0]) / dz
+            hits = [(0, 1, line(g.z[0])), (8, 1, line(g.z[8])), (4, 1, line(g.z[4])),
+                    (8, 1, line(g.z[8]) + sg * s), (4, 1, x1)]
+            res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]))
+            perm = res["packed"]["perm"]
+            h2s = {int(perm[res["trip"][0, k, 3]]) for k in range(res["n_trip"][0])}
+            assert 1 in h2s, "true doublet lost"
+            assert (3 in h2s) == inside, ("magnet tolerance", sg, s, h2s)
 
 
 # ------------------------------------------------------------------- quality
@@ -512,6 +523,147 @@ def pin_ty_cut(orc):
         res = orc.run_batch(make_batch([dict(hits=hits, states=[(xs, ys, txs, tys + d, qop)])]),
                             params=_params(T_uv_min=1e4))
         assert bool(res["found"][0]) == found, ("T_ty", d)
+
+
+# ------------------------------------------------------------ cut boundaries
+
+def pin_cuts_strict(orc):
+    """Reading R12: the method's cuts are strict (the paper prints "<").  The
+    oracle's own chi2 of a triplet, Q of a candidate and |t_y fit - t_y in|
+    of a track are set as the thresholds T_triplet, T_Q and T_ty: at exactly
+    that value the triplet or track is refused, one binary32 step above it
+    accepted."""
+    up = lambda v: float(np.nextafter(np.float32(v), np.float32(np.inf), dtype=np.float32))
+    st = _vertical_track()
+    b = make_batch([dict(hits=[(0, 1, 100.0), (8, 1, 100.0), (4, 1, 101.25)], states=[st])])
+    r0 = orc.run_batch(b)
+    assert r0["n_trip"][0] == 1
+    chi2 = float(np.float32(r0["trip_chi2"][0, 0]))
+    assert chi2 > 1.0
+    assert orc.run_batch(b, params=_params(T_triplet=chi2))["n_trip"][0] == 0, "chi2 == T_triplet kept"
+    assert orc.run_batch(b, params=_params(T_triplet=up(chi2)))["n_trip"][0] == 1
+    # Q against T_Q (ten hits with known residuals, Q about 0.1)
+    hits, st, _, _ = known_residual_event((1, 6))
+    b = make_batch([dict(hits=hits, states=[st])])
+    r0 = orc.run_batch(b)
+    assert r0["found"][0]
+    q = float(np.float32(r0["quality"][0]))
+    assert 0.0 < q < 0.5
+    assert not orc.run_batch(b, params=_params(T_Q=q))["found"][0], "Q == T_Q accepted"
+    assert orc.run_batch(b, params=_params(T_Q=up(q)))["found"][0]
+    # |t_y fit - t_y in| against T_ty (input t_y 0.012 off the particle's)
+    tx, ty, p = 0.1, 0.1, 10.0
+    hits = track_hits(tx, ty, 1.0 / p)
+    xs, ys, txs, tys, qop = synth.state_of(tx, ty, 1.0 / p)
+    b = make_batch([dict(hits=hits, states=[(xs, ys, txs, tys + 0.012, qop)])])
+    par = dict(T_uv_min=1e4)
+    r0 = orc.run_batch(b, params=_params(**par))
+    assert r0["found"][0]
+    d = float(np.abs(np.float32(r0["state"][0, 3]) - np.float32(tys + 0.012)))
+    assert 0.005 < d < 0.02
+    assert not orc.run_batch(b, params=_params(T_ty=d, **par))["found"][0], "|dty| == T_ty accepted"
+    assert orc.run_batch(b, params=_params(T_ty=up(d), **par))["found"][0]
+
+
+def pin_bending_filter_zero(orc):
+    """Reading R6 of Sec. "Triplet Seeding": below p_bend the doublet slope
+    must move away from the input slope in the charge's bending direction; a
+    doublet with exactly the input slope fails, for either charge.  Here
+    (x2 - x0) / (z2 - z0) = 0.0625 exactly in binary32 and the input t_x is
+    0.0625; the same doublet seeds once the filter is off (p_bend = 0)."""
+    g = synth.Geometry()
+    z0, z1, z2 = (float(np.float32(g.z[l])) for l in (0, 4, 8))
+    txd = 0.0625
+    x0 = 10.0
+    x2 = x0 + txd * (z2 - z0)                         # 95.4375, exact
+    assert np.float32(np.float32(x2 - x0) / np.float32(z2 - z0)) == np.float32(txd)
+    x1 = x0 + txd * (z1 - z0) + 0.5                   # chi2 = 0.25
+    x_mag = x0 + txd * (g.z_magnet - z0)              # the doublet's line at the magnet
+    wide = dict(xtol_c=5000.0, uv_tol=5000.0)
+    for qop in (1.0 / 3.0, -1.0 / 3.0):
+        st = (x_mag - txd * (g.z_magnet - g.z_state), 270.0, txd, 0.1, qop)
+        b = make_batch([dict(hits=[(0, 1, x0), (8, 1, x2), (4, 1, x1)], states=[st])])
+        assert orc.run_batch(b, params=_params(**wide))["n_trip"][0] == 0, ("no bend accepted", qop)
+        assert orc.run_batch(b, params=_params(p_bend=0.0, **wide))["n_trip"][0] == 1
+
+
+def pin_zone_at_zero_ty(orc):
+    """Reading R20 of Sec. "Defining the search windows": an input track with
+    t_y = 0 exactly searches the upper zone (y >= 0)."""
+    tx, p = 0.05, 10.0
+    hits = track_hits(tx, 0.0, 1.0 / p)
+    st = synth.state_of(tx, 0.0, 1.0 / p)
+    assert st[3] == 0.0
+    for zone, found in ((1, True), (0, False)):
+        hz = [(l, zone, x) for (l, _, x) in hits]
+        res = orc.run_batch(make_batch([dict(hits=hz, states=[st])]))
+        assert bool(res["found"][0]) == found, ("zone at t_y = 0", zone)
+
+
+def pin_window_centre_model(orc):
+    """Sec. "Defining the search windows" with Eq. pt_kick and Eq.
+    dratio_model_x_expected: an x layer's window centre is the track's x
+    there, extrapolated to the magnet, kicked, and carried on the x(z) model
+    (c dz^2 (1 + dRatio dz) around z_ref); for particles of the generator
+    with exact q/p it is their true x.  With z_ref = 6000 mm the curvature
+    term is 10 to 60 um at these momenta, far above the binary32 rounding of
+    the centre (< 2 um at |x| < 4000 mm), so a dropped or wrong curvature or
+    dRatio term is seen."""
+    for pol in (1, -1):
+        geo = synth.Geometry(polarity=pol, z_ref=6000.0)
+        for tx, ty, qop in ((0.05, 0.1, 1.0 / 2.0), (-0.1, -0.05, -1.0 / 3.0), (0.2, 0.02, -1.0 / 1.5)):
+            _, _, xm = synth.trajectory(tx, ty, qop, geo)
+            st = synth.state_of(tx, ty, qop, geo)
+            zone = 1 if ty >= 0 else 0
+            res = orc.run_batch(make_batch([dict(hits=[(0, zone, 0.0)], states=[st])], geo),
+                                geometry=geo_dict(geo))
+            z = np.asarray(geo.z, np.float64)
+            dz = z - geo.z_ref
+            curv = np.abs(pol * geo.gamma * qop * dz * dz * (1.0 + geo.dratio * dz))
+            for l in (0, 3, 4, 7, 8, 11):
+                err = abs(float(res["win_centre"][0, l]) - float(np.ravel(xm)[l]))
+                assert err < 2e-3, ("window centre", pol, tx, qop, l, err)
+            assert curv[11] > 5e-3 and curv[11] * geo.dratio * dz[11] / (1.0 + geo.dratio * dz[11]) > 4e-3
+
+
+def pin_closed_form_missing_x_layer(orc):
+    """Closed form with a missing x layer: without its layer-3 hit a particle
+    seeds only from (0, 4, 8), finds nothing in layer 3, and the x refit over
+    the five x hits it has still returns the generating parameters (binary64
+    refit to 1e-5; binary32 as in pin_closed_form)."""
+    for tx, ty, p in ((0.05, 0.1, 10.0), (-0.12, -0.06, 4.0)):
+        hits, st = _extension_track(tx, ty, p, drop=(3,))
+        b = make_batch([dict(hits=hits, states=[st])])
+        b.hit_x64 = None
+        res = orc.run_batch(b)
+        assert res["found"][0] and res["nhits"][0] == 11 and res["hit_idx"][0, 3] < 0, ("missing x layer", tx)
+        truth = synth.truth_params(tx, ty, 1.0 / p)
+        for k, (rt, at) in enumerate([(1e-5, 1e-3), (1e-5, 2e-2), (1e-5, 1e-6), (1e-5, 2e-5),
+                                      (0.0, 5e-9), (1e-5, 1e-6)]):
+            assert _rel_close(res["state"][0, k], truth[k], rt, at), ("state", tx, k, res["state"][0, k], truth[k])
+
+
+def pin_selection_lowest_Q(orc):
+    """Sec. "Quality Filter": the track keeps, of its accepted candidates, the
+    one with the lowest Q (reading R18), whatever its triplet's rank.  On a
+    minimum-bias sample the output Q of every found track is the smallest Q
+    among its candidates that passed, and some tracks' lowest Q is not their
+    first candidate (so the rule is exercised)."""
+    b = synth.generate(1, n_events=25)
+    res = orc.run_batch(b)
+    n_not_first = 0
+    for t in np.nonzero(res["found"])[0]:
+        n = res["n_trip"][t]
+        ok = res["cand_status"][t, :n] == 0
+        q = res["cand_q"][t, :n]
+        assert ok.any()
+        qmin = np.min(q[ok])
+        assert np.float32(res["quality"][t]) == np.float32(qmin), ("selected Q", t)
+        first_ok = int(np.argmax(ok))
+        n_not_first += bool(q[first_ok] > qmin)
+    for t in np.nonzero(~res["found"].astype(bool))[0]:
+        assert not np.any(res["cand_status"][t, :res["n_trip"][t]] == 0)
+    assert n_not_first > 10
 
 
 # ---------------------------------------------------------------- invariants
@@ -754,4 +906,6 @@ ALL_PINS = [pin_pack_lexsort, pin_closed_form, pin_closed_form_md, pin_qop_polyn
             pin_magnet_tolerance, pin_known_residual_Q, pin_T_Q, pin_ty_cut, pin_invariants,
             pin_true_hits_in_window, pin_fit32_vs_fit64, pin_compact,
             pin_no_ut_window_edges, pin_no_ut_closed_form, pin_no_ut_closed_form_md, pin_no_ut_overlap,
-            pin_no_ut_magnet_tolerance, pin_no_ut_qop_unused]
+            pin_no_ut_magnet_tolerance, pin_no_ut_qop_unused,
+            pin_cuts_strict, pin_bending_filter_zero, pin_zone_at_zero_ty, pin_window_centre_model,
+            pin_closed_form_missing_x_layer, pin_selection_lowest_Q]
