@@ -748,9 +748,9 @@ def _no_ut(**kw):
     return p
 
 
-def _golden_no_ut_windows():
+def _golden_no_ut_windows(name="no_ut_window_examples.txt"):
     rows = []
-    with open(os.path.join(GOLDEN, "no_ut_window_examples.txt")) as f:
+    with open(os.path.join(GOLDEN, name)) as f:
         for ln in f:
             ln = ln.strip()
             if ln and not ln.startswith("#"):
@@ -769,10 +769,10 @@ def _side_ids(res, t, side):
     return out
 
 
-def pin_no_ut_window_edges(orc):
+def pin_no_ut_window_edges(orc, golden="no_ut_window_examples.txt", **params):
     g = synth.Geometry()
     xs, ys = 37.0, -21.0
-    for (tx, ty, _p, x_tol) in _golden_no_ut_windows():
+    for (tx, ty, _p, x_tol) in _golden_no_ut_windows(golden):
         zone = 1 if ty >= 0 else 0
         hits, inside = [], {0: {}, 1: {}}
         for l in range(12):
@@ -795,11 +795,19 @@ def pin_no_ut_window_edges(orc):
         # the input q/p is not used by the variant: give it a nonsense value
         st = (xs, ys, tx, ty, 0.7)
         b = make_batch([dict(hits=hits, states=[st])], g)
-        res = orc.run_batch(b, params=_no_ut())
+        res = orc.run_batch(b, params=_no_ut(**params))
         for sd in (0, 1):
             got = _side_ids(res, 0, sd)
             for l in range(12):
                 assert got[l] == sorted(inside[sd][l]), ("no-UT window", tx, ty, sd, l, got[l], inside[sd][l])
+
+
+def pin_no_ut_pt_min(orc):
+    """Eq. tol_noUT at an assumed momentum set by the pT threshold: with
+    pT_min = 1.5 GeV the hand-worked windows of
+    tests/golden/no_ut_window_examples_ptmin.txt (the default pT_min of 1 GeV
+    cannot tell pT_min / sin(theta) from sin(theta) * pT_min)."""
+    pin_no_ut_window_edges(orc, golden="no_ut_window_examples_ptmin.txt", pt_min=1.5)
 
 
 def pin_no_ut_closed_form(orc, polarity=1):
@@ -908,4 +916,4 @@ ALL_PINS = [pin_pack_lexsort, pin_closed_form, pin_closed_form_md, pin_qop_polyn
             pin_no_ut_window_edges, pin_no_ut_closed_form, pin_no_ut_closed_form_md, pin_no_ut_overlap,
             pin_no_ut_magnet_tolerance, pin_no_ut_qop_unused,
             pin_cuts_strict, pin_bending_filter_zero, pin_zone_at_zero_ty, pin_window_centre_model,
-            pin_closed_form_missing_x_layer, pin_selection_lowest_Q]
+            pin_closed_form_missing_x_layer, pin_selection_lowest_Q, pin_no_ut_pt_min]
