@@ -28,7 +28,9 @@ What pins what:
                   hits inside windows, true hits inside pre-cap windows
   binary32 fit    the binary32 fit agrees with the binary64 refit
   strict cuts     the oracle's own chi2, Q and |dty| as thresholds are refused,
-                  one binary32 step above accepted (reading R12)
+                  one binary32 step above accepted (reading R12); hits exactly
+                  at sqrt(T_x) and sqrt(T_uv) from an exact straight model
+                  likewise; the bending filter strictly below p_bend
   bending at 0    a doublet with exactly the input slope fails below p_bend
   zone at ty = 0  the upper zone
   window centre   x-layer centres equal the generator's true x with a far
@@ -418,7 +420,13 @@ def pin_bending_filter(orc):
     tx, ty, p = 0.05, 0.1, 4.0
     hits = track_hits(tx, ty, 1.0 / p)
     wide = dict(xtol_c=5000.0, uv_tol=5000.0)   # windows that hold the hits whatever the charge
-    for qop_in, p_bend, found in ((1.0 / p, 5.0, True), (-1.0 / p, 5.0, False), (-1.0 / p, 0.0, True)):
+    p5 = float(1.0 / abs(np.float32(-0.2)))             # 5.0: 1/|q/p| of q/p = -0.2 in binary32
+    assert np.float32(1.0) / np.abs(np.float32(-0.2)) == np.float32(5.0) == np.float32(p5)
+    above = float(np.nextafter(np.float32(5.0), np.float32(np.inf), dtype=np.float32))
+    # the filter applies strictly below p_bend: at p = p_bend exactly the
+    # wrongly bending doublet is kept, one binary32 step above it refused
+    for qop_in, p_bend, found in ((1.0 / p, 5.0, True), (-1.0 / p, 5.0, False), (-1.0 / p, 0.0, True),
+                                  (-0.2, 5.0, True), (-0.2, above, False)):
         st = synth.state_of(tx, ty, qop_in)
         res = orc.run_batch(make_batch([dict(hits=hits, states=[st])]), params=_params(p_bend=p_bend, **wide))
         assert bool(res["found"][0]) == found, ("bending filter", qop_in, p_bend)
@@ -563,6 +571,33 @@ def pin_cuts_strict(orc):
     assert 0.005 < d < 0.02
     assert not orc.run_batch(b, params=_params(T_ty=d, **par))["found"][0], "|dty| == T_ty accepted"
     assert orc.run_batch(b, params=_params(T_ty=up(d), **par))["found"][0]
+
+
+def pin_extension_cuts_strict(orc):
+    """Reading R12 for the extension cuts of Sec. "Extending triplets to
+    other layers": a hit whose squared distance to the expectation equals T_x
+    (missing x layer) or T_uv (stereo layer) is refused, one binary32 step of
+    the threshold above it is accepted.  The particle is straight at
+    x = 100 mm with y = 0 in the T stations (no layer 11, so only (0, 4, 8)
+    seeds), so the three-point solution and the refit are x = 100 exactly and
+    the probe hits at 101.5 and 102 mm sit at exactly 1.5 and 2 mm."""
+    up = lambda v: float(np.nextafter(np.float32(v), np.float32(np.inf), dtype=np.float32))
+    qop = 0.05
+    txs = -1.2 * qop
+    st = (100.0 - txs * 2500.0, 0.0, txs, 0.0, qop)
+    loose = dict(T_ty=1.0, T_Q=1e3)
+    for probe, layer, key, value in ((101.5, 3, "T_x", 2.25), (102.0, 5, "T_uv_min", 4.0)):
+        hits = [(l, 1, probe if l == layer else 100.0) for l in range(11)]
+        b = make_batch([dict(hits=hits, states=[st])])
+        for thr, kept in ((value, False), (up(value), True)):
+            par = _params(T_uv_scale=0.0, **loose)
+            if key == "T_x":
+                par.update(T_x=thr, T_uv_min=4.0)
+            else:
+                par.update(T_uv_min=thr)
+            res = orc.run_batch(b, params=par)
+            assert res["found"][0], (key, thr)
+            assert (res["hit_idx"][0, layer] >= 0) == kept, ("extension cut at equality", key, thr)
 
 
 def pin_bending_filter_zero(orc):
@@ -916,4 +951,5 @@ ALL_PINS = [pin_pack_lexsort, pin_closed_form, pin_closed_form_md, pin_qop_polyn
             pin_no_ut_window_edges, pin_no_ut_closed_form, pin_no_ut_closed_form_md, pin_no_ut_overlap,
             pin_no_ut_magnet_tolerance, pin_no_ut_qop_unused,
             pin_cuts_strict, pin_bending_filter_zero, pin_zone_at_zero_ty, pin_window_centre_model,
-            pin_closed_form_missing_x_layer, pin_selection_lowest_Q, pin_no_ut_pt_min]
+            pin_closed_form_missing_x_layer, pin_selection_lowest_Q, pin_no_ut_pt_min,
+            pin_extension_cuts_strict]

@@ -82,6 +82,21 @@ def _cases():
             hits, st = pins._extension_track(tx_, ty_, offsets={5: f * np.sqrt(t_uv)})
             out.append(("T_uv, slopes %+.2f %+.2f, x %.3f" % (tx_, ty_, f), make_batch([dict(hits=hits, states=[st])]),
                         None, None))
+    # extension cuts exactly at T_x and T_uv (a straight track at x = 100 mm, y = 0)
+    qop = 0.05
+    st = (100.0 + 1.2 * qop * 2500.0, 0.0, -1.2 * qop, 0.0, qop)
+    for probe, layer, key, value in ((101.5, 3, "T_x", 2.25), (102.0, 5, "T_uv_min", 4.0)):
+        b = make_batch([dict(hits=[(l, 1, probe if l == layer else 100.0) for l in range(11)], states=[st])])
+        for thr in (value, _up(value)):
+            par = pins._params(T_uv_scale=0.0, T_ty=1.0, T_Q=1e3)
+            par.update({key: thr} if key == "T_uv_min" else dict(T_x=thr, T_uv_min=4.0))
+            out.append(("%s at %.7g" % (key, thr), b, par, None))
+    # the bending filter at p = p_bend exactly and one step above
+    hits = track_hits(0.05, 0.1, 0.25)
+    st = synth.state_of(0.05, 0.1, -0.2)
+    b = make_batch([dict(hits=hits, states=[st])])
+    for pb in (5.0, _up(5.0)):
+        out.append(("p == p_bend %.7g" % pb, b, pins._params(p_bend=pb, xtol_c=5000.0, uv_tol=5000.0), None))
     # a missing x layer
     hits, st = pins._extension_track(-0.12, -0.06, 4.0, drop=(3,))
     out.append(("missing x layer", make_batch([dict(hits=hits, states=[st])]), None, None))
