@@ -19,6 +19,8 @@ What pins what:
   triplet chi2/K  chi2 of a hit placed at a known offset from the straight line;
                   K multiplies the intercept (Sec. Triplet Seeding)
   top-n           kept triplets are the smallest chi2 (prefix property)
+  brute force     every (h0, h1, h2) of tiny events enumerated in numpy binary32
+                  gives the oracle's triplet lists, order and chi2 bits
   bending filter  below 5 GeV the doublet must bend with the charge
   magnet tol      doublets inside/outside the 8..40 mm tolerance
   known-residual Q  Q of the paper's formula on residuals fixed by construction,
@@ -701,6 +703,77 @@ def pin_selection_lowest_Q(orc):
     assert n_not_first > 10
 
 
+# --------------------------------------------------------------- brute force
+
+def pin_triplets_brute_force(orc):
+    """Brute force on tiny events (Sec. "Triplet Seeding"): for every input
+    track, every (h0, h1, h2) of its windows in both configurations is
+    enumerated in binary32 (numpy), each (h0, h2) takes the h1 of smallest
+    |x1 - x1_expected| (ties to the lower index) if the doublet passes the
+    bending and magnet filters, and the triplets with chi2 < T_triplet sorted
+    by (chi2, configuration, h0, h2) and cut to n_triplets must be the
+    oracle's list, order and chi2 bits included.  Windows are the oracle's
+    (pinned separately); the paper's K constants make K != 1."""
+    f = np.float32
+    cfg_l = ((0, 4, 8), (3, 7, 11))
+    for paper_K, nt in ((False, 12), (True, 5)):
+        par = _params(n_hits_window=8, n_triplets=nt, **({} if not paper_K else
+                      dict(K_first=oracle.default_params(paper_K=True)["K_first"],
+                           K_last=oracle.default_params(paper_K=True)["K_last"])))
+        cfg = synth.EventConfig("tiny", 6, 41, ("fixed", 12), match_frac=0.8, extra=("none",),
+                                noise=("per_layer", 30), p_min=2.0)
+        b = synth.generate(cfg)
+        res = orc.run_batch(b, params=par)
+        pk = res["packed"]
+        x, z = pk["x"].astype(np.float32), pk["z"].astype(np.float32)
+        g = synth.Geometry()
+        st = np.stack([b.sx.numpy(), b.sy.numpy(), b.stx.numpy(), b.sty.numpy(), b.sqop.numpy()], 1).astype(np.float32)
+        n_checked = 0
+        for t in range(b.n_tracks):
+            xs, ys, txs, tys, qop = (f(v) for v in st[t])
+            x_mag_in = xs + txs * (f(g.z_magnet) - f(g.z_state))
+            pmom = f(1.0) / abs(qop)
+            pol = f(g.polarity)
+            bend = pol if qop > f(0.0) else -pol
+            tol_base = f(par["magtol_min"]) + f(par["magtol_c"]) / pmom
+            found = []
+            for c, (L0, L1, L2) in enumerate(cfg_l):
+                K = f(par["K_first"] if c == 0 else par["K_last"])
+                z1 = f(g.z[L1])
+                w = lambda l: range(int(res["win_begin"][t, l]), int(res["win_begin"][t, l] + res["win_count"][t, l]))
+                for h0 in w(L0):
+                    for h2 in w(L2):
+                        tx_d = (x[h2] - x[h0]) / (z[h2] - z[h0])
+                        if pmom < f(par["p_bend"]):
+                            d = tx_d - txs
+                            if not ((d > f(0.0)) if bend > f(0.0) else (d < f(0.0))):
+                                continue
+                        x_mag_d = x[h0] + tx_d * (f(g.z_magnet) - z[h0])
+                        tol = tol_base + f(par["magtol_tx"]) * abs(tx_d)
+                        tol = min(max(tol, f(par["magtol_min"])), f(par["magtol_max"]))
+                        if not (abs(x_mag_d - x_mag_in) < tol):
+                            continue
+                        x1e = z1 * tx_d + (x[h0] - tx_d * z[h0]) * K
+                        h1s = list(w(L1))
+                        if not h1s:
+                            continue
+                        dist = [abs(x[h] - x1e) for h in h1s]
+                        h1 = h1s[int(np.argmin(dist))]          # first of the smallest
+                        dx = x[h1] - x1e
+                        chi2 = dx * dx
+                        if chi2 < f(par["T_triplet"]):
+                            found.append((chi2, c, h0, h2, h1))
+            found.sort(key=lambda v: (v[0], v[1], v[2], v[3]))
+            found = found[:nt]
+            n = int(res["n_trip"][t])
+            assert n == len(found), ("brute force count", t, n, len(found))
+            for r, (chi2, c, h0, h2, h1) in enumerate(found):
+                assert tuple(res["trip"][t, r]) == (c, h0, h1, h2), ("brute force triplet", t, r)
+                assert np.float32(res["trip_chi2"][t, r]).view(np.uint32) == np.float32(chi2).view(np.uint32)
+            n_checked += n
+        assert n_checked > 50, n_checked
+
+
 # ---------------------------------------------------------------- invariants
 
 def pin_invariants(orc):
@@ -952,4 +1025,4 @@ ALL_PINS = [pin_pack_lexsort, pin_closed_form, pin_closed_form_md, pin_qop_polyn
             pin_no_ut_magnet_tolerance, pin_no_ut_qop_unused,
             pin_cuts_strict, pin_bending_filter_zero, pin_zone_at_zero_ty, pin_window_centre_model,
             pin_closed_form_missing_x_layer, pin_selection_lowest_Q, pin_no_ut_pt_min,
-            pin_extension_cuts_strict]
+            pin_extension_cuts_strict, pin_triplets_brute_force]
