@@ -10,12 +10,23 @@
 #include <map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lf.h"
 #include "lf_internal.h"
 
 using namespace lfk;
 
 namespace {
+
+// NVTX range over a scope: names the host-side enqueueing of each stage for a
+// timeline profiler (no cost without one attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct DevBuf {
     void* p = nullptr;
@@ -282,8 +293,14 @@ lf_status plain_stages(lf_ctx* c, const lf_batch* b, cudaStream_t s) {
         kb.x_coarse = (const float*)c->coarse.p;
         LF_CUDA(c, launch_coarse(kb, (float*)c->coarse.p, c->n_sm, s));
     }
-    LF_CUDA(c, launch_windows(c->kp, kb, te, wb, wc, s));
-    LF_CUDA(c, launch_triplets(c->kp, kb, te, wb, wc, (uint64_t*)c->keys.p, (uint8_t*)c->ntrip.p, s));
+    {
+        NvtxRange r("lf windows");
+        LF_CUDA(c, launch_windows(c->kp, kb, te, wb, wc, s));
+    }
+    {
+        NvtxRange r("lf triplets");
+        LF_CUDA(c, launch_triplets(c->kp, kb, te, wb, wc, (uint64_t*)c->keys.p, (uint8_t*)c->ntrip.p, s));
+    }
     return LF_OK;
 }
 
@@ -364,6 +381,7 @@ int32_t lf_device_host_numa(void) {
 }
 
 lf_status lf_pack_hits(lf_ctx* c, const lf_raw_hits* raw, const lf_packed* pk, void* stream) {
+    NvtxRange r("lf pack");
     if (!c) return LF_ERR_ARG;
     if (!raw || !pk) return fail(c, LF_ERR_ARG, "raw or packed is NULL");
     if (raw->n_events < 0 || raw->n_hits < 0) return fail(c, LF_ERR_ARG, "negative size");
@@ -381,6 +399,7 @@ lf_status lf_pack_hits(lf_ctx* c, const lf_raw_hits* raw, const lf_packed* pk, v
 }
 
 lf_status lf_find_tracks(lf_ctx* c, const lf_batch* b, const lf_output* o, void* stream) {
+    NvtxRange r("lf find (plain)");
     if (!c) return LF_ERR_ARG;
     lf_status st;
     if ((st = check_batch(c, b)) != LF_OK) return st;
@@ -494,6 +513,7 @@ lf_status launch_batched(lf_ctx* c, const lf_batch* b, const lf_output* o, const
             auto* nt = (uint8_t*)c->ntrip.p;
             auto* cd = (CandRec*)c->cands.p;
             LF_CUDA(c, launch_track_event(kb, te, s));
+            NvtxRange r("lf find stages (windows, triplets, extension)");
             LF_CUDA(c, launch_windows(c->kp, kb, te, wb, wc, s, c->cursor + 0, stage_grid(c, sh, 0)));
             LF_CUDA(c, launch_triplets(c->kp, kb, te, wb, wc, ky, nt, s, c->cursor + 1, stage_grid(c, sh, 1),
                                        sh.prefilter));
@@ -555,6 +575,7 @@ lf_status graph_replay(lf_ctx* c, const GraphKey& key, cudaStream_t s, Launch&& 
         ++c->graph_captures;
     }
     it->second.used = ++c->graph_clock;
+    NvtxRange r("lf graph replay");
     LF_CUDA(c, cudaGraphLaunch(it->second.exec, s));
     return LF_OK;
 }
@@ -618,6 +639,7 @@ lf_status lf_process_slot(lf_ctx* c, const lf_raw_hits* raw, const lf_packed* pk
                           const lf_gather* g, const int32_t* n_events_dev, const lf_output* o,
                           const lf_tuning* tuning, void* stream) {
     if (!c) return LF_ERR_ARG;
+    NvtxRange r("lf slot");
     lf_status st;
     if (!raw || !pk || !n_events_dev) return fail(c, LF_ERR_ARG, "raw, packed or n_events_dev is NULL");
     if ((st = check_batch(c, b)) != LF_OK) return st;
@@ -913,6 +935,7 @@ lf_status lf_process_host(lf_ctx* c, const lf_host_batch* hb, const lf_host_outp
                         (const float*)(A + o_d), (const float*)(A + o_w), (const uint8_t*)(A + o_pl)};
         lf_packed pk{(int32_t*)(A + o_ho), (float*)(A + o_px), (float*)(A + o_pz), (float*)(A + o_pd),
                      (float*)(A + o_pw), (uint8_t*)(A + o_pl2), (int32_t*)(A + o_pm), (float*)(A + o_pc)};
+        NvtxRange rk("lf host chunk (pack, find, copies out)");
         if ((rc = lf_pack_hits(sc, &raw, &pk, s_comp)) != LF_OK) break;
         lf_batch bt{ne, nh, nt, pk.hit_offsets, pk.x, pk.z, pk.dxdy, pk.w, (const int32_t*)(A + o_to),
                     (const float*)(A + o_st), (const float*)(A + o_st + 4 * T), (const float*)(A + o_st + 8 * T),
