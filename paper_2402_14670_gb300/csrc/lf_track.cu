@@ -1199,7 +1199,7 @@ __device__ __forceinline__ void prefetch_window_lines(const KBatch& b, const Slo
     }
 }
 
-__global__ void __launch_bounds__(XB_THREADS, 4) k_extend_block(KParams k, KBatch b, const int* __restrict__ wbeg,
+__global__ void __launch_bounds__(XB_THREADS, 5) k_extend_block(KParams k, KBatch b, const int* __restrict__ wbeg,
                                                               const uint8_t* __restrict__ wcnt,
                                                               const uint64_t* __restrict__ keys,
                                                               const uint8_t* __restrict__ ntrip, KOut o, int* cursor) {
@@ -1695,9 +1695,11 @@ cudaError_t stage_blocks_per_sm(const KParams& k, int* out4) {
                    : k.cap <= 16 ? (const void*)k_triplets<1, true, false>
                    : k.cap <= 32 ? (const void*)k_triplets<2, true, false>
                                  : (const void*)k_triplets<4, true, false>;
-    const void* fe = k.no_ut  ? (const void*)k_extend<1, true, true>
-                   : tpw == 2 ? (const void*)k_extend<2, true, false>
-                              : (const void*)k_extend<1, true, false>;
+    // the extension's grid follows its default form: the block form for
+    // VELO-UT input (the warp form, when chosen instead, then has a few more
+    // blocks than fit at once; the extra ones find the queue drained)
+    if (!k.no_ut) sme = xblock_smem_bytes(k.cap, k.n_trip);
+    const void* fe = k.no_ut ? (const void*)k_extend<1, true, true> : (const void*)k_extend_block;
     const void* fw = k.no_ut ? (const void*)k_windows<true, true> : (const void*)k_windows<true, false>;
     if ((err = set_smem(ft, smt)) != cudaSuccess) return err;
     if ((err = set_smem(fe, sme)) != cudaSuccess) return err;
