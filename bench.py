@@ -583,8 +583,8 @@ def main():
         fracs = (0.1, 0.2, 0.4, 0.6, 0.8, 1.0, 1.2)
         graphs = lambda srv: sum(sl.tr.graph_count() for sl in srv.slots)
         # events arriving in device memory (arrivals written straight to HBM)
-        srv = serve.Server(batch, n_slots=4, max_events=1024, budget_bytes=16 << 30)
-        srv.tune_buckets((256, 1024))
+        srv = serve.Server(batch, n_slots=4, max_events=2048, budget_bytes=16 << 30)
+        srv.tune_buckets((256, 2048))
         g0 = graphs(srv)
         n_sat = min(n_ev, 60000)
         sat_d = srv.run(np.zeros(n_sat))
@@ -592,7 +592,8 @@ def main():
         at80 = [p for p in pts_d if p["offered_frac_of_batched"] == 0.8][0]
         served = {"p99_bound_ms": P99_BOUND_MS, "bound_load_frac_of_batched": 0.8,
                   "bound_met": bool(at80["p99_ms"] <= P99_BOUND_MS),
-                  "slots": len(srv.slots), "budget_bytes": 16 << 30,
+                  "slots": len(srv.slots), "slot_events": 2048, "host_fed_slot_events": 1024,
+                  "budget_bytes": 16 << 30,
                   "batching": "oldest pending events in arrival order up to the slot's capacity in events, "
                               "hits and tracks; one lf_process_slot graph per slot and launch shape, replayed "
                               "for every batch size",
@@ -606,8 +607,8 @@ def main():
                               "latency = arrival to results on host"}}
         srv.close()
         # the same load batched by size class, for comparison
-        srv = serve.Server(batch, n_slots=4, max_events=1024, budget_bytes=16 << 30, group_by_size=True)
-        srv.tune_buckets((256, 1024))
+        srv = serve.Server(batch, n_slots=4, max_events=2048, budget_bytes=16 << 30, group_by_size=True)
+        srv.tune_buckets((256, 2048))
         served["device_resident"]["by_size_class_at_80"] = sweep_rates(srv, (0.8,), 100)[0]
         srv.close()
         # events arriving in page-locked host memory: copied into the device
