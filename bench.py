@@ -296,14 +296,27 @@ def pack_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def pack_traffic_per_launch(units_hits: int):
-    """DRAM bytes of k_pack_event from the committed ncu capture, scaled to
-    this launch by hits, or None when the pack kernel changed since."""
+def profile_for(config: int, key: str, digest: str):
+    """The committed ncu figures of one workload (DRAM bytes and warp
+    instructions of the captured launches), or None when that workload has
+    no capture or the captured sources (key: their hash field) changed."""
     p = os.path.join(ROOT, "profiles", "find_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("pack_source_sha256_16") != pack_source_hash():
+    if d.get(key) != digest:
+        return None
+    if int(d.get("config", 2)) == config:
+        return d
+    return d.get("configs", {}).get(str(config))
+
+
+def pack_traffic_per_launch(config: int, units_hits: int):
+    """DRAM bytes of k_pack_event from the committed capture of this
+    workload, scaled to this launch by hits, or None (no capture, or the pack
+    kernel changed since)."""
+    d = profile_for(config, "pack_source_sha256_16", pack_source_hash())
+    if d is None:
         return None
     k = [v for n, v in d.get("kernels", {}).items() if "k_pack" in n]
     if len(k) != 1:
@@ -311,23 +324,17 @@ def pack_traffic_per_launch(units_hits: int):
     return (float(k[0]["read_gb"]) + float(k[0]["write_gb"])) * 1e9 * units_hits / float(d["hits"])
 
 
-def find_profile():
-    """The committed ncu figures of the find kernels (DRAM bytes and warp
-    instructions of one launch on a 10 000-event slice), or None when the
-    kernels changed since the capture."""
-    p = os.path.join(ROOT, "profiles", "find_traffic.json")
-    if not os.path.exists(p):
-        return None
-    d = json.load(open(p))
-    if d.get("kernel_source_sha256_16") != kernel_source_hash():
-        return None
-    return d
+def find_profile(config: int):
+    """The committed ncu figures of the find kernels on this workload (one
+    launch on a slice of it), or None (no capture, or the kernels changed
+    since)."""
+    return profile_for(config, "kernel_source_sha256_16", kernel_source_hash())
 
 
-def traffic_per_launch(units_hits: int):
-    """DRAM bytes of the find kernels from the committed ncu capture, scaled
-    to this launch by hits, or None when the kernels changed since."""
-    d = find_profile()
+def traffic_per_launch(config: int, units_hits: int):
+    """DRAM bytes of the find kernels from the committed capture of this
+    workload, scaled to this launch by hits, or None."""
+    d = find_profile(config)
     if d is None:
         return None
     return float(d["dram_bytes_per_launch"]) * units_hits / float(d["hits"])
@@ -637,14 +644,14 @@ def main():
     roof = {"kernel": "find pipeline of lf_find_tracks_batched (persistent windows, triplet, extension and "
                       "selection kernels + compaction), one graph launch", "bound": "hbm",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_kind": peak_kind, "traffic": traffic_per_launch(n_hits), "algorithmic_bytes": algo,
+            "peak_kind": peak_kind, "traffic": traffic_per_launch(args.config, n_hits), "algorithmic_bytes": algo,
             "launch_ms": find_avg}
     # the find kernels are bound by instruction issue, not by DRAM: their warp
     # instructions (committed ncu count, scaled by input tracks) per second
     # against the issue peak (4 warp instructions per SM per cycle at the
     # median SM clock of the timed region)
     roof_issue = None
-    fp = find_profile()
+    fp = find_profile(args.config)
     if fp is not None and torch.cuda.is_available():
         n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
@@ -659,7 +666,7 @@ def main():
     roof_pack = {"kernel": "k_pack_event (persistent per-event distribution sort, payload through shared memory)", "bound": "hbm",
                  "achieved": pk_algo / (pack_avg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                  "frac": pk_algo / (pack_avg / 1e3) / 1e9 / peak, "launch_ms": pack_avg,
-                 "algorithmic_bytes": pk_algo, "traffic": pack_traffic_per_launch(n_hits)}
+                 "algorithmic_bytes": pk_algo, "traffic": pack_traffic_per_launch(args.config, n_hits)}
 
     # ---------------- CPU oracle on a bounded sample (rank 0, N = 1)
     cpu = None
