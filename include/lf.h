@@ -216,19 +216,20 @@ typedef struct {
  * parameter outside its range. */
 lf_status lf_create(const lf_geometry* geometry, const lf_params* params, lf_ctx** out);
 
-/* Release the context and its scratch (synchronises the device). */
+/* Release the context and its scratch (synchronises the device).
+ * Infrastructure: no step of the paper. */
 void lf_destroy(lf_ctx* ctx);
 
-/* Message of the last error on this context ("" if none). */
+/* Message of the last error on this context ("" if none).  Infrastructure. */
 const char* lf_last_error(const lf_ctx* ctx);
 
-/* Number of SMs of the current device (for launch sizing). */
+/* Number of SMs of the current device (for launch sizing).  Infrastructure. */
 int32_t lf_device_sm_count(void);
 
 /* Host NUMA node nearest to the current device (cudaDevAttrHostNumaId), or
  * -1 when the platform does not report one.  Page-locked host buffers placed
  * on that node (allocated by a thread running there) give the host link its
- * full bandwidth to this device. */
+ * full bandwidth to this device.  Infrastructure. */
 int32_t lf_device_host_numa(void);
 
 /* Bucket and sort raw hits (the per-layer x-sorted hit containers the
@@ -275,7 +276,8 @@ typedef struct {
 } lf_gather;
 
 /* Slot form, for a serving loop: pack (as lf_pack_hits) and the persistent
- * find (as lf_find_tracks_batched) of one batch held in a slot, the buffers
+ * find (as lf_find_tracks_batched; the method of the sections listed for
+ * lf_find_tracks) of one batch held in a slot, the buffers
  * of fixed capacity a server reuses from batch to batch, with the batch's
  * event count read from device memory when the kernels run.
  *   - raw, packed, batch and out are the slot's buffers.  raw->n_events ==
@@ -308,7 +310,7 @@ lf_status lf_process_slot(lf_ctx* ctx, const lf_raw_hits* raw, const lf_packed* 
                           const lf_tuning* tuning, void* stream);
 
 /* Number of CUDA graphs the context has captured since its creation (the
- * batched and slot forms), or -1 for a NULL context. */
+ * batched and slot forms), or -1 for a NULL context.  Infrastructure. */
 int64_t lf_graph_count(const lf_ctx* ctx);
 
 /* Host-resident batch for lf_process_host: pointers are HOST pointers
@@ -337,7 +339,8 @@ typedef struct {
  * so that later calls within those sizes allocate nothing.  Growing scratch
  * inside a call frees and reallocates device memory, and cudaFree
  * synchronises the whole device, so a serving loop reserves once at start.
- * LF_ERR_OOM when the allocation fails. */
+ * LF_ERR_OOM when the allocation fails.  Infrastructure: no step of the
+ * paper. */
 lf_status lf_reserve(lf_ctx* ctx, int32_t n_events, int32_t n_hits, int32_t n_tracks, const lf_tuning* tuning);
 
 /* Page-locked host memory of exactly `bytes` bytes (cudaHostAlloc, portable
@@ -347,11 +350,12 @@ lf_status lf_reserve(lf_ctx* ctx, int32_t n_events, int32_t n_hits, int32_t n_tr
  * block the calling thread until they finish, which serialises the copies
  * with the compute queued behind them.)  *out receives the pointer (NULL
  * when bytes is 0); LF_ERR_OOM when the allocation fails.  Release with
- * lf_host_free. */
+ * lf_host_free.  Infrastructure: no step of the paper. */
 lf_status lf_host_alloc(size_t bytes, void** out);
 void lf_host_free(void* p);
 
-/* End-to-end call on host buffers: the batch is cut at event boundaries into
+/* End-to-end call on host buffers (the method of the sections listed for
+ * lf_find_tracks, with the pack of lf_pack_hits): the batch is cut at event boundaries into
  * chunks of at most chunk_hits hits; each chunk is copied to the device,
  * packed, followed (persistent form) and its results copied back.  Three
  * internal streams (copies in, compute, copies out) chained by events over
@@ -376,8 +380,9 @@ lf_status lf_process_host(lf_ctx* ctx, const lf_host_batch* batch, const lf_host
  * owned by its own pool, code on a latency-critical path where cudaMalloc and
  * cudaFree (which synchronises the device) are not acceptable, or a framework
  * that forbids allocation after start-up.  Such callers cannot use lf_create.
- * This call runs the same persistent kernel and compaction as
- * lf_find_tracks_batched (default launch shape) without a context and without
+ * This call runs the same method (the sections listed for lf_find_tracks) in
+ * the persistent kernel and compaction of lf_find_tracks_batched (default
+ * launch shape) without a context and without
  * allocating: its scratch (work-queue cursor, per-event counts) is a static
  * device array of 4*(64 + LF_STATIC_MAX_EVENTS) bytes (about 1 MiB) that every
  * GPU loading the library keeps until the process exits.  The caller passes
@@ -395,14 +400,17 @@ lf_status lf_process_host(lf_ctx* ctx, const lf_host_batch* batch, const lf_host
 lf_status lf_find_tracks_static(const lf_geometry* geometry, const lf_params* params, const lf_batch* batch,
                                 const lf_output* out, void* stream);
 
-/* Stage dumps of the plain form for debugging and parity tests:
+/* Stage dumps of the plain form for debugging and parity tests (the windows
+ * of Sec. "Defining the search windows", the kept triplets of Sec. "Triplet
+ * Seeding"):
  * win_begin/win_count [n_tracks*12] (int32), n_trip [n_tracks] (int32),
  * trip [n_tracks*n_triplets*4] (int32 cfg, h0, h1, h2; packed indices),
  * trip_chi2 [n_tracks*n_triplets] (float).  Device pointers. */
 lf_status lf_debug_stages(lf_ctx* ctx, const lf_batch* batch, int32_t* win_begin, int32_t* win_count,
                           int32_t* n_trip, int32_t* trip, float* trip_chi2, void* stream);
 
-/* The same triplet dumps (win_count, n_trip, trip, trip_chi2 as above)
+/* The same triplet dumps (win_count, n_trip, trip, trip_chi2 as above; the
+ * kept triplets of Sec. "Triplet Seeding")
  * decoded from what the last lf_find_tracks_batched call on the stage
  * pipeline (lf_tuning.queue 0) left in the context's scratch, for that call's
  * batch: no stage runs again.  For parity tests of the persistent triplet
@@ -420,7 +428,9 @@ lf_status lf_debug_triplets(lf_ctx* ctx, const lf_batch* batch, int32_t* win_cou
  * (the buckets are checked only once the offsets pass). */
 lf_status lf_validate_batch(lf_ctx* ctx, const lf_batch* batch, void* stream);
 
-/* Synchronise the stream, read and clear the device status word.
+/* Synchronise the stream, read and clear the device status word (the
+ * capacity flags of the pack and of the capped windows and triplet lists of
+ * Sec. "Defining the search windows" and "Triplet Seeding").
  * Returns LF_OK, LF_ERR_CAPACITY or LF_ERR_TIMEOUT; *flags gets the bits. */
 lf_status lf_sync_status(lf_ctx* ctx, void* stream, int32_t* flags);
 
